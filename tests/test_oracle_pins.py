@@ -1,0 +1,519 @@
+"""Pins for the FP64 CPU oracle against facts fixed by the paper or by mathematics,
+independent of the oracle's own code: closed forms, exact discrete fixed points,
+invariants, library routines (numpy Philox, dense LU) and brute force.
+
+Each pin is chosen so that a plausible mistake (a dropped term, a wrong sign, a
+transposed index, a wrong boundary reflection) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_23812_gb300 import synth
+
+TWO_PI = 2.0 * math.pi
+
+
+def periodic_box(n, Re, dt, advection=1, origin=0.0):
+    return oracle.make_params(nx=n, ny=n, x0=origin, x1=origin + TWO_PI, y0=origin, y1=origin + TWO_PI,
+                              Re=Re, dt=dt, bc_x=1, bc_y=1, geometry=1, advection=advection)
+
+
+def face_coords(P):
+    dx, dy = P.dx, P.dy
+    xu = P.x0 + np.arange(P.nx + 1) * dx           # u faces (x)
+    yu = P.y0 + (np.arange(P.ny) + 0.5) * dy       # u faces (y)
+    xv = P.x0 + (np.arange(P.nx) + 0.5) * dx       # v faces (x)
+    yv = P.y0 + np.arange(P.ny + 1) * dy           # v faces (y)
+    return xu, yu, xv, yv
+
+
+# --------------------------------------------------------------------------
+# random numbers: Philox4x64-10 against numpy's implementation (a library
+# routine built from the same published definition), Box-Muller from its
+# textbook formula applied to numpy's words.
+# --------------------------------------------------------------------------
+def test_philox_matches_numpy():
+    M = 2**64 - 1
+    for key in [(0, 0), (123, 456), (M, 7), (1000, 0)]:
+        # counter pre-incremented by numpy: start at -1 so the first block is counter 0
+        bg = np.random.Philox(key=np.array(key, dtype=np.uint64),
+                              counter=np.array([M, M, M, M], dtype=np.uint64))
+        raw = bg.random_raw(20)
+        for b in range(5):
+            out = oracle.philox4x64_10([b, 0, 0, 0], key)
+            assert (out == raw[4 * b:4 * b + 4]).all(), (key, b)
+
+
+def test_normals_are_box_muller_of_philox_words():
+    seed, stream = 1001, 0
+    M = 2**64 - 1
+    bg = np.random.Philox(key=np.array([seed, stream], dtype=np.uint64),
+                          counter=np.array([M, M, M, M], dtype=np.uint64))
+    w = bg.random_raw(64).reshape(16, 4)
+    ref = []
+    for blk in w:
+        for a, b in ((blk[0], blk[1]), (blk[2], blk[3])):
+            u1 = (float(int(a) >> 11) + 1.0) * 2.0**-53
+            u2 = float(int(b) >> 11) * 2.0**-53
+            r = math.sqrt(-2.0 * math.log(u1))
+            ref += [r * math.cos(TWO_PI * u2), r * math.sin(TWO_PI * u2)]
+    got = oracle.normals(seed, stream, 0, 64)
+    np.testing.assert_allclose(got, ref, rtol=1e-14, atol=1e-15)
+    # an offset window is the same stream
+    np.testing.assert_array_equal(oracle.normals(seed, stream, 13, 20), got[13:33])
+
+
+def test_normals_distribution():
+    scipy_stats = pytest.importorskip("scipy.stats")
+    z = oracle.normals(99, 3, 0, 200000)
+    assert abs(z.mean()) < 5.0 / math.sqrt(len(z))
+    assert abs(z.var() - 1.0) < 5.0 * math.sqrt(2.0 / len(z))
+    assert scipy_stats.kstest(z, "norm").pvalue > 1e-4
+
+
+# --------------------------------------------------------------------------
+# Poiseuille: the exact discrete steady state with walls on face lines is
+# u_j = (f Re / 2) ((y_j - y_lo)(y_hi - y_j) + h^2/4)  (the h^2/4 term is what
+# the mirror-ghost no-slip rule adds to the parabola; it solves the discrete
+# equations exactly).  Pins diffusion, forcing, both wall reflections (domain
+# edge and buried solid faces) and the projection being inert.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("geometry", [1, 2])
+def test_poiseuille_horizontal_fixed_point(geometry):
+    lo, hi = (0.0, 1.0) if geometry == 1 else (0.25, 0.75)
+    P = oracle.make_params(nx=8, ny=32, x0=0.0, x1=0.5, y0=0.0, y1=1.0, Re=50.0, dt=2e-3,
+                           bc_x=1, bc_y=2, geometry=geometry, ch_lo=lo, ch_hi=hi)
+    fx, Re, dy = 0.3, P.Re, P.dy
+    _, yu, _, _ = face_coords(P)
+    prof = np.where((yu > lo) & (yu < hi), 0.5 * fx * Re * ((yu - lo) * (hi - yu) + 0.25 * dy * dy), 0.0)
+    u = np.repeat(prof[:, None], P.nx + 1, axis=1)
+    v = np.zeros((P.ny + 1, P.nx))
+    s = oracle.Sim(P)
+    s.set_state(u, v)
+    s.set_forcing(np.full_like(u, fx), np.zeros_like(v))
+    s.step(25)
+    u1, v1, _ = s.state()
+    assert np.abs(u1 - u).max() <= 1e-12 * np.abs(u).max()
+    assert np.abs(v1).max() <= 1e-13
+    # and the plain parabola (no h^2/4) is NOT a fixed point: the ghost rule matters
+    prof2 = np.where((yu > lo) & (yu < hi), 0.5 * fx * Re * (yu - lo) * (hi - yu), 0.0)
+    s.set_state(np.repeat(prof2[:, None], P.nx + 1, axis=1), v)
+    s.step(25)
+    assert np.abs(s.state()[0] - np.repeat(prof2[:, None], P.nx + 1, axis=1)).max() > 1e-6
+
+
+def test_poiseuille_vertical_fixed_point():
+    lo, hi = 0.25, 0.75
+    P = oracle.make_params(nx=32, ny=8, x0=0.0, x1=1.0, y0=0.0, y1=0.5, Re=40.0, dt=2e-3,
+                           bc_x=1, bc_y=1, geometry=3, ch_lo=lo, ch_hi=hi)
+    fy, Re, dx = -0.2, P.Re, P.dx
+    _, _, xv, _ = face_coords(P)
+    prof = np.where((xv > lo) & (xv < hi), 0.5 * fy * Re * ((xv - lo) * (hi - xv) + 0.25 * dx * dx), 0.0)
+    v = np.repeat(prof[None, :], P.ny + 1, axis=0)
+    u = np.zeros((P.ny, P.nx + 1))
+    s = oracle.Sim(P)
+    s.set_state(u, v)
+    s.set_forcing(np.zeros_like(u), np.full_like(v, fy))
+    s.step(25)
+    u1, v1, _ = s.state()
+    assert np.abs(v1 - v).max() <= 1e-12 * np.abs(v).max()
+    assert np.abs(u1).max() <= 1e-13
+
+
+# --------------------------------------------------------------------------
+# Taylor-Green, Stokes: on a square periodic MAC grid the sampled TG field is
+# discretely divergence-free and an eigenvector of the discrete Laplacian with
+# eigenvalue lam = -(4/dx^2) sin^2(dx/2) - (4/dy^2) sin^2(dy/2).  The explicit
+# scheme then multiplies the amplitude by the Euler-then-AB2 recurrence exactly.
+# --------------------------------------------------------------------------
+def tg_fields(P):
+    xu, yu, xv, yv = face_coords(P)
+    u = np.sin(xu)[None, :] * np.cos(yu)[:, None]
+    v = -np.cos(xv)[None, :] * np.sin(yv)[:, None]
+    return u, v
+
+
+def test_taylor_green_stokes_exact_recurrence():
+    P = periodic_box(16, Re=10.0, dt=0.01, advection=0)
+    u0, v0 = tg_fields(P)
+    nu, dt = 1.0 / P.Re, P.dt
+    lam = -(4 / P.dx**2) * math.sin(P.dx / 2) ** 2 - (4 / P.dy**2) * math.sin(P.dy / 2) ** 2
+    a = [1.0, 1.0 + dt * nu * lam]
+    for _ in range(40):
+        a.append(a[-1] + dt * nu * lam * (1.5 * a[-1] - 0.5 * a[-2]))
+    s = oracle.Sim(P)
+    s.set_state(u0, v0)
+    done = 0
+    for n in (1, 2, 7, 41):
+        s.step(n - done)
+        done = n
+        u, v, _ = s.state()
+        np.testing.assert_allclose(u, a[n] * u0, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(v, a[n] * v0, rtol=0, atol=1e-13)
+
+
+def test_taylor_green_second_order():
+    """Full Navier-Stokes TG decay u = sin x cos y e^{-2t/Re}: second-order error."""
+    errs = []
+    for n in (16, 32, 64):
+        dx = TWO_PI / n
+        P = periodic_box(n, Re=100.0, dt=0.2 * dx)
+        T = 0.8
+        steps = int(round(T / P.dt))
+        u0, v0 = tg_fields(P)
+        u, v, _, md, _ = oracle.trajectory(P, u0, v0, steps)
+        decay = math.exp(-2.0 * steps * P.dt / P.Re)
+        errs.append(max(np.abs(u - decay * u0).max(), np.abs(v - decay * v0).max()))
+        assert md < 1e-11
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(slopes) > 1.85, (errs, slopes)
+
+
+def test_manufactured_solution_second_order():
+    """Steady manufactured flow with a non-gradient advection term; f = (u.grad)u - lap(u)/Re.
+    A dropped or mis-signed advection or diffusion piece leaves an O(T) error instead of O(h^2)."""
+    sp = pytest.importorskip("sympy")
+    X, Y = sp.symbols("x y")
+    Re = 10.0
+    psi = sp.sin(X) * sp.sin(Y) + sp.Rational(3, 10) * sp.sin(2 * X + Y)
+    U, V = sp.diff(psi, Y), -sp.diff(psi, X)
+    fx = U * sp.diff(U, X) + V * sp.diff(U, Y) - (sp.diff(U, X, 2) + sp.diff(U, Y, 2)) / Re
+    fy = U * sp.diff(V, X) + V * sp.diff(V, Y) - (sp.diff(V, X, 2) + sp.diff(V, Y, 2)) / Re
+    lam = {k: sp.lambdify((X, Y), e, "numpy") for k, e in dict(psi=psi, U=U, V=V, fx=fx, fy=fy).items()}
+    errs, errs_noadv = [], []
+    for n in (16, 32, 64):
+        dx = TWO_PI / n
+        P = periodic_box(n, Re=Re, dt=min(0.1 * dx * dx * Re, 0.1 * dx))
+        xu, yu, xv, yv = face_coords(P)
+        xc_, yc_ = np.meshgrid(P.x0 + np.arange(n + 1) * dx, P.y0 + np.arange(n + 1) * P.dy)
+        ps = lam["psi"](xc_, yc_)                       # psi at cell corners [j][i]
+        u0 = (ps[1:, :] - ps[:-1, :]) / P.dy            # (ny, nx+1)
+        v0 = -(ps[:, 1:] - ps[:, :-1]) / dx             # (ny+1, nx)
+        fu = lam["fx"](xu[None, :], yu[:, None]) * np.ones((n, n + 1))
+        fv = lam["fy"](xv[None, :], yv[:, None]) * np.ones((n + 1, n))
+        ue = lam["U"](xu[None, :], yu[:, None]) * np.ones((n, n + 1))
+        ve = lam["V"](xv[None, :], yv[:, None]) * np.ones((n + 1, n))
+        steps = int(round(0.3 / P.dt))
+        u, v, _, _, _ = oracle.trajectory(P, u0, v0, steps, fu, fv)
+        errs.append(max(np.abs(u - ue).max(), np.abs(v - ve).max()))
+        # forcing without its advection part: the solution must drift O(1)
+        fxd = sp.lambdify((X, Y), -(sp.diff(U, X, 2) + sp.diff(U, Y, 2)) / Re, "numpy")
+        fyd = sp.lambdify((X, Y), -(sp.diff(V, X, 2) + sp.diff(V, Y, 2)) / Re, "numpy")
+        u2, v2, _, _, _ = oracle.trajectory(P, u0, v0, steps, fxd(xu[None, :], yu[:, None]) * np.ones((n, n + 1)),
+                                            fyd(xv[None, :], yv[:, None]) * np.ones((n + 1, n)))
+        errs_noadv.append(max(np.abs(u2 - ue).max(), np.abs(v2 - ve).max()))
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(slopes) > 1.85, (errs, slopes)
+    assert min(errs_noadv) > 20 * errs[-1]
+
+
+def test_inviscid_energy_conservation():
+    """Central divergence-form advection conserves discrete kinetic energy for a
+    divergence-free field; the only drift is the time integrator's, which falls
+    at least 2^2 per halving of dt (a sign error in any advection term gives a
+    drift that does not fall with dt)."""
+    drifts = []
+    n = 24
+    for dt in (0.02, 0.01):
+        P = periodic_box(n, Re=1e30, dt=dt)
+        dx = P.dx
+        xc_, yc_ = np.meshgrid(np.arange(n + 1) * dx, np.arange(n + 1) * dx)
+        ps = np.zeros_like(xc_)
+        r = np.random.default_rng(5)
+        for kx in range(1, 4):
+            for ky in range(1, 4):
+                ps += r.normal() * np.sin(kx * xc_ + r.uniform(0, 6)) * np.sin(ky * yc_ + r.uniform(0, 6)) / (kx * kx + ky * ky)
+        u0 = (ps[1:, :] - ps[:-1, :]) / dx
+        v0 = -(ps[:, 1:] - ps[:, :-1]) / dx
+        steps = int(round(0.6 / dt))
+        u, v, _, _, _ = oracle.trajectory(P, u0, v0, steps)
+        e0 = (u0[:, :-1] ** 2).sum() + (v0[:-1, :] ** 2).sum()
+        e1 = (u[:, :-1] ** 2).sum() + (v[:-1, :] ** 2).sum()
+        drifts.append(abs(e1 - e0) / e0)
+    assert drifts[0] < 1e-3
+    assert drifts[1] < drifts[0] / 3.5, drifts
+
+
+# --------------------------------------------------------------------------
+# Open cavity invariants: divergence below the solver tolerance, inflow flux
+# equals outflow flux, walls and buried faces hold zero, inlet holds erf(y/0.1).
+# --------------------------------------------------------------------------
+def test_cavity_invariants():
+    P = oracle.cavity_params(64, 32, 1000.0)
+    u0, v0 = synth.cavity_ic(64, 32)
+    s = oracle.Sim(P)
+    s.set_state(u0, v0)
+    s.step(15)
+    u, v, _ = s.state()
+    assert s.max_div() < 1e-11
+    qin, qout = s.fluxes()
+    assert abs(qin - qout) <= 1e-13 * abs(qin)
+    uk, vk = s.face_kinds()
+    assert np.all(u[(uk == oracle.FK_WALL) | (uk == oracle.FK_SOLID)] == 0.0)
+    assert np.all(v[(vk == oracle.FK_WALL) | (vk == oracle.FK_SOLID)] == 0.0)
+    yc = P.y0 + (np.arange(P.ny) + 0.5) * P.dy
+    inl = uk[:, 0] == oracle.FK_INLET
+    np.testing.assert_allclose(u[inl, 0], [math.erf(y / 0.1) for y in yc[inl]], rtol=1e-15)
+    assert np.all(yc[inl] > 0) and np.all(~inl[yc < 0])
+    F = oracle.fluid_mask(P)
+    # open cavity geometry: everything above y=0 fluid; below, exactly the cells with 0 < xc < 1
+    xc = P.x0 + (np.arange(P.nx) + 0.5) * P.dx
+    assert F[yc > 0].all()
+    assert (F[yc < 0] == ((xc > 0) & (xc < 1))[None, :]).all()
+
+
+def test_projection_idempotent_and_symmetric():
+    P = oracle.cavity_params(32, 16, 1000.0)
+    s = oracle.Sim(P)
+    uk, vk = s.face_kinds()
+    rng = np.random.default_rng(3)
+
+    def rand_field():
+        u = np.where(uk == oracle.FK_UNKNOWN, rng.standard_normal(uk.shape), 0.0)
+        v = np.where(vk == oracle.FK_UNKNOWN, rng.standard_normal(vk.shape), 0.0)
+        return u, v
+
+    a, b = rand_field(), rand_field()
+    pa, pb = s.project(*a), s.project(*b)
+    ppa = s.project(*pa)
+    np.testing.assert_allclose(ppa[0], pa[0], atol=1e-11)
+    np.testing.assert_allclose(ppa[1], pa[1], atol=1e-11)
+    lhs = (pa[0] * b[0]).sum() + (pa[1] * b[1]).sum()
+    rhs = (a[0] * pb[0]).sum() + (a[1] * pb[1]).sum()
+    assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + 1.0)
+    # projected field is discretely divergence-free
+    div = (pa[0][:, 1:] - pa[0][:, :-1]) / P.dx + (pa[1][1:, :] - pa[1][:-1, :]) / P.dy
+    F = oracle.fluid_mask(P).astype(bool)
+    assert np.abs(div[F]).max() < 1e-10
+
+
+# --------------------------------------------------------------------------
+# Poisson: periodic eigenfunctions (closed form), dense least-squares solve
+# (library) of the masked Neumann Laplacian assembled from the face rule.
+# --------------------------------------------------------------------------
+def test_negative_laplacian_periodic_eigen():
+    P = oracle.make_params(nx=20, ny=12, x0=0.0, x1=TWO_PI, y0=0.0, y1=TWO_PI, bc_x=1, bc_y=1, geometry=1)
+    s = oracle.Sim(P)
+    xc = (np.arange(P.nx) + 0.5) * P.dx
+    yc = (np.arange(P.ny) + 0.5) * P.dy
+    for kx, ky in ((1, 0), (2, 3), (3, 1)):
+        x = np.cos(kx * xc)[None, :] * np.cos(ky * yc)[:, None]
+        lam = (4 / P.dx**2) * math.sin(kx * P.dx / 2) ** 2 + (4 / P.dy**2) * math.sin(ky * P.dy / 2) ** 2
+        np.testing.assert_allclose(s.apply_negL(x), lam * x, atol=1e-10)
+
+
+def test_poisson_solve_matches_dense_lstsq():
+    P = oracle.cavity_params(24, 12, 1000.0)
+    s = oracle.Sim(P)
+    F = oracle.fluid_mask(P).astype(bool)
+    uk, vk = s.face_kinds()
+    ny, nx = F.shape
+    idx = -np.ones((ny, nx), dtype=int)
+    idx[F] = np.arange(F.sum())
+    n = F.sum()
+    A = np.zeros((n, n))
+    for j in range(ny):
+        for i in range(nx):
+            if not F[j, i]:
+                continue
+            for (di, dj, open_, h) in ((1, 0, i + 1 < nx and uk[j, i + 1] == oracle.FK_UNKNOWN, P.dx),
+                                       (-1, 0, i > 0 and uk[j, i] == oracle.FK_UNKNOWN, P.dx),
+                                       (0, 1, j + 1 < ny and vk[j + 1, i] == oracle.FK_UNKNOWN, P.dy),
+                                       (0, -1, j > 0 and vk[j, i] == oracle.FK_UNKNOWN, P.dy)):
+                if open_:
+                    A[idx[j, i], idx[j, i]] += 1 / h**2
+                    A[idx[j, i], idx[j + dj, i + di]] -= 1 / h**2
+    rng = np.random.default_rng(11)
+    b = np.zeros((ny, nx))
+    b[F] = rng.standard_normal(n)
+    b[F] -= b[F].mean()
+    x = s.poisson_solve(b)
+    xd = np.linalg.lstsq(A, b[F], rcond=None)[0]
+    xd -= xd.mean()
+    np.testing.assert_allclose(x[F], xd, atol=1e-9 * np.abs(xd).max())
+    assert np.all(x[~F] == 0.0)
+    # and the oracle's operator is the assembled one
+    np.testing.assert_allclose(s.apply_negL(x)[F], A @ x[F], atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Ensemble (Sec. 3.3.2): the sampler's factors reproduce the paper's kernel
+# exp(-d^2/a^2); E is sigma (Gx (x) Gy) Z restricted to the control cells; the
+# sample covariance of many draws approaches B.
+# --------------------------------------------------------------------------
+def test_sampler_factor_reproduces_gaussian_kernel():
+    for nx, ny in ((32, 16), (128, 64), (512, 256)):
+        P = oracle.cavity_params(nx, ny, 1000.0)
+        a = 0.05
+        Gx, Gy = oracle.sampler_factors(P, a)
+        ia, ib, ja, jb = oracle.control_rect(P)
+        xc = P.x0 + (np.arange(ia, ib + 1) + 0.5) * P.dx
+        yc = P.y0 + (np.arange(ja, jb + 1) + 0.5) * P.dy
+        Kx = np.exp(-((xc[:, None] - xc[None, :]) ** 2) / a**2)
+        Ky = np.exp(-((yc[:, None] - yc[None, :]) ** 2) / a**2)
+        np.testing.assert_allclose(Gx @ Gx.T, Kx, atol=1e-13)
+        np.testing.assert_allclose(Gy @ Gy.T, Ky, atol=1e-13)
+
+
+def test_ensemble_is_kronecker_draw_on_control_cells():
+    P = oracle.cavity_params(32, 16, 1000.0)
+    sigma, a, N = 0.1, 0.05, 3
+    nrx, nry, nxix, nxiy = oracle.sampler_dims(P, a)
+    rng = np.random.default_rng(2)
+    Z = rng.standard_normal((N, 2, nxiy, nxix))
+    E = oracle.ensemble_from_noise(P, sigma, a, N, Z)
+    Gx, Gy = oracle.sampler_factors(P, a)
+    ci, cj = oracle.control_cells(P)
+    ia, _, ja, _ = oracle.control_rect(P)
+    ncc = len(ci)
+    assert E.shape == (2 * ncc, N)
+    for k in range(N):
+        for c in range(2):
+            field = sigma * np.einsum("yk,ckx,xj->cyj", Gy, Z[k, c][None], Gx.T)[0]   # [iy][ix]
+            np.testing.assert_allclose(E[c * ncc:(c + 1) * ncc, k], field[cj - ja, ci - ia], atol=1e-14)
+    Es = oracle.ensemble_seeded(P, sigma, a, N, 1000)
+    Zs = oracle.normals(1000, 0, 0, N * 2 * nxiy * nxix).reshape(N, 2, nxiy, nxix)
+    np.testing.assert_allclose(Es, oracle.ensemble_from_noise(P, sigma, a, N, Zs), atol=0)
+
+
+def test_ensemble_sample_covariance_approaches_B():
+    P = oracle.make_params(nx=40, ny=40, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=1, bc_y=1, geometry=1)
+    region = (0.3, 0.45, 0.4, 0.5)
+    sigma, a, N = 0.1, 0.05, 4000
+    E = oracle.ensemble_seeded(P, sigma, a, N, 77, region=region)
+    ci, cj = oracle.control_cells(P, region)
+    x = P.x0 + (ci + 0.5) * P.dx
+    y = P.y0 + (cj + 0.5) * P.dy
+    B = sigma**2 * np.exp(-((x[:, None] - x[None, :]) ** 2 + (y[:, None] - y[None, :]) ** 2) / a**2)
+    ncc = len(ci)
+    for c in range(2):
+        S = E[c * ncc:(c + 1) * ncc] @ E[c * ncc:(c + 1) * ncc].T / N
+        assert np.abs(S - B).max() < 5 * sigma**2 * math.sqrt(2.0 / N)
+    # components are independent
+    C = E[:ncc] @ E[ncc:].T / N
+    assert np.abs(C).max() < 5 * sigma**2 * math.sqrt(2.0 / N)
+
+
+def test_control_to_faces_is_cell_average():
+    P = oracle.cavity_params(32, 16, 1000.0)
+    ci, cj = oracle.control_cells(P)
+    ncc = len(ci)
+    s = oracle.Sim(P)
+    uk, vk = s.face_kinds()
+    q = ncc // 2
+    f = np.zeros(2 * ncc)
+    f[q] = 1.0
+    f[ncc + q] = -2.0
+    fu, fv = oracle.control_to_faces(P, f)
+    i, j = ci[q], cj[q]
+    expect_u = np.zeros_like(fu)
+    for ii in (i, i + 1):
+        if uk[j, ii] == oracle.FK_UNKNOWN:
+            expect_u[j, ii] = 0.5
+    expect_v = np.zeros_like(fv)
+    for jj in (j, j + 1):
+        if vk[jj, i] == oracle.FK_UNKNOWN:
+            expect_v[jj, i] = -1.0
+    np.testing.assert_array_equal(fu, expect_u)
+    np.testing.assert_array_equal(fv, expect_v)
+    # the control region is the fluid part of [-0.5,1]x[-0.2,0.3] (centres, inclusive)
+    F = oracle.fluid_mask(P)
+    xc = P.x0 + (np.arange(P.nx) + 0.5) * P.dx
+    yc = P.y0 + (np.arange(P.ny) + 0.5) * P.dy
+    inside = ((xc[None, :] >= -0.5) & (xc[None, :] <= 1.0) & (yc[:, None] >= -0.2) & (yc[:, None] <= 0.3)) & (F > 0)
+    assert inside.sum() == ncc
+    assert inside[cj, ci].all()
+
+
+# --------------------------------------------------------------------------
+# EnVar gradient (Eq. gradient_EnVar) against closed forms and brute force.
+# --------------------------------------------------------------------------
+def test_gradient_quadratic_closed_form():
+    """J(w) = 1/2 w^T Q w + b^T w with E = I: forward differences of step eps give
+    exactly Q w + b + eps/2 diag(Q); plus the prior gradient (N-1) w."""
+    rng = np.random.default_rng(4)
+    N = 6
+    A = rng.standard_normal((N, N))
+    Q = A @ A.T + N * np.eye(N)
+    bvec = rng.standard_normal(N)
+    w = rng.standard_normal(N)
+    eps = 1e-3
+    Jf = lambda x: 0.5 * x @ Q @ x + bvec @ x
+    J = np.array([Jf(w)] + [Jf(w + eps * np.eye(N)[i]) for i in range(N)])
+    g, jp = oracle.gradient_from_costs(J, w, eps)
+    np.testing.assert_allclose(g, Q @ w + bvec + 0.5 * eps * np.diag(Q) + (N - 1) * w, rtol=1e-9)
+    assert jp == pytest.approx(0.5 * (N - 1) * w @ w, rel=1e-15)
+
+
+def test_envar_gradient_matches_central_differences():
+    """Brute force: each g_i must agree with a central difference of the oracle's
+    own observation cost along column i of E (forcings built here, not by the
+    oracle's EnVar driver), to O(eps)."""
+    P = oracle.cavity_params(32, 16, 300.0)
+    N, eps, sigma, a = 3, 1e-2, 0.1, 0.05
+    E = oracle.ensemble_seeded(P, sigma, a, N, 1000)
+    u0, v0 = synth.cavity_ic(32, 16)
+    w = np.array([0.3, -0.2, 0.1])
+    n_steps, n_window = 120, 60
+    for mode, key in ((oracle.COST_DOMAIN, "J_domain"), (oracle.COST_SENSORS, "J_sensor")):
+        out = oracle.envar_gradient(P, u0, v0, E, w, eps, n_steps, n_window, cost_mode=mode, nthreads=4)
+
+        def Jobs(f):
+            fu, fv = oracle.control_to_faces(P, f)
+            return oracle.member_run(P, u0, v0, n_steps, n_window, fu, fv)[key]
+
+        f0 = E @ w
+        assert out["J"][0] == pytest.approx(Jobs(f0), rel=1e-12)
+        h = 1e-2
+        gc = np.array([(Jobs(f0 + h * E[:, i]) - Jobs(f0 - h * E[:, i])) / (2 * h) for i in range(N)])
+        gobs = out["g"] - (N - 1) * w
+        assert np.abs(gobs - gc).max() <= 0.05 * np.abs(gc).max() + 1e-12, (mode, gobs, gc)
+        # and its members are the N+1 forcings of Eq. (fdapprox)
+        for i in range(N):
+            assert out["J"][i + 1] == pytest.approx(Jobs(f0 + eps * E[:, i]), rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Costs (Sec. 4.1, Eq. specific_cost_function; Eq. kinenergy): closed forms.
+# --------------------------------------------------------------------------
+def test_costs_closed_form_on_stokes_decay():
+    """With Stokes TG the window samples are a_t * (initial field), so both costs
+    are known in closed form from the exact amplitude recurrence."""
+    P = periodic_box(16, Re=5.0, dt=0.02, advection=0, origin=-math.pi)  # sensors (x, 0) interior
+    u0, v0 = tg_fields(P)
+    nu, dt = 1.0 / P.Re, P.dt
+    lam = -(4 / P.dx**2) * math.sin(P.dx / 2) ** 2 - (4 / P.dy**2) * math.sin(P.dy / 2) ** 2
+    a = [1.0, 1.0 + dt * nu * lam]
+    n_steps, n_window = 30, 12
+    for _ in range(n_steps):
+        a.append(a[-1] + dt * nu * lam * (1.5 * a[-1] - 0.5 * a[-2]))
+    at = np.array(a[n_steps - n_window + 1:n_steps + 1])
+    var_sum = ((at - at.mean()) ** 2).sum()
+    uc = 0.5 * (u0[:, :-1] + u0[:, 1:])
+    vc = 0.5 * (v0[:-1, :] + v0[1:, :])
+    Jd = P.dx * P.dy / (2 * n_window) * ((uc**2).sum() + (vc**2).sum()) * var_sum
+    s = oracle.Sim(P)
+    s.set_state(u0, v0)
+    s0 = s.sensors()
+    Js = 0.5 * (s0**2).sum() * var_sum
+    out = oracle.member_run(P, u0, v0, n_steps, n_window, want_series=True)
+    assert out["J_domain"] == pytest.approx(Jd, rel=1e-10)
+    assert out["J_sensor"] == pytest.approx(Js, rel=1e-10)
+    np.testing.assert_allclose(out["series"], at[:, None] * s0[None, :], atol=1e-14)
+
+
+def test_sensors_exact_for_bilinear_field():
+    P = oracle.cavity_params(64, 32, 1000.0)
+    xu, yu, xv, yv = face_coords(P)
+    u = 0.3 + 0.7 * xu[None, :] - 0.4 * yu[:, None]
+    v = -0.2 + 0.5 * xv[None, :] + 0.9 * yv[:, None]
+    s = oracle.Sim(P)
+    s.set_state(u, v)
+    got = s.sensors()
+    for q in range(4):
+        x = 0.2 * (q + 1)
+        assert got[2 * q] == pytest.approx(0.3 + 0.7 * x, abs=1e-14)
+        assert got[2 * q + 1] == pytest.approx(-0.2 + 0.5 * x, abs=1e-14)
