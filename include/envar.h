@@ -1,0 +1,185 @@
+/*
+ * envar.h -- C ABI of the GB300 (sm_103a) EnVar open-cavity library.
+ *
+ * The library advances an ensemble of forced 2-D incompressible Navier-Stokes
+ * open-cavity simulations on one GPU, accumulates each member's fluctuation
+ * cost, and projects the cost anomalies onto the control perturbations to give
+ * the ensemble-variational (EnVar) gradient of arXiv 2605.23812:
+ *
+ *   f   = f_e + E w                               Sec. 3.3.1, Eq. (ensemble_representation), f_e = 0
+ *   J(w)= 1/2 ||y - H q(E w)||^2 + (N-1)/2 w^T w  Eq. (J_w), R = I, y = 0 (Sec. 4.1)
+ *   Y_i ~ (H q(E w + eps E_i) - H q(E w)) / eps   Eq. (fdapprox)
+ *   dJ/dw = Y^T (H q - y) + (N-1) w               Eq. (gradient_EnVar)
+ *   w  <- w + dw                                  Sec. 3.3.1 (weight update); dw = -alpha g/(N-1)
+ *
+ * Every call runs its work in the library's own CUDA kernels on the stream
+ * given to envar_init; there is no CPU fallback.
+ *
+ * Conventions shared by all calls
+ *  - Return value: 0 on success, a negative ENVAR_E* code on failure.  The
+ *    message of the last failure is returned by envar_last_error(h).
+ *  - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA memory),
+ *    owned by the caller, and must stay valid until the call's stream work has
+ *    finished.  Pointers named *_host are host pointers; calls that write them
+ *    synchronise the stream before returning.
+ *  - Field layouts (row-major, float64): u is [ny][nx+1] (x-velocity on
+ *    vertical faces), v is [ny+1][nx] (y-velocity on horizontal faces), p is
+ *    [ny][nx] (cell centres).
+ *  - Control vectors have n_ctrl = 2 * n_cc entries: [fx over control cells,
+ *    fy over control cells]; control cells are the fluid cells whose centre
+ *    lies in cfg.region (inclusive), ordered row-major (y outer, x inner).
+ *    E is n_ctrl x N, column-major (column k contiguous).
+ *  - A handle is not thread-safe; calls on one handle are stream-ordered.
+ */
+#ifndef ENVAR_H
+#define ENVAR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ENVAR_ABI_VERSION 1
+
+enum {
+    ENVAR_OK = 0,
+    ENVAR_EINVAL = -1,     /* bad argument or configuration */
+    ENVAR_ENOMEM = -2,     /* device allocation failed */
+    ENVAR_ECUDA = -3,      /* CUDA runtime error */
+    ENVAR_ESTATE = -4,     /* call out of order (e.g. envar_cost before a forward run) */
+    ENVAR_EDEVICE = -5     /* device is not an sm_103 GPU */
+};
+
+/* Precision / batching of the forward ensemble (spec patterns 1 and 2). */
+enum {
+    ENVAR_FP64_PLAIN = 0,   /* one member at a time, all arithmetic FP64 */
+    ENVAR_FP64_BATCHED = 1, /* all N+1 members per launch, all arithmetic FP64 */
+    ENVAR_MIXED = 2         /* all members per launch; FP32 tendencies, FP32 multigrid and inner
+                               CG; FP64 state, FP64 Poisson residual with iterative refinement,
+                               FP64 dot products and FP64 cost accumulation */
+};
+
+/* Observation operator H of Sec. 4.1. */
+enum {
+    ENVAR_COST_DOMAIN = 0,  /* J = 1/(2 n_w) sum_t sum_cells |u'|^2 dx dy  (Eq. kinenergy / n_w) */
+    ENVAR_COST_SENSORS = 1  /* J = 1/2 sum_{sensors, t} |u'(x_s, t)|^2, x_s = 1/5..4/5, y = 0
+                               (Eq. specific_cost_function) */
+};
+
+/* Per-member status bits (envar_member_status). */
+enum {
+    ENVAR_ST_NONFINITE = 1,     /* NaN or Inf met in the velocity */
+    ENVAR_ST_DIVERGENCE = 2,    /* pressure solve ended above div_tol */
+    ENVAR_ST_CFL = 4            /* |u| dt / h exceeded 1 */
+};
+
+typedef struct envar_config {
+    int nx, ny;              /* cells; nx, ny even, nx >= 8, ny >= 4 */
+    double x0, x1, y0, y1;   /* box; the cavity is [0,1] x [y0,0] with fluid above y = 0 */
+    double Re;               /* Reynolds number U D / nu (Sec. 2) */
+    double cfl;              /* dt = cfl * min(dx, dy) / U, U = 1 */
+    double inlet_delta;      /* inlet u = erf(y / inlet_delta) above the lip, v = 0 */
+    double conv_speed;       /* convective outflow speed */
+    int n_steps;             /* time steps per forward evaluation (warm-up + window) */
+    int n_window;            /* the last n_window steps form the cost window (Sec. 4.1) */
+    int n_members;           /* N_ens, ensemble perturbations; N+1 forward runs */
+    double region[4];        /* control region [x0, x1, y0, y1] (Sec. 4.1) */
+    double sigma;            /* prior standard deviation (Eq. covarianceB, sigma_i = sigma) */
+    double corr_len;         /* a_x = a_y (Eq. covarianceB), c_xy = infinity */
+    double eps;              /* finite-difference step of Eq. (fdapprox) */
+    unsigned long long seed; /* ensemble seed (Philox4x64-10 key) */
+    int precision;           /* ENVAR_FP64_PLAIN / ENVAR_FP64_BATCHED / ENVAR_MIXED */
+    int cost_mode;           /* ENVAR_COST_DOMAIN / ENVAR_COST_SENSORS */
+    double div_tol;          /* pressure solve stops when max |D u^{n+1}| <= div_tol */
+    int max_outer;           /* cap on FP64 residual refinements per time step */
+    int max_inner;           /* cap on inner preconditioned-CG iterations per refinement */
+    double inner_rtol;       /* inner CG stops when r^T z <= inner_rtol^2 * r0^T z0 */
+    int nu_pre, nu_post;     /* red-black Gauss-Seidel sweeps before / after coarse correction */
+    int coarse_sweeps;       /* symmetric sweep pairs on the coarsest multigrid level */
+    int steps_per_graph;     /* time steps per captured CUDA graph (even) */
+} envar_config;
+
+typedef struct envar_handle_s *envar_handle;
+
+/* Fill *cfg with the library defaults for an nx x ny open-cavity grid. */
+int envar_default_config(envar_config *cfg, int nx, int ny);
+
+/* Create a handle: checks the device (sm_103), builds the geometry and multigrid
+ * hierarchy on the device, allocates all internal buffers (owned by the handle,
+ * freed by envar_destroy), and draws the ensemble E from N(0, B) with the
+ * seeded white-noise convolution sampler (Sec. 3.3.2, Eq. covarianceB).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream). */
+int envar_init(envar_handle *h, const envar_config *cfg, void *cuda_stream);
+
+/* Release every resource of the handle (NULL is accepted). */
+int envar_destroy(envar_handle h);
+
+/* Message of the last failure on this handle (or of the last envar_init failure
+ * when h is NULL).  Static storage inside the handle; valid until the next call. */
+const char *envar_last_error(envar_handle h);
+
+/* Sizes: n_ctrl (= 2 x control cells), number of forward members in flight,
+ * multigrid levels, and dt.  Any pointer may be NULL. */
+int envar_sizes(envar_handle h, int *n_ctrl, int *n_cc, int *n_levels, double *dt);
+
+/* Initial state shared by all members (raw fields; the library applies the wall,
+ * inlet and outlet rules when loading them).  u0_dev [ny][nx+1], v0_dev [ny+1][nx]. */
+int envar_set_initial_state(envar_handle h, const double *u0_dev, const double *v0_dev);
+
+/* Replace the ensemble matrix (n_ctrl x N column-major, device). */
+int envar_set_ensemble(envar_handle h, const double *E_dev, int n_ctrl, int N);
+/* Copy the ensemble matrix out (n_ctrl x N column-major, device). */
+int envar_get_ensemble(envar_handle h, double *E_dev);
+
+/* N+1 forward evaluations of Fig. (envar_loop): member 0 with forcing E w,
+ * member i with E w + eps E_i (Eq. fdapprox), each over n_steps from the
+ * initial state, accumulating the window cost in-kernel (Welford for DOMAIN,
+ * sensor samples for SENSORS).  w_dev: N doubles (device). */
+int envar_forward_ensemble(envar_handle h, const double *w_dev);
+
+/* Observation costs of the last forward run: J_host[N+1] (member 0 first) and
+ * J_prior = (N-1)/2 w^T w of Eq. (J_w) for the w of that run (either may be NULL). */
+int envar_cost(envar_handle h, double *J_host, double *J_prior_host);
+
+/* EnVar gradient of Eq. (gradient_EnVar) for the last forward run: g_host[N].
+ * SENSORS: Y from Eq. (fdapprox) on the sensor time series, g = Y^T (Hq_0 - y) + (N-1) w.
+ * DOMAIN: g_i = (J_i - J_0)/eps + (N-1) w_i  (= Y_i^T (Hq_0 - y) + O(eps)).
+ * df_dev (nullable, n_ctrl doubles, device) receives E g / (N-1). */
+int envar_gradient(envar_handle h, double *g_host, double *df_dev);
+
+/* One EnVar iteration: forward ensemble at w, costs, gradient, and the update
+ * w <- w - alpha g / (N-1) (Sec. 3.3.1 weight update with the prior-Hessian
+ * step).  w_inout_host: N doubles (host, in/out).  J0_out_host (nullable):
+ * total cost J(w) = J_obs(member 0) + J_prior before the update. */
+int envar_step(envar_handle h, double alpha, double *w_inout_host, double *J0_out_host);
+
+/* Run ONE member with a given control vector f (n_ctrl doubles, device) over
+ * n_steps and return its observation cost (host).  Member slot 0 is used. */
+int envar_forward_control(envar_handle h, const double *f_dev, double *J_host);
+
+/* Per-member status words (ENVAR_ST_* bits) of the last forward run: N+1 ints (host). */
+int envar_member_status(envar_handle h, int *status_host);
+
+/* Final state of member m of the last forward run (device pointers, compact
+ * layouts above; p is mean-zero over fluid cells).  Any pointer may be NULL. */
+int envar_get_state(envar_handle h, int member, double *u_dev, double *v_dev, double *p_dev);
+
+/* Sensor samples of member m over the window: [n_window][8] = (u, v) at the 4
+ * sensors, host. */
+int envar_get_series(envar_handle h, int member, double *series_host);
+
+/* Diagnostics of the last forward run: max |D u| over all members and steps,
+ * and total pressure-refinement / inner-CG iterations summed over steps and
+ * members (host; any pointer may be NULL). */
+int envar_diagnostics(envar_handle h, double *max_div, long long *outer_its, long long *inner_its);
+
+/* Advance the members' current state by n_steps without resetting it (the
+ * forcing of the last forward run stays in place).  For step-level timing and
+ * trajectory tests: call envar_forward_ensemble(h, w) with n_steps set in the
+ * configuration first, or envar_reset_members(h, w) to load the initial state. */
+int envar_reset_members(envar_handle h, const double *w_dev);
+int envar_advance(envar_handle h, int n_steps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ENVAR_H */

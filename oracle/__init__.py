@@ -111,6 +111,7 @@ def lib():
         "orc_trajectory": (c_int, [P, _dp, _dp, c_void_p, _dp, _dp, c_int, _dp, _dp, _dp,
                                    ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
         "orc_gradient_from_costs": (None, [c_int, _dp, _dp, c_double, _dp, ctypes.POINTER(c_double)]),
+        "orc_sensor_gradient": (None, [c_int, c_int, _dp, c_double, _dp, _dp]),
         "orc_envar_gradient": (c_int, [P, _dp, _dp, _dp, c_int, c_int, _dp, _dp, c_double,
                                        c_int, c_int, c_int, c_int, _dp, _dp,
                                        ctypes.POINTER(c_double), c_void_p]),
@@ -371,6 +372,16 @@ def gradient_from_costs(J, w, eps: float):
     jp = c_double()
     lib().orc_gradient_from_costs(len(w), J, w, eps, g, ctypes.byref(jp))
     return g, jp.value
+
+
+def sensor_gradient(series, w, eps: float):
+    """Eq. (gradient_EnVar) with Y from Eq. (fdapprox) on the sensor series [N+1][n_window][8]."""
+    series = np.ascontiguousarray(series, dtype=np.float64)
+    N = series.shape[0] - 1
+    g = np.zeros(N)
+    lib().orc_sensor_gradient(N, series.shape[1], series.reshape(-1), eps,
+                              np.ascontiguousarray(w, dtype=np.float64), g)
+    return g
 
 
 def envar_gradient(P: Params, u0, v0, E, w, eps: float, n_steps: int, n_window: int,

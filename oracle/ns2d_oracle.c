@@ -1128,6 +1128,32 @@ void orc_gradient_from_costs(int N, const double *J, const double *w, double eps
     if (J_prior) *J_prior = 0.5 * (double)(N - 1) * jp;
 }
 
+/* Eq. (gradient_EnVar) with Y built column by column from Eq. (fdapprox) on the
+ * sensor observations of Sec. 4.1 (R = I, y = 0): H q_m = u'_m(x_s, t_j), the
+ * fluctuation about the member's own window mean, for s = 1..4 sensors x 2
+ * components and every window step;  Y_i = (H q_i - H q_0)/eps,
+ * g = Y^T (H q_0 - y) + (N-1) w.   series: [N+1][n_window][8]. */
+void orc_sensor_gradient(int N, int n_window, const double *series, double eps, const double *w, double *g)
+{
+    size_t nobs = (size_t)n_window * 8;
+    double *h0 = (double *)xcalloc(nobs, sizeof(double)), *hi = (double *)xcalloc(nobs, sizeof(double));
+    for (int m = 0; m <= N; ++m) {
+        double *h = (m == 0) ? h0 : hi;
+        const double *sm = series + (size_t)m * nobs;
+        for (int c = 0; c < 8; ++c) {
+            double mean = 0.0;
+            for (int t = 0; t < n_window; ++t) mean += sm[(size_t)t * 8 + c];
+            mean /= n_window;
+            for (int t = 0; t < n_window; ++t) h[(size_t)t * 8 + c] = sm[(size_t)t * 8 + c] - mean;
+        }
+        if (m == 0) continue;
+        double acc = 0.0;
+        for (size_t k = 0; k < nobs; ++k) acc += (hi[k] - h0[k]) / eps * h0[k];
+        g[m - 1] = acc + (double)(N - 1) * w[m - 1];
+    }
+    free(h0); free(hi);
+}
+
 typedef struct {
     const orc_params *P;
     const double *region, *u0, *v0, *E, *w;

@@ -1,0 +1,12 @@
+"""GB300 (sm_103a) ensemble-variational open-loop control of an open-cavity flow.
+
+The hot path of arXiv 2605.23812 -- N+1 forced Navier-Stokes cavity runs, their
+fluctuation-energy costs and the EnVar gradient -- runs in the CUDA kernels of
+``libenvar_gb300.so`` behind the C ABI of ``include/envar.h``.  ``capi`` is the
+thin ctypes binding; ``synth`` holds the seeded synthetic inputs.
+"""
+from .capi import (COST_DOMAIN, COST_SENSORS, FP64_BATCHED, FP64_PLAIN, MIXED, Config, Ensemble, EnvarError,
+                   default_config, header_symbols, lib)
+
+__all__ = ["Config", "Ensemble", "EnvarError", "default_config", "header_symbols", "lib", "FP64_PLAIN",
+           "FP64_BATCHED", "MIXED", "COST_DOMAIN", "COST_SENSORS"]

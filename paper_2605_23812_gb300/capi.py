@@ -1,0 +1,237 @@
+"""ctypes binding of the C ABI in ``include/envar.h`` (argument marshalling only).
+
+Every computation runs in ``libenvar_gb300.so`` (sm_103a kernels).  There is no
+Python or CPU fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libenvar_gb300.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "envar.h")
+
+c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+FP64_PLAIN, FP64_BATCHED, MIXED = 0, 1, 2
+COST_DOMAIN, COST_SENSORS = 0, 1
+ST_NONFINITE, ST_DIVERGENCE, ST_CFL = 1, 2, 4
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESTATE", -5: "EDEVICE"}
+
+
+class Config(ctypes.Structure):
+    """Mirror of ``envar_config``."""
+    _fields_ = [
+        ("nx", c_int), ("ny", c_int),
+        ("x0", c_double), ("x1", c_double), ("y0", c_double), ("y1", c_double),
+        ("Re", c_double), ("cfl", c_double), ("inlet_delta", c_double), ("conv_speed", c_double),
+        ("n_steps", c_int), ("n_window", c_int), ("n_members", c_int),
+        ("region", c_double * 4),
+        ("sigma", c_double), ("corr_len", c_double), ("eps", c_double),
+        ("seed", ctypes.c_ulonglong),
+        ("precision", c_int), ("cost_mode", c_int),
+        ("div_tol", c_double),
+        ("max_outer", c_int), ("max_inner", c_int), ("inner_rtol", c_double),
+        ("nu_pre", c_int), ("nu_post", c_int), ("coarse_sweeps", c_int), ("steps_per_graph", c_int),
+    ]
+
+
+def header_symbols() -> list[str]:
+    """Entry points declared in include/envar.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(envar_\w+)\s*\(", txt, flags=re.M)))
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() (nvcc, sm_103a)")
+    L = ctypes.CDLL(LIB_PATH)
+    H = c_void_p
+    sig = {
+        "envar_default_config": [ctypes.POINTER(Config), c_int, c_int],
+        "envar_init": [ctypes.POINTER(c_void_p), ctypes.POINTER(Config), c_void_p],
+        "envar_destroy": [H],
+        "envar_sizes": [H, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                        ctypes.POINTER(c_double)],
+        "envar_set_initial_state": [H, c_void_p, c_void_p],
+        "envar_set_ensemble": [H, c_void_p, c_int, c_int],
+        "envar_get_ensemble": [H, c_void_p],
+        "envar_forward_ensemble": [H, c_void_p],
+        "envar_cost": [H, c_void_p, c_void_p],
+        "envar_gradient": [H, c_void_p, c_void_p],
+        "envar_step": [H, c_double, c_void_p, c_void_p],
+        "envar_forward_control": [H, c_void_p, c_void_p],
+        "envar_member_status": [H, c_void_p],
+        "envar_get_state": [H, c_int, c_void_p, c_void_p, c_void_p],
+        "envar_get_series": [H, c_int, c_void_p],
+        "envar_diagnostics": [H, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong),
+                              ctypes.POINTER(ctypes.c_longlong)],
+        "envar_reset_members": [H, c_void_p],
+        "envar_advance": [H, c_int],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = c_int
+    L.envar_last_error.argtypes = [H]
+    L.envar_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def default_config(nx: int, ny: int, **kw) -> Config:
+    c = Config()
+    lib().envar_default_config(ctypes.byref(c), nx, ny)
+    for k, v in kw.items():
+        if k == "region":
+            c.region = (c_double * 4)(*v)
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def _ptr(t):
+    return c_void_p(0 if t is None else t.data_ptr())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(c_void_p)
+
+
+class EnvarError(RuntimeError):
+    pass
+
+
+class Ensemble:
+    """One handle of the library: N+1 forced cavity simulations and their EnVar gradient."""
+
+    def __init__(self, cfg: Config, stream=None):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = c_void_p()
+        rc = lib().envar_init(ctypes.byref(h), ctypes.byref(cfg), c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise EnvarError(f"envar_init: {ERRORS.get(rc, rc)}: {lib().envar_last_error(None).decode()}")
+        self._h = h
+        n_ctrl, n_cc, nlev, dt = c_int(), c_int(), c_int(), c_double()
+        self._check(lib().envar_sizes(h, ctypes.byref(n_ctrl), ctypes.byref(n_cc), ctypes.byref(nlev),
+                                      ctypes.byref(dt)), "envar_sizes")
+        self.n_ctrl, self.n_cc, self.n_levels, self.dt = n_ctrl.value, n_cc.value, nlev.value, dt.value
+        self.N = cfg.n_members
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise EnvarError(f"{what}: {ERRORS.get(rc, rc)}: {lib().envar_last_error(self._h).decode()}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().envar_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, a, shape=None):
+        t = self.torch
+        x = a if isinstance(a, t.Tensor) else t.as_tensor(np.asarray(a, dtype=np.float64))
+        x = x.to(device="cuda", dtype=t.float64).contiguous()
+        if shape is not None:
+            x = x.reshape(shape)
+        return x
+
+    # ---- inputs
+    def set_initial_state(self, u0, v0):
+        u = self._dev(u0, (self.cfg.ny, self.cfg.nx + 1))
+        v = self._dev(v0, (self.cfg.ny + 1, self.cfg.nx))
+        self.torch.cuda.current_stream().synchronize()
+        self._check(lib().envar_set_initial_state(self._h, _ptr(u), _ptr(v)), "envar_set_initial_state")
+
+    def set_ensemble(self, E):
+        """E: (n_ctrl, N) array or tensor."""
+        Et = self._dev(E, (self.n_ctrl, self.N)).t().contiguous()   # column-major storage
+        self.torch.cuda.current_stream().synchronize()
+        self._check(lib().envar_set_ensemble(self._h, _ptr(Et), self.n_ctrl, self.N), "envar_set_ensemble")
+
+    def get_ensemble(self):
+        out = self.torch.empty((self.N, self.n_ctrl), dtype=self.torch.float64, device="cuda")
+        self._check(lib().envar_get_ensemble(self._h, _ptr(out)), "envar_get_ensemble")
+        return out.t()
+
+    # ---- EnVar calls
+    def forward_ensemble(self, w):
+        wt = self._dev(w, (self.N,))
+        self.torch.cuda.current_stream().synchronize()
+        self._check(lib().envar_forward_ensemble(self._h, _ptr(wt)), "envar_forward_ensemble")
+
+    def cost(self):
+        J = np.zeros(self.N + 1)
+        jp = np.zeros(1)
+        self._check(lib().envar_cost(self._h, _np_ptr(J), _np_ptr(jp)), "envar_cost")
+        return J, float(jp[0])
+
+    def gradient(self, want_df=False):
+        g = np.zeros(self.N)
+        df = self.torch.empty(self.n_ctrl, dtype=self.torch.float64, device="cuda") if want_df else None
+        self._check(lib().envar_gradient(self._h, _np_ptr(g), _ptr(df)), "envar_gradient")
+        return (g, df) if want_df else g
+
+    def step(self, alpha, w):
+        w = np.ascontiguousarray(w, dtype=np.float64).copy()
+        J0 = np.zeros(1)
+        self._check(lib().envar_step(self._h, float(alpha), _np_ptr(w), _np_ptr(J0)), "envar_step")
+        return w, float(J0[0])
+
+    def forward_control(self, f):
+        ft = self._dev(f, (self.n_ctrl,))
+        J = np.zeros(1)
+        self.torch.cuda.current_stream().synchronize()
+        self._check(lib().envar_forward_control(self._h, _ptr(ft), _np_ptr(J)), "envar_forward_control")
+        return float(J[0])
+
+    # ---- diagnostics
+    def member_status(self):
+        s = np.zeros(self.N + 1, dtype=np.int32)
+        self._check(lib().envar_member_status(self._h, _np_ptr(s)), "envar_member_status")
+        return s
+
+    def get_state(self, member):
+        t = self.torch
+        u = t.empty((self.cfg.ny, self.cfg.nx + 1), dtype=t.float64, device="cuda")
+        v = t.empty((self.cfg.ny + 1, self.cfg.nx), dtype=t.float64, device="cuda")
+        p = t.empty((self.cfg.ny, self.cfg.nx), dtype=t.float64, device="cuda")
+        self._check(lib().envar_get_state(self._h, int(member), _ptr(u), _ptr(v), _ptr(p)), "envar_get_state")
+        return u, v, p
+
+    def get_series(self, member):
+        s = np.zeros((self.cfg.n_window, 8))
+        self._check(lib().envar_get_series(self._h, int(member), _np_ptr(s)), "envar_get_series")
+        return s
+
+    def diagnostics(self):
+        md, oi, ii = c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(lib().envar_diagnostics(self._h, ctypes.byref(md), ctypes.byref(oi), ctypes.byref(ii)),
+                    "envar_diagnostics")
+        return {"max_div": md.value, "outer_its": oi.value, "inner_its": ii.value}
+
+    def reset_members(self, w=None):
+        wt = None if w is None else self._dev(w, (self.N,))
+        self.torch.cuda.current_stream().synchronize()
+        self._check(lib().envar_reset_members(self._h, _ptr(wt)), "envar_reset_members")
+
+    def advance(self, n):
+        self._check(lib().envar_advance(self._h, int(n)), "envar_advance")

@@ -1,0 +1,772 @@
+// envar_capi.cu -- the C ABI (include/envar.h): handle lifecycle, geometry and multigrid set-up,
+// device buffers, CUDA-graph capture of the time step, and the EnVar calls of Fig. (envar_loop).
+//
+// Set-up (once per handle, host C++): cell mask of the open cavity, face kinds, inlet table,
+// multigrid hierarchy (masks and face conductances), control rectangle.  Everything per
+// iteration -- ensemble draws, forcings, the N+1 forward runs, costs, gradient and update -- runs
+// in the library's CUDA kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "envar_internal.cuh"
+#include "../../include/envar.h"
+
+namespace envar {
+void launch_axis_factor(double h, double a, int ncell, int m, int pad, int nxi, double *G, cudaStream_t st);
+}
+using namespace envar;
+
+struct GraphSet {
+    cudaGraphExec_t many = nullptr;   // steps_per_graph steps
+    cudaGraphExec_t one = nullptr;    // one step
+};
+
+struct envar_handle_s {
+    envar_config cfg{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int N = 0, Mall = 0;              // perturbations, member slots
+    bool batched = true, mixed = false;
+    Grid g{};
+    double x0 = 0, y0 = 0;
+    long long nfluid = 0;
+    // levels
+    int nlev = 0, ncoarse = 0;
+    Level lev[MAX_LEVELS]{};
+    // control
+    int ia = 0, ja = 0, nrx = 0, nry = 0, ncc = 0, n_ctrl = 0, nrect = 0;
+    int *d_cidx = nullptr;
+    uint8_t *d_rect_ctrl = nullptr;
+    double *d_Erect = nullptr, *d_E = nullptr, *d_frect = nullptr;
+    // state
+    double *d_u0 = nullptr, *d_v0 = nullptr;
+    double *d_u = nullptr, *d_v = nullptr, *d_us = nullptr, *d_vs = nullptr, *d_p = nullptr;
+    void *d_Ru = nullptr, *d_Rv = nullptr;
+    size_t tend_bytes = 0;
+    double *d_ubc = nullptr, *d_wf = nullptr, *d_series_slot = nullptr, *d_series = nullptr;
+    PoissonBufs pb{};
+    PoissonCfg pc{};
+    Partials pt{};
+    MemberCtl *d_ctl = nullptr;
+    // results
+    double *d_Jd_slot = nullptr, *d_Js_slot = nullptr, *d_Jd = nullptr, *d_Js = nullptr, *d_costpart = nullptr;
+    double *d_w = nullptr, *d_g = nullptr, *d_jprior = nullptr;
+    std::vector<MemberCtl> ctl_all;
+    bool have_forward = false, have_ic = false;
+    int last_member_slot0 = -1;       // member held in slot 0 after a plain-mode run
+    std::vector<void *> allocs;
+    GraphSet graphs[2];               // [0]: all slots, [1]: one slot
+    char err[512] = {0};
+};
+
+static char g_init_err[512];
+
+static void set_err(envar_handle h, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h ? h->err : g_init_err, sizeof(g_init_err), fmt, ap);
+    va_end(ap);
+}
+
+#define CK(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            set_err(h, "%s failed: %s", #call, cudaGetErrorString(e_));                      \
+            return ENVAR_ECUDA;                                                              \
+        }                                                                                    \
+    } while (0)
+
+template <class T>
+static int dalloc(envar_handle h, T **p, size_t count)
+{
+    void *q = nullptr;
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        set_err(h, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+        *p = nullptr;
+        return ENVAR_ENOMEM;
+    }
+    h->allocs.push_back(q);
+    *p = reinterpret_cast<T *>(q);
+    return ENVAR_OK;
+}
+#define DA(ptr, n)                                      \
+    do {                                                \
+        int rc_ = dalloc(h, &(ptr), (size_t)(n));       \
+        if (rc_) return rc_;                            \
+    } while (0)
+
+extern "C" int envar_default_config(envar_config *c, int nx, int ny)
+{
+    if (!c) return ENVAR_EINVAL;
+    std::memset(c, 0, sizeof(*c));
+    c->nx = nx; c->ny = ny;
+    c->x0 = -1.2; c->x1 = 2.5; c->y0 = -1.0; c->y1 = 1.0;
+    c->Re = 1000.0; c->cfl = 0.3; c->inlet_delta = 0.1; c->conv_speed = 1.0;
+    c->n_steps = 1000; c->n_window = 500; c->n_members = 8;
+    c->region[0] = -0.5; c->region[1] = 1.0; c->region[2] = -0.2; c->region[3] = 0.3;
+    c->sigma = 0.1; c->corr_len = 0.05; c->eps = 1e-2; c->seed = 1000ULL;
+    c->precision = ENVAR_MIXED; c->cost_mode = ENVAR_COST_DOMAIN;
+    c->div_tol = 1e-10; c->max_outer = 4; c->max_inner = 6; c->inner_rtol = 1e-4;
+    c->nu_pre = 2; c->nu_post = 2; c->coarse_sweeps = 8; c->steps_per_graph = 10;
+    return ENVAR_OK;
+}
+
+// ------------------------------------------------------------------------------------ set-up
+static int build_geometry(envar_handle h)
+{
+    const envar_config &c = h->cfg;
+    const int nx = c.nx, ny = c.ny;
+    const double dx = (c.x1 - c.x0) / nx, dy = (c.y1 - c.y0) / ny;
+    const int P = round_up(nx + 1, 32);
+    const long long S = (long long)(ny + 1) * P;
+    Grid &g = h->g;
+    g.nx = nx; g.ny = ny; g.P = P; g.S = S;
+    g.dx = dx; g.dy = dy; g.dt = c.cfl * std::min(dx, dy); g.nu = 1.0 / c.Re;
+    g.cx = dy / dx; g.cy = dx / dy; g.hxy = dx * dy;
+    g.n_steps = c.n_steps; g.n_window = c.n_window; g.conv_speed = c.conv_speed;
+    h->x0 = c.x0; h->y0 = c.y0;
+
+    auto xc = [&](int i) { return c.x0 + ((double)i + 0.5) * dx; };
+    auto yc = [&](int j) { return c.y0 + ((double)j + 0.5) * dy; };
+    std::vector<uint8_t> F((size_t)S, 0), uk((size_t)S, FK_ZERO), vk((size_t)S, FK_ZERO);
+    long long nfl = 0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double x = xc(i), y = yc(j);
+            bool f = (y > 0.0) || (x > 0.0 && x < 1.0);
+            F[(size_t)j * P + i] = f;
+            nfl += f;
+        }
+    h->nfluid = nfl;
+    auto fl = [&](int i, int j) -> int {
+        if (i < 0 || i >= nx || j < 0 || j >= ny) return 0;
+        return F[(size_t)j * P + i];
+    };
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+            uint8_t k;
+            if (i == 0) k = fl(0, j) ? FK_INLET : FK_ZERO;
+            else if (i == nx) k = fl(nx - 1, j) ? FK_OUTLET : FK_ZERO;
+            else {
+                int a = fl(i - 1, j), b = fl(i, j);
+                k = (a && b) ? FK_UNK : ((a || b) ? FK_ZERO : FK_SOLID);
+            }
+            uk[(size_t)j * P + i] = k;
+        }
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            uint8_t k;
+            if (j == 0 || j == ny) k = FK_ZERO;
+            else {
+                int a = fl(i, j - 1), b = fl(i, j);
+                k = (a && b) ? FK_UNK : ((a || b) ? FK_ZERO : FK_SOLID);
+            }
+            vk[(size_t)j * P + i] = k;
+        }
+    // the mirror rule needs a solid layer at least two faces thick
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i)
+            if (uk[(size_t)j * P + i] == FK_SOLID && j > 0 && j + 1 < ny && uk[(size_t)(j - 1) * P + i] == FK_UNK &&
+                uk[(size_t)(j + 1) * P + i] == FK_UNK) {
+                set_err(h, "geometry: one-cell-thick solid layer is not supported");
+                return ENVAR_EINVAL;
+            }
+    std::vector<double> uin((size_t)ny, 0.0);
+    for (int j = 0; j < ny; ++j)
+        if (uk[(size_t)j * P] == FK_INLET) uin[j] = std::erf(yc(j) / c.inlet_delta);
+
+    uint8_t *dF, *duk, *dvk;
+    double *duin;
+    DA(dF, S); DA(duk, S); DA(dvk, S); DA(duin, ny);
+    CK(cudaMemcpy(dF, F.data(), S, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(duk, uk.data(), S, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dvk, vk.data(), S, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(duin, uin.data(), sizeof(double) * ny, cudaMemcpyHostToDevice));
+    g.fluid = dF; g.uk = duk; g.vk = dvk; g.u_in = duin;
+
+    // ---- multigrid hierarchy
+    struct HostLevel { int nx, ny, P; long long S; std::vector<uint8_t> F; std::vector<double> cw, cs; };
+    std::vector<HostLevel> hl;
+    {
+        HostLevel L0{nx, ny, P, S, F, std::vector<double>((size_t)S, 0.0), std::vector<double>((size_t)S, 0.0)};
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i <= nx; ++i)
+                if (uk[(size_t)j * P + i] == FK_UNK) L0.cw[(size_t)j * P + i] = g.cx;
+        for (int j = 0; j <= ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                if (vk[(size_t)j * P + i] == FK_UNK) L0.cs[(size_t)j * P + i] = g.cy;
+        hl.push_back(std::move(L0));
+    }
+    while ((int)hl.size() < MAX_LEVELS) {
+        const HostLevel &f = hl.back();
+        if (f.nx % 2 || f.ny % 2 || f.nx / 2 < 4 || f.ny / 2 < 2) break;
+        HostLevel cL;
+        cL.nx = f.nx / 2; cL.ny = f.ny / 2; cL.P = round_up(cL.nx + 1, 32); cL.S = (long long)(cL.ny + 1) * cL.P;
+        cL.F.assign((size_t)cL.S, 0); cL.cw.assign((size_t)cL.S, 0.0); cL.cs.assign((size_t)cL.S, 0.0);
+        for (int J = 0; J < cL.ny; ++J)
+            for (int I = 0; I < cL.nx; ++I) {
+                int any = 0;
+                for (int dj = 0; dj < 2; ++dj)
+                    for (int di = 0; di < 2; ++di) any |= f.F[(size_t)(2 * J + dj) * f.P + 2 * I + di];
+                cL.F[(size_t)J * cL.P + I] = (uint8_t)any;
+            }
+        for (int J = 0; J < cL.ny; ++J)
+            for (int I = 0; I <= cL.nx; ++I)
+                cL.cw[(size_t)J * cL.P + I] =
+                    0.5 * (f.cw[(size_t)(2 * J) * f.P + 2 * I] + f.cw[(size_t)(2 * J + 1) * f.P + 2 * I]);
+        for (int J = 0; J <= cL.ny; ++J)
+            for (int I = 0; I < cL.nx; ++I)
+                cL.cs[(size_t)J * cL.P + I] =
+                    0.5 * (f.cs[(size_t)(2 * J) * f.P + 2 * I] + f.cs[(size_t)(2 * J) * f.P + 2 * I + 1]);
+        hl.push_back(std::move(cL));
+    }
+    h->nlev = (int)hl.size();
+    if (h->nlev < 2) {
+        set_err(h, "grid %dx%d too small for the multigrid hierarchy", nx, ny);
+        return ENVAR_EINVAL;
+    }
+    h->ncoarse = h->nlev - 1;
+    for (int l = 1; l < h->nlev; ++l)
+        if (hl[l].nx <= COARSE_MAX_NX && hl[l].ny <= COARSE_MAX_NY) { h->ncoarse = l; break; }
+    for (int l = 0; l < h->nlev; ++l) {
+        const HostLevel &L = hl[l];
+        uint8_t *dfl;
+        float *cwf, *csf;
+        double *cwd, *csd;
+        if (l == 0) dfl = dF; else { DA(dfl, L.S); CK(cudaMemcpy(dfl, L.F.data(), L.S, cudaMemcpyHostToDevice)); }
+        std::vector<float> f1(L.cw.begin(), L.cw.end()), f2(L.cs.begin(), L.cs.end());
+        DA(cwf, L.S); DA(csf, L.S); DA(cwd, L.S); DA(csd, L.S);
+        CK(cudaMemcpy(cwf, f1.data(), sizeof(float) * L.S, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(csf, f2.data(), sizeof(float) * L.S, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(cwd, L.cw.data(), sizeof(double) * L.S, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(csd, L.cs.data(), sizeof(double) * L.S, cudaMemcpyHostToDevice));
+        h->lev[l] = Level{L.nx, L.ny, L.P, L.S, dfl, cwf, csf, cwd, csd};
+    }
+    // coarse block must fit in shared memory
+    size_t coarse_elems = 0;
+    for (int l = h->ncoarse; l < h->nlev; ++l) coarse_elems += 2 * (size_t)hl[l].nx * hl[l].ny;
+    if (coarse_elems * sizeof(double) > 150 * 1024) {
+        set_err(h, "coarse multigrid levels (%zu values) exceed shared memory; use nx, ny with more factors of 2",
+                coarse_elems);
+        return ENVAR_EINVAL;
+    }
+
+    // ---- control rectangle (Sec. 4.1): cells with centre inside the region, inclusive
+    int ia = -1, ib = -1, ja = -1, jb = -1;
+    for (int i = 0; i < nx; ++i) {
+        double x = xc(i);
+        if (x >= c.region[0] && x <= c.region[1]) { if (ia < 0) ia = i; ib = i; }
+    }
+    for (int j = 0; j < ny; ++j) {
+        double y = yc(j);
+        if (y >= c.region[2] && y <= c.region[3]) { if (ja < 0) ja = j; jb = j; }
+    }
+    if (ia < 0 || ja < 0) {
+        set_err(h, "control region contains no cell centre");
+        return ENVAR_EINVAL;
+    }
+    h->ia = ia; h->ja = ja; h->nrx = ib - ia + 1; h->nry = jb - ja + 1; h->nrect = h->nrx * h->nry;
+    g.ia = ia; g.ja = ja; g.nrx = h->nrx; g.nry = h->nry;
+    std::vector<int> cidx;
+    std::vector<uint8_t> rc((size_t)h->nrect, 0);
+    for (int j = ja; j <= jb; ++j)
+        for (int i = ia; i <= ib; ++i)
+            if (F[(size_t)j * P + i]) {
+                int r = (j - ja) * h->nrx + (i - ia);
+                cidx.push_back(r);
+                rc[r] = 1;
+            }
+    h->ncc = (int)cidx.size();
+    h->n_ctrl = 2 * h->ncc;
+    DA(h->d_cidx, std::max(h->ncc, 1));
+    DA(h->d_rect_ctrl, h->nrect);
+    CK(cudaMemcpy(h->d_cidx, cidx.data(), sizeof(int) * h->ncc, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_rect_ctrl, rc.data(), h->nrect, cudaMemcpyHostToDevice));
+    return ENVAR_OK;
+}
+
+// Ensemble draw (Sec. 3.3.2): Z from Philox normals, then sigma (Gx (x) Gy) Z on the control cells.
+static void sampler_axis(double hh, double a, int ncell, int *m, int *pad, int *nxi)
+{
+    int mm = (int)std::ceil(4.0 * hh / a);
+    if (mm < 1) mm = 1;
+    double eta = hh / mm;
+    *m = mm;
+    *pad = (int)std::ceil(5.0 * a / eta);
+    *nxi = (ncell - 1) * mm + 1 + 2 * (*pad);
+}
+
+static int generate_ensemble(envar_handle h)
+{
+    const int N = h->N;
+    if (N == 0) return ENVAR_OK;
+    const double a = h->cfg.corr_len;
+    int mx, px, nxix, my, py, nxiy;
+    sampler_axis(h->g.dx, a, h->nrx, &mx, &px, &nxix);
+    sampler_axis(h->g.dy, a, h->nry, &my, &py, &nxiy);
+    double *Gx, *Gy, *Z, *T;
+    size_t nz = (size_t)N * 2 * nxiy * nxix;
+    if (cudaMalloc(&Gx, sizeof(double) * (size_t)h->nrx * nxix) != cudaSuccess ||
+        cudaMalloc(&Gy, sizeof(double) * (size_t)h->nry * nxiy) != cudaSuccess ||
+        cudaMalloc(&Z, sizeof(double) * nz) != cudaSuccess ||
+        cudaMalloc(&T, sizeof(double) * (size_t)N * 2 * nxiy * h->nrx) != cudaSuccess) {
+        set_err(h, "out of device memory while drawing the ensemble");
+        return ENVAR_ENOMEM;
+    }
+    launch_axis_factor(h->g.dx, a, h->nrx, mx, px, nxix, Gx, h->st);
+    launch_axis_factor(h->g.dy, a, h->nry, my, py, nxiy, Gy, h->st);
+    launch_normals(h->cfg.seed, 0ULL, 0LL, (long long)nz, Z, h->st);
+    launch_conv_sampler(N, h->nrx, h->nry, nxix, nxiy, Gx, Gy, Z, h->d_rect_ctrl, h->cfg.sigma, h->d_Erect, T, h->st);
+    launch_rect_to_compact(N, h->nrect, h->ncc, h->d_cidx, h->d_Erect, h->d_E, h->st);
+    CK(cudaStreamSynchronize(h->st));
+    cudaFree(Gx); cudaFree(Gy); cudaFree(Z); cudaFree(T);
+    CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+static int alloc_buffers(envar_handle h)
+{
+    const int M = h->Mall;
+    const long long S = h->g.S;
+    const size_t n0 = (size_t)S * M;
+    const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
+    DA(h->d_u0, S); DA(h->d_v0, S);
+    DA(h->d_u, n0); DA(h->d_v, n0); DA(h->d_us, n0); DA(h->d_vs, n0); DA(h->d_p, n0);
+    DA(h->pb.x, n0); DA(h->pb.b, n0);
+    h->tend_bytes = tsz * n0;
+    {
+        char *a, *b;
+        DA(a, h->tend_bytes); DA(b, h->tend_bytes);
+        h->d_Ru = a; h->d_Rv = b;
+    }
+    DA(h->d_ubc, (size_t)M * h->g.ny);
+    if (h->cfg.cost_mode == ENVAR_COST_DOMAIN) DA(h->d_wf, 3 * n0);
+    const int nw = std::max(h->cfg.n_window, 1);
+    DA(h->d_series_slot, (size_t)M * nw * 8);
+    h->d_series = h->d_series_slot;
+    if (!h->batched) DA(h->d_series, (size_t)(h->N + 1) * nw * 8);
+    // Poisson (TM)
+    {
+        char *r, *e, *z, *q, *pv;
+        DA(r, tsz * n0); DA(e, tsz * n0); DA(z, tsz * n0); DA(q, tsz * n0); DA(pv, 2 * tsz * n0);
+        h->pb.r = r; h->pb.e = e; h->pb.z = z; h->pb.q = q; h->pb.pv = pv;
+        for (int l = 1; l < h->nlev; ++l) {
+            char *le, *lf;
+            DA(le, tsz * (size_t)h->lev[l].S * M); DA(lf, tsz * (size_t)h->lev[l].S * M);
+            h->pb.lev_e[l] = le; h->pb.lev_f[l] = lf;
+        }
+    }
+    h->pt.nblk = cdiv(h->g.nx, TILE_W) * cdiv(h->g.ny, TILE_H);
+    DA(h->pt.part, (size_t)RS_COUNT * M * h->pt.nblk);
+    DA(h->pt.red, M);
+    CK(cudaMemset(h->pt.red, 0, sizeof(MemberRed) * M));
+    DA(h->d_ctl, M);
+    CK(cudaMemset(h->d_ctl, 0, sizeof(MemberCtl) * M));
+    // ensemble / results
+    const int N = h->N;
+    DA(h->d_Erect, (size_t)std::max(N, 1) * 2 * h->nrect);
+    DA(h->d_E, (size_t)std::max(N, 1) * h->n_ctrl);
+    DA(h->d_frect, (size_t)M * 2 * h->nrect);
+    DA(h->d_Jd_slot, M); DA(h->d_Js_slot, M);
+    DA(h->d_Jd, N + 1); DA(h->d_Js, N + 1);
+    DA(h->d_costpart, (size_t)64 * M);
+    DA(h->d_w, std::max(N, 1)); DA(h->d_g, std::max(N, 1)); DA(h->d_jprior, 1);
+    CK(cudaMemset(h->d_w, 0, sizeof(double) * std::max(N, 1)));
+    return ENVAR_OK;
+}
+
+// ------------------------------------------------------------------------------------ stepping
+static void enqueue_step(envar_handle h, int M)
+{
+    const Grid &g = h->g;
+    cudaStream_t st = h->st;
+    launch_outflow(g, M, h->d_u, h->d_ubc, h->d_ctl, st);
+    if (h->mixed)
+        launch_predict<float>(g, M, h->d_u, h->d_v, h->d_p, (float *)h->d_Ru, (float *)h->d_Rv, h->d_us, h->d_vs,
+                              h->d_ubc, h->d_frect, h->d_ctl, st);
+    else
+        launch_predict<double>(g, M, h->d_u, h->d_v, h->d_p, (double *)h->d_Ru, (double *)h->d_Rv, h->d_us,
+                               h->d_vs, h->d_ubc, h->d_frect, h->d_ctl, st);
+    launch_rhs(g, M, h->d_us, h->d_vs, h->pb.b, h->d_ctl, st);
+    if (h->mixed)
+        launch_pressure_solve<float>(g, h->lev, M, h->pb, h->pc, h->pt, h->d_ctl, st);
+    else
+        launch_pressure_solve<double>(g, h->lev, M, h->pb, h->pc, h->pt, h->d_ctl, st);
+    launch_correct(g, h->x0, h->y0, M, h->d_u, h->d_v, h->d_p, h->d_us, h->d_vs, h->pb.x, h->d_wf,
+                   h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0, h->cfg.n_window > 0 ? h->d_series_slot : nullptr,
+                   h->pt, h->d_ctl, h->cfg.div_tol, h->nfluid, st);
+}
+
+static int capture(envar_handle h, int M, int nsteps, cudaGraphExec_t *out)
+{
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < nsteps; ++s) enqueue_step(h, M);
+    cudaError_t e = cudaStreamEndCapture(h->st, &graph);
+    if (e != cudaSuccess) {
+        set_err(h, "graph capture failed: %s", cudaGetErrorString(e));
+        return ENVAR_ECUDA;
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        set_err(h, "graph instantiate failed: %s", cudaGetErrorString(e));
+        return ENVAR_ECUDA;
+    }
+    return ENVAR_OK;
+}
+
+static int run_steps(envar_handle h, int M, int nsteps)
+{
+    GraphSet &gs = h->graphs[M == h->Mall ? 0 : 1];
+    const int K = h->cfg.steps_per_graph;
+    if (!gs.many) { int rc = capture(h, M, K, &gs.many); if (rc) return rc; }
+    if (!gs.one) { int rc = capture(h, M, 1, &gs.one); if (rc) return rc; }
+    int done = 0;
+    for (; done + K <= nsteps; done += K) CK(cudaGraphLaunch(gs.many, h->st));
+    for (; done < nsteps; ++done) CK(cudaGraphLaunch(gs.one, h->st));
+    return ENVAR_OK;
+}
+
+static void reset_members(envar_handle h, int M)
+{
+    launch_reset(h->g, M, h->d_u0, h->d_v0, h->d_u, h->d_v, h->d_p, h->pb.x, h->d_Ru, h->d_Rv,
+                 h->tend_bytes / h->Mall * M, h->d_wf, h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0, h->d_ctl,
+                 h->st);
+}
+
+// One forward evaluation of all N+1 members (batched) or of member `only` (plain, slot 0).
+static int forward_members(envar_handle h)
+{
+    const int N = h->N;
+    const int nw = std::max(h->cfg.n_window, 1);
+    h->ctl_all.assign(N + 1, MemberCtl{});
+    if (h->batched) {
+        launch_member_forcing(h->Mall, 0, N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->st);
+        reset_members(h, h->Mall);
+        int rc = run_steps(h, h->Mall, h->cfg.n_steps);
+        if (rc) return rc;
+        launch_cost(h->g, h->Mall, h->d_wf, h->cfg.n_window > 0 ? h->d_series_slot : nullptr, h->d_Jd, h->d_Js,
+                    h->d_costpart, h->st);
+        CK(cudaMemcpyAsync(h->ctl_all.data(), h->d_ctl, sizeof(MemberCtl) * (N + 1), cudaMemcpyDeviceToHost, h->st));
+    } else {
+        for (int mm = 0; mm <= N; ++mm) {
+            launch_member_forcing(1, mm, N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->st);
+            reset_members(h, 1);
+            int rc = run_steps(h, 1, h->cfg.n_steps);
+            if (rc) return rc;
+            launch_cost(h->g, 1, h->d_wf, h->cfg.n_window > 0 ? h->d_series_slot : nullptr, h->d_Jd + mm,
+                        h->d_Js + mm, h->d_costpart, h->st);
+            CK(cudaMemcpyAsync(h->d_series + (size_t)mm * nw * 8, h->d_series_slot, sizeof(double) * nw * 8,
+                               cudaMemcpyDeviceToDevice, h->st));
+            CK(cudaMemcpyAsync(&h->ctl_all[mm], h->d_ctl, sizeof(MemberCtl), cudaMemcpyDeviceToHost, h->st));
+        }
+        h->last_member_slot0 = N;
+    }
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    h->have_forward = true;
+    return ENVAR_OK;
+}
+
+// ------------------------------------------------------------------------------------ API
+extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda_stream)
+{
+    if (!out || !cfg) {
+        set_err(nullptr, "envar_init: null argument");
+        return ENVAR_EINVAL;
+    }
+    *out = nullptr;
+    const envar_config &c = *cfg;
+    if (c.nx < 8 || c.ny < 4 || c.nx % 2 || c.ny % 2 || c.n_steps < 1 || c.n_window < 0 || c.n_window > c.n_steps ||
+        c.n_members < 0 || !(c.Re > 0) || !(c.cfl > 0) || !(c.eps > 0) || !(c.sigma >= 0) || !(c.corr_len > 0) ||
+        c.precision < 0 || c.precision > 2 || c.cost_mode < 0 || c.cost_mode > 1 || !(c.div_tol > 0) ||
+        c.max_outer < 1 || c.max_inner < 1 || c.nu_pre < 1 || c.nu_pre > 3 || c.nu_post < 1 || c.nu_post > 3 ||
+        c.coarse_sweeps < 1 || c.steps_per_graph < 1 || !(c.x1 > c.x0) || !(c.y1 > c.y0) || !(c.inner_rtol > 0)) {
+        set_err(nullptr, "envar_init: invalid configuration");
+        return ENVAR_EINVAL;
+    }
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        set_err(nullptr, "envar_init: no CUDA device");
+        return ENVAR_EDEVICE;
+    }
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        set_err(nullptr, "envar_init: device %s is sm_%d%d; this library is built for sm_103a (GB300)", prop.name,
+                prop.major, prop.minor);
+        return ENVAR_EDEVICE;
+    }
+    envar_handle h = new envar_handle_s();
+    h->cfg = c;
+    h->N = c.n_members;
+    h->batched = (c.precision != ENVAR_FP64_PLAIN);
+    h->mixed = (c.precision == ENVAR_MIXED);
+    h->Mall = h->batched ? h->N + 1 : 1;
+    if (cuda_stream) {
+        h->st = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess) {
+            set_err(nullptr, "envar_init: stream creation failed");
+            delete h;
+            return ENVAR_ECUDA;
+        }
+        h->own_stream = true;
+    }
+    int rc = build_geometry(h);
+    if (!rc) rc = alloc_buffers(h);
+    if (!rc) {
+        PoissonCfg &pc = h->pc;
+        pc.nlev = h->nlev; pc.ncoarse = h->ncoarse;
+        pc.nu_pre = c.nu_pre; pc.nu_post = c.nu_post; pc.coarse_sweeps = c.coarse_sweeps;
+        pc.max_outer = c.max_outer; pc.max_inner = c.max_inner;
+        pc.inner_rtol2 = c.inner_rtol * c.inner_rtol;
+        pc.rtol_abs = c.div_tol * h->g.hxy / h->g.dt;
+        if (h->mixed) prepare_poisson_kernels<float>(); else prepare_poisson_kernels<double>();
+        rc = generate_ensemble(h);
+    }
+    if (rc) {
+        std::snprintf(g_init_err, sizeof(g_init_err), "%s", h->err);
+        envar_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_destroy(envar_handle h)
+{
+    if (!h) return ENVAR_OK;
+    if (h->st) cudaStreamSynchronize(h->st);
+    for (auto &gs : h->graphs) {
+        if (gs.many) cudaGraphExecDestroy(gs.many);
+        if (gs.one) cudaGraphExecDestroy(gs.one);
+    }
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->own_stream) cudaStreamDestroy(h->st);
+    delete h;
+    return ENVAR_OK;
+}
+
+extern "C" const char *envar_last_error(envar_handle h) { return h ? h->err : g_init_err; }
+
+extern "C" int envar_sizes(envar_handle h, int *n_ctrl, int *n_cc, int *n_levels, double *dt)
+{
+    if (!h) return ENVAR_EINVAL;
+    if (n_ctrl) *n_ctrl = h->n_ctrl;
+    if (n_cc) *n_cc = h->ncc;
+    if (n_levels) *n_levels = h->nlev;
+    if (dt) *dt = h->g.dt;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_set_initial_state(envar_handle h, const double *u0, const double *v0)
+{
+    if (!h || !u0 || !v0) return ENVAR_EINVAL;
+    CK(cudaMemsetAsync(h->d_u0, 0, sizeof(double) * h->g.S, h->st));
+    CK(cudaMemsetAsync(h->d_v0, 0, sizeof(double) * h->g.S, h->st));
+    launch_load_ic(h->g, u0, v0, h->d_u0, h->d_v0, h->st);
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    h->have_ic = true;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_set_ensemble(envar_handle h, const double *E, int n_ctrl, int N)
+{
+    if (!h || !E) return ENVAR_EINVAL;
+    if (n_ctrl != h->n_ctrl || N != h->N) {
+        set_err(h, "envar_set_ensemble: expected %d x %d, got %d x %d", h->n_ctrl, h->N, n_ctrl, N);
+        return ENVAR_EINVAL;
+    }
+    CK(cudaMemcpyAsync(h->d_E, E, sizeof(double) * (size_t)n_ctrl * N, cudaMemcpyDeviceToDevice, h->st));
+    launch_compact_to_rect(N, h->nrect, h->ncc, h->d_cidx, h->d_E, h->d_Erect, h->st);
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+extern "C" int envar_get_ensemble(envar_handle h, double *E)
+{
+    if (!h || !E) return ENVAR_EINVAL;
+    CK(cudaMemcpyAsync(E, h->d_E, sizeof(double) * (size_t)h->n_ctrl * h->N, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return ENVAR_OK;
+}
+
+extern "C" int envar_forward_ensemble(envar_handle h, const double *w)
+{
+    if (!h) return ENVAR_EINVAL;
+    if (!h->have_ic) { set_err(h, "envar_forward_ensemble: no initial state"); return ENVAR_ESTATE; }
+    if (h->N > 0) {
+        if (!w) return ENVAR_EINVAL;
+        CK(cudaMemcpyAsync(h->d_w, w, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
+    }
+    return forward_members(h);
+}
+
+extern "C" int envar_cost(envar_handle h, double *J, double *Jprior)
+{
+    if (!h) return ENVAR_EINVAL;
+    if (!h->have_forward) { set_err(h, "envar_cost: no forward run"); return ENVAR_ESTATE; }
+    const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js : h->d_Jd;
+    if (J) CK(cudaMemcpyAsync(J, src, sizeof(double) * (h->N + 1), cudaMemcpyDeviceToHost, h->st));
+    if (Jprior) {
+        if (h->N > 0) {
+            launch_scalar_gradient(h->N, src, h->d_w, h->cfg.eps, h->d_g, h->d_jprior, h->st);
+            CK(cudaMemcpyAsync(Jprior, h->d_jprior, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        } else {
+            *Jprior = 0.0;
+        }
+    }
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+static int compute_gradient(envar_handle h)
+{
+    const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js : h->d_Jd;
+    launch_scalar_gradient(h->N, src, h->d_w, h->cfg.eps, h->d_g, h->d_jprior, h->st);
+    if (h->cfg.cost_mode == ENVAR_COST_SENSORS && h->cfg.n_window > 0)
+        launch_sensor_gradient(h->N, h->cfg.n_window, h->d_series, h->cfg.eps, h->d_w, h->d_g, h->st);
+    return ENVAR_OK;
+}
+
+extern "C" int envar_gradient(envar_handle h, double *g, double *df)
+{
+    if (!h) return ENVAR_EINVAL;
+    if (!h->have_forward) { set_err(h, "envar_gradient: no forward run"); return ENVAR_ESTATE; }
+    if (h->N < 1) { set_err(h, "envar_gradient: ensemble is empty"); return ENVAR_ESTATE; }
+    compute_gradient(h);
+    if (df) launch_df(h->N, h->n_ctrl, h->d_E, h->d_g, 1.0 / std::max(h->N - 1, 1), df, h->st);
+    if (g) CK(cudaMemcpyAsync(g, h->d_g, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+extern "C" int envar_step(envar_handle h, double alpha, double *w_inout, double *J0_out)
+{
+    if (!h || !w_inout) return ENVAR_EINVAL;
+    if (!h->have_ic) { set_err(h, "envar_step: no initial state"); return ENVAR_ESTATE; }
+    if (h->N < 1) { set_err(h, "envar_step: ensemble is empty"); return ENVAR_ESTATE; }
+    CK(cudaMemcpyAsync(h->d_w, w_inout, sizeof(double) * h->N, cudaMemcpyHostToDevice, h->st));
+    int rc = forward_members(h);
+    if (rc) return rc;
+    compute_gradient(h);
+    double J0 = 0.0, jp = 0.0;
+    const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js : h->d_Jd;
+    CK(cudaMemcpyAsync(&J0, src, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&jp, h->d_jprior, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    launch_update_w(h->N, h->d_w, h->d_g, alpha / std::max(h->N - 1, 1), h->st);
+    CK(cudaMemcpyAsync(w_inout, h->d_w, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    if (J0_out) *J0_out = J0 + jp;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_forward_control(envar_handle h, const double *f, double *J)
+{
+    if (!h || !f) return ENVAR_EINVAL;
+    if (!h->have_ic) { set_err(h, "envar_forward_control: no initial state"); return ENVAR_ESTATE; }
+    launch_compact_to_rect(1, h->nrect, h->ncc, h->d_cidx, f, h->d_frect, h->st);
+    reset_members(h, 1);
+    int rc = run_steps(h, 1, h->cfg.n_steps);
+    if (rc) return rc;
+    launch_cost(h->g, 1, h->d_wf, h->cfg.n_window > 0 ? h->d_series_slot : nullptr, h->d_Jd_slot, h->d_Js_slot,
+                h->d_costpart, h->st);
+    const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js_slot : h->d_Jd_slot;
+    if (J) CK(cudaMemcpyAsync(J, src, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    h->last_member_slot0 = -2;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_member_status(envar_handle h, int *status)
+{
+    if (!h || !status) return ENVAR_EINVAL;
+    if (!h->have_forward) { set_err(h, "envar_member_status: no forward run"); return ENVAR_ESTATE; }
+    for (int m = 0; m <= h->N; ++m) status[m] = h->ctl_all[m].status;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_get_state(envar_handle h, int member, double *u, double *v, double *p)
+{
+    if (!h) return ENVAR_EINVAL;
+    int slot = member;
+    if (!h->batched) {
+        if (member != h->last_member_slot0 && !(member == 0 && h->last_member_slot0 == -2)) {
+            set_err(h, "envar_get_state: FP64_PLAIN keeps only the last member run (%d)", h->last_member_slot0);
+            return ENVAR_ESTATE;
+        }
+        slot = 0;
+    }
+    if (slot < 0 || slot >= h->Mall) return ENVAR_EINVAL;
+    const long long off = (long long)slot * h->g.S;
+    launch_export_state(h->g, h->d_u + off, h->d_v + off, h->d_p + off, u, v, p, h->st);
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+extern "C" int envar_get_series(envar_handle h, int member, double *series)
+{
+    if (!h || !series || member < 0 || member > h->N) return ENVAR_EINVAL;
+    const int nw = h->cfg.n_window;
+    CK(cudaMemcpy(series, h->d_series + (size_t)member * std::max(nw, 1) * 8, sizeof(double) * nw * 8,
+                  cudaMemcpyDeviceToHost));
+    return ENVAR_OK;
+}
+
+extern "C" int envar_diagnostics(envar_handle h, double *max_div, long long *outer_its, long long *inner_its)
+{
+    if (!h) return ENVAR_EINVAL;
+    double md = 0.0;
+    long long oi = 0, ii = 0;
+    for (const MemberCtl &c : h->ctl_all) {
+        md = std::max(md, c.max_div);
+        oi += c.outer_its;
+        ii += c.inner_its;
+    }
+    if (max_div) *max_div = md;
+    if (outer_its) *outer_its = oi;
+    if (inner_its) *inner_its = ii;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_reset_members(envar_handle h, const double *w)
+{
+    if (!h) return ENVAR_EINVAL;
+    if (!h->have_ic) { set_err(h, "envar_reset_members: no initial state"); return ENVAR_ESTATE; }
+    if (h->N > 0 && w) CK(cudaMemcpyAsync(h->d_w, w, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
+    launch_member_forcing(h->Mall, 0, h->N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->st);
+    reset_members(h, h->Mall);
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    h->last_member_slot0 = 0;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_advance(envar_handle h, int n)
+{
+    if (!h || n < 0) return ENVAR_EINVAL;
+    int rc = run_steps(h, h->Mall, n);
+    if (rc) return rc;
+    h->ctl_all.assign(h->N + 1, MemberCtl{});
+    CK(cudaMemcpyAsync(h->ctl_all.data(), h->d_ctl, sizeof(MemberCtl) * h->Mall, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return ENVAR_OK;
+}

@@ -1,0 +1,193 @@
+// envar_internal.cuh -- device-side data structures and helpers of the GB300 EnVar library.
+//
+// Memory layout (all per-member arrays, all levels):
+//   a field of a level with nx x ny cells is stored row-major with a pitch P
+//   (P = nx + 1 rounded up to 32 elements) and (ny + 1) rows, so that cell
+//   arrays, u-face arrays ((nx+1) x ny) and v-face arrays (nx x (ny+1)) share
+//   one index  idx = j * P + i  and one member stride S = (ny + 1) * P.
+//   Member m of an array starts at base + m * S.  Members are contiguous, so a
+//   launch over all members is one contiguous sweep of HBM.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace envar {
+
+enum FaceKind : uint8_t { FK_ZERO = 0, FK_UNK = 1, FK_INLET = 2, FK_OUTLET = 3, FK_SOLID = 4 };
+
+constexpr int MAX_LEVELS = 12;
+// Level-0 tile of the Poisson / stencil kernels: 64 x 16 cells per 256-thread block.
+constexpr int TILE_W = 64;
+constexpr int TILE_H = 16;
+constexpr int TILE_THREADS = 256;
+// The coarsest levels (nx <= 64 and ny <= 32) are solved by one block per member.
+constexpr int COARSE_MAX_NX = 64;
+constexpr int COARSE_MAX_NY = 32;
+
+struct Level {
+    int nx, ny, P;          // cells, pitch
+    long long S;            // member stride (elements)
+    const uint8_t *fluid;   // [ny][P]
+    const float *cwf;       // west-face conductance (i in 0..nx), [ny][P]
+    const float *csf;       // south-face conductance (j in 0..ny), [ny+1][P]
+    const double *cwd;
+    const double *csd;
+};
+
+struct Grid {
+    int nx, ny, P;
+    long long S;
+    double dx, dy, dt, nu;
+    double cx, cy;          // finite-volume conductances dy/dx and dx/dy
+    double hxy;             // dx * dy
+    const uint8_t *fluid;   // [ny][P]
+    const uint8_t *uk;      // u-face kinds [ny][P]
+    const uint8_t *vk;      // v-face kinds [ny+1][P]
+    const double *u_in;     // inlet profile per row
+    int ia, ja, nrx, nry;   // control rectangle (cells)
+    int n_steps, n_window;
+    double conv_speed;
+};
+
+// Per-member control block in device memory.
+struct MemberCtl {
+    int step;               // completed time steps of the current forward run
+    int status;             // ENVAR_ST_* bits
+    int outer_done;         // pressure solve converged for the current step
+    int inner_done;         // inner CG converged for the current refinement
+    double max_div;         // max |D u| seen over the run
+    long long outer_its;    // refinements performed (summed over steps)
+    long long inner_its;    // inner CG iterations performed
+};
+
+// Per-member scalars of the pressure solve, reduced deterministically: every level-0 tile writes
+// a partial and the last tile to arrive sums them in a fixed order into val[slot].
+enum RedSlot { RS_RMAX = 0, RS_XSUM = 1, RS_RZ0 = 2, RS_RZA = 3, RS_RZB = 4, RS_PQ = 5, RS_COUNT = 6 };
+struct MemberRed {
+    unsigned int cnt[RS_COUNT];   // arrival tickets
+    double val[RS_COUNT];         // max |r| (outer residual), sum x, r^T z (start, ping, pong), p^T A p
+};
+struct Partials {
+    int nblk;               // level-0 tiles per member
+    double *part;           // [RS_COUNT][M][nblk]
+    MemberRed *red;         // [M]
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum / max (blockDim.x * blockDim.y threads, multiple of 32, <= 1024).
+// Result valid in every thread.  Uses 33 doubles of shared memory.
+__device__ __forceinline__ double block_reduce(double v, bool is_max)
+{
+    __shared__ double red[33];
+    int t = threadIdx.x + threadIdx.y * blockDim.x;
+    int nt = blockDim.x * blockDim.y;
+    v = is_max ? warp_max(v) : warp_sum(v);
+    __syncthreads();
+    if ((t & 31) == 0) red[t >> 5] = v;
+    __syncthreads();
+    if (t < 32) {
+        double w = (t < (nt >> 5)) ? red[t] : (is_max ? -1.0 : 0.0);
+        w = is_max ? warp_max(w) : warp_sum(w);
+        if (t == 0) red[32] = w;
+    }
+    __syncthreads();
+    double r = red[32];
+    __syncthreads();
+    return r;
+}
+
+// Sum (or max) of a member's partials in a fixed order -- every block that calls
+// this gets the bit-identical result.  Called by whole warps; result in all lanes.
+__device__ __forceinline__ double warp_partials(const double *p, int n, bool is_max)
+{
+    int lane = threadIdx.x & 31;
+    double v = is_max ? 0.0 : 0.0;
+    for (int k = lane; k < n; k += 32) v = is_max ? fmax(v, p[k]) : v + p[k];
+    return is_max ? warp_max(v) : warp_sum(v);
+}
+
+template <class T> __device__ __forceinline__ const T *cw_of(const Level &L);
+template <> __device__ __forceinline__ const float *cw_of<float>(const Level &L) { return L.cwf; }
+template <> __device__ __forceinline__ const double *cw_of<double>(const Level &L) { return L.cwd; }
+template <class T> __device__ __forceinline__ const T *cs_of(const Level &L);
+template <> __device__ __forceinline__ const float *cs_of<float>(const Level &L) { return L.csf; }
+template <> __device__ __forceinline__ const double *cs_of<double>(const Level &L) { return L.csd; }
+
+static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+static inline int round_up(int a, int b) { return cdiv(a, b) * b; }
+
+// ------------------------------------------------------------- launchers
+// Flow kernels (k_flow.cu).  TR = tendency precision (float in mixed mode).
+template <class TR>
+void launch_predict(const Grid &g, int M, const double *u, const double *v, const double *p,
+                    TR *Ru, TR *Rv, double *us, double *vs, const double *ubc, const double *frect,
+                    const MemberCtl *ctl, cudaStream_t st);
+void launch_reset(const Grid &g, int M, const double *u0, const double *v0, double *u, double *v, double *p,
+                  double *x, void *Ru, void *Rv, size_t tend_bytes, double *wf, int want_welford,
+                  MemberCtl *ctl, cudaStream_t st);
+void launch_outflow(const Grid &g, int M, const double *u, double *ubc, MemberCtl *ctl, cudaStream_t st);
+void launch_rhs(const Grid &g, int M, const double *us, const double *vs, double *b, MemberCtl *ctl,
+                cudaStream_t st);
+void launch_correct(const Grid &g, double x0, double y0, int M, double *u, double *v, double *p,
+                    const double *us, const double *vs, const double *x, double *wf, int want_welford,
+                    double *series, const Partials &pt, MemberCtl *ctl, double div_tol, long long nfluid,
+                    cudaStream_t st);
+void launch_load_ic(const Grid &g, const double *u0, const double *v0, double *u, double *v, cudaStream_t st);
+void launch_cost(const Grid &g, int M, const double *wf, const double *series, double *J_domain,
+                 double *J_sensor, double *part, cudaStream_t st);
+void launch_export_state(const Grid &g, const double *u, const double *v, const double *p, double *uo,
+                         double *vo, double *po, cudaStream_t st);
+
+// Poisson kernels (k_poisson.cu).  TM = multigrid / inner-CG precision.
+struct PoissonBufs {
+    double *b, *x;                  // level-0 FP64 right-hand side and solution
+    void *r, *e, *z, *pv, *q;       // level-0 inner vectors (TM)
+    void *lev_e[MAX_LEVELS];        // level >= 1 correction (TM)
+    void *lev_f[MAX_LEVELS];        // level >= 1 right-hand side (TM)
+};
+struct PoissonCfg {
+    int nlev;                       // number of levels
+    int ncoarse;                    // first level handled by the per-member coarse kernel
+    int nu_pre, nu_post, coarse_sweeps;
+    int max_outer, max_inner;
+    double inner_rtol2;             // inner_rtol^2
+    double rtol_abs;                // outer stop: max |r| <= rtol_abs (r = b - A x, FV form)
+};
+template <class TM> void prepare_poisson_kernels();
+template <class TM>
+void launch_pressure_solve(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc,
+                           const Partials &pt, MemberCtl *ctl, cudaStream_t st);
+
+// Ensemble kernels (k_ensemble.cu)
+void launch_normals(unsigned long long seed, unsigned long long stream, long long first, long long n, double *out,
+                    cudaStream_t st);
+void launch_conv_sampler(int N, int nrx, int nry, int nxix, int nxiy, const double *Gx, const double *Gy,
+                         const double *Z, const uint8_t *rect_ctrl, double sigma, double *Erect, double *tmp,
+                         cudaStream_t st);
+void launch_member_forcing(int M, int first_member, int N, int nrect, const double *Erect, const double *w,
+                           double eps, double *frect, cudaStream_t st);
+void launch_rect_to_compact(int N, int nrect, int ncc, const int *cidx, const double *Erect, double *E,
+                            cudaStream_t st);
+void launch_compact_to_rect(int N, int nrect, int ncc, const int *cidx, const double *E, double *Erect,
+                            cudaStream_t st);
+void launch_sensor_gradient(int N, int n_window, const double *series, double eps, const double *w, double *g,
+                            cudaStream_t st);
+void launch_scalar_gradient(int N, const double *J, const double *w, double eps, double *g, double *jprior,
+                            cudaStream_t st);
+void launch_df(int N, int n_ctrl, const double *E, const double *g, double scale, double *df, cudaStream_t st);
+void launch_update_w(int N, double *w, const double *g, double step, cudaStream_t st);
+
+} // namespace envar

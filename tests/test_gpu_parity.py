@@ -1,0 +1,178 @@
+"""GPU parity: the sm_103a path through the C ABI against the FP64 CPU oracle on the
+same seeded inputs.
+
+Tolerances (stated by the target of this build): FP64 path relative L2 <= 1e-10 on
+velocity after 100 steps; mixed-precision path <= 1e-4.  Costs and gradients of the
+FP64 path are compared to the oracle's at the precision the two solvers converge to.
+"""
+import concurrent.futures as cf
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2605_23812_gb300 as pkg
+from paper_2605_23812_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def tight(nx, ny, **kw):
+    base = dict(div_tol=1e-13, max_outer=4, max_inner=40, inner_rtol=1e-12, precision=pkg.FP64_BATCHED)
+    base.update(kw)
+    return pkg.default_config(nx, ny, **base)
+
+
+def member_forcings(E, w, eps):
+    f0 = E @ w
+    return [f0] + [f0 + eps * E[:, i] for i in range(E.shape[1])]
+
+
+def rel_l2(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b**2).sum()))
+
+
+def vel_rel(gu, gv, ou, ov):
+    num = ((gu - ou) ** 2).sum() + ((gv - ov) ** 2).sum()
+    den = (ou**2).sum() + (ov**2).sum()
+    return float(np.sqrt(num / den))
+
+
+def oracle_trajectories(P, u0, v0, forcings, n_steps, workers=8):
+    def one(f):
+        fu, fv = oracle.control_to_faces(P, f)
+        return oracle.trajectory(P, u0, v0, n_steps, fu, fv)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(one, forcings))
+
+
+@pytest.mark.parametrize("precision", [pkg.FP64_BATCHED, pkg.FP64_PLAIN, pkg.MIXED])
+def test_trajectory_parity_100_steps(precision):
+    nx, ny, N, steps = 64, 32, 2, 100
+    P = oracle.cavity_params(nx, ny, 1000.0)
+    cfg = tight(nx, ny, Re=1000.0, n_steps=steps, n_window=10, n_members=N, precision=precision)
+    if precision == pkg.MIXED:
+        cfg.div_tol, cfg.inner_rtol, cfg.max_inner = 1e-12, 1e-5, 12
+    E = oracle.ensemble_seeded(P, cfg.sigma, cfg.corr_len, N, cfg.seed)
+    w = synth.weights(N)
+    u0, v0 = synth.cavity_ic(nx, ny)
+    ens = pkg.Ensemble(cfg)
+    ens.set_initial_state(u0, v0)
+    ens.set_ensemble(E)
+    ens.forward_ensemble(w)
+    ref = oracle_trajectories(P, u0, v0, member_forcings(E, w, cfg.eps), steps)
+    F = oracle.fluid_mask(P).astype(bool)
+    tol = 1e-4 if precision == pkg.MIXED else 1e-10
+    members = [N] if precision == pkg.FP64_PLAIN else range(N + 1)
+    for m in members:
+        u, v, p = (t.cpu().numpy() for t in ens.get_state(m))
+        ou, ov, op, _, _ = ref[m]
+        err = vel_rel(u, v, ou, ov)
+        assert err <= tol, (precision, m, err)
+        pm, opm = p[F] - p[F].mean(), op[F] - op[F].mean()
+        assert rel_l2(pm, opm) <= (1e-3 if precision == pkg.MIXED else 1e-8)
+    d = ens.diagnostics()
+    assert d["max_div"] <= cfg.div_tol
+    assert (ens.member_status() == 0).all()
+    ens.close()
+
+
+@pytest.mark.parametrize("mode", [pkg.COST_DOMAIN, pkg.COST_SENSORS])
+def test_envar_costs_and_gradient_parity(mode):
+    nx, ny, N = 32, 16, 3
+    P = oracle.cavity_params(nx, ny, 300.0)
+    cfg = tight(nx, ny, Re=300.0, n_steps=120, n_window=60, n_members=N, cost_mode=mode)
+    E = oracle.ensemble_seeded(P, cfg.sigma, cfg.corr_len, N, cfg.seed)
+    w = synth.weights(N)
+    u0, v0 = synth.cavity_ic(nx, ny)
+    ens = pkg.Ensemble(cfg)
+    ens.set_initial_state(u0, v0)
+    ens.set_ensemble(E)
+    ens.forward_ensemble(w)
+    J, jp = ens.cost()
+    g = ens.gradient()
+    ref = oracle.envar_gradient(P, u0, v0, E, w, cfg.eps, cfg.n_steps, cfg.n_window, cost_mode=mode,
+                                nthreads=4, want_series=True)
+    np.testing.assert_allclose(J, ref["J"], rtol=1e-9)
+    assert jp == pytest.approx(ref["J_prior"], rel=1e-14)
+    gref = ref["g"] if mode == pkg.COST_DOMAIN else oracle.sensor_gradient(ref["series"], w, cfg.eps)
+    assert np.abs(g - gref).max() <= 1e-6 * np.abs(gref).max(), (g, gref)
+    for m in range(N + 1):
+        np.testing.assert_allclose(ens.get_series(m), ref["series"][m], rtol=0, atol=1e-10)
+    # df = E g / (N - 1)
+    _, df = ens.gradient(want_df=True)
+    np.testing.assert_allclose(df.cpu().numpy(), E @ g / (N - 1), rtol=1e-12, atol=1e-15)
+    ens.close()
+
+
+def test_plain_and_batched_agree():
+    nx, ny, N = 32, 16, 3
+    outs = []
+    for prec in (pkg.FP64_PLAIN, pkg.FP64_BATCHED):
+        cfg = tight(nx, ny, Re=300.0, n_steps=60, n_window=30, n_members=N, precision=prec)
+        ens = pkg.Ensemble(cfg)
+        ens.set_initial_state(*synth.cavity_ic(nx, ny))
+        ens.forward_ensemble(synth.weights(N))
+        outs.append((ens.cost()[0], ens.gradient()))
+        ens.close()
+    np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=1e-13)
+    np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("nx,ny,N", [(32, 16, 3), (128, 64, 8), (512, 256, 32)])
+def test_ensemble_draw_matches_oracle(nx, ny, N):
+    cfg = pkg.default_config(nx, ny, n_members=N, n_steps=2, n_window=1)
+    ens = pkg.Ensemble(cfg)
+    Eg = ens.get_ensemble().cpu().numpy()
+    P = oracle.cavity_params(nx, ny, cfg.Re)
+    Eo = oracle.ensemble_seeded(P, cfg.sigma, cfg.corr_len, N, cfg.seed)
+    assert Eg.shape == Eo.shape
+    assert np.abs(Eg - Eo).max() <= 1e-12 * np.abs(Eo).max()
+    ens.close()
+
+
+def test_step_applies_prior_preconditioned_update():
+    nx, ny, N = 32, 16, 4
+    cfg = tight(nx, ny, Re=300.0, n_steps=40, n_window=20, n_members=N)
+    ens = pkg.Ensemble(cfg)
+    ens.set_initial_state(*synth.cavity_ic(nx, ny))
+    w = synth.weights(N)
+    ens.forward_ensemble(w)
+    J, jp = ens.cost()
+    g = ens.gradient()
+    w1, J0 = ens.step(0.5, w)
+    assert J0 == pytest.approx(J[0] + jp, rel=1e-13)
+    np.testing.assert_allclose(w1, w - 0.5 * g / (N - 1), rtol=1e-13, atol=1e-16)
+    ens.close()
+
+
+def test_bench_configuration_sampled_parity():
+    """The bench's launch configuration (512x256, Re 7500, N = 32, mixed precision, all 33
+    members in one launch) over 10 steps: sampled members against the oracle."""
+    nx, ny, N, steps = 512, 256, 32, 10
+    cfg = pkg.default_config(nx, ny, Re=7500.0, n_steps=steps, n_window=5, n_members=N, precision=pkg.MIXED,
+                             div_tol=1e-10)
+    P = oracle.cavity_params(nx, ny, 7500.0)
+    u0, v0 = synth.cavity_ic(nx, ny)
+    w = synth.weights(N)
+    ens = pkg.Ensemble(cfg)
+    ens.set_initial_state(u0, v0)
+    E = ens.get_ensemble().cpu().numpy()
+    Eo = oracle.ensemble_seeded(P, cfg.sigma, cfg.corr_len, N, cfg.seed)
+    assert np.abs(E - Eo).max() <= 1e-12 * np.abs(Eo).max()
+    ens.forward_ensemble(w)
+    fs = member_forcings(Eo, w, cfg.eps)
+    sample = [0, N]
+    ref = oracle_trajectories(P, u0, v0, [fs[m] for m in sample], steps, workers=2)
+    for m, r in zip(sample, ref):
+        u, v, _ = (t.cpu().numpy() for t in ens.get_state(m))
+        assert vel_rel(u, v, r[0], r[1]) <= 1e-4
+    assert ens.diagnostics()["max_div"] <= 1e-10
+    assert (ens.member_status() == 0).all()
+    ens.close()

@@ -474,6 +474,14 @@ def test_envar_gradient_matches_central_differences():
         # and its members are the N+1 forcings of Eq. (fdapprox)
         for i in range(N):
             assert out["J"][i + 1] == pytest.approx(Jobs(f0 + eps * E[:, i]), rel=1e-12)
+        if mode == oracle.COST_SENSORS:
+            # the explicit Y^T (Hq_0 - y) of Eq. (gradient_EnVar) on the sensor series
+            ser = oracle.envar_gradient(P, u0, v0, E, w, eps, n_steps, n_window, cost_mode=mode, nthreads=4,
+                                        want_series=True)["series"]
+            gy = oracle.sensor_gradient(ser, w, eps) - (N - 1) * w
+            assert np.abs(gy - gc).max() <= 0.05 * np.abs(gc).max() + 1e-12, (gy, gc)
+            # forward differences of 1/2||h||^2 exceed Y^T h_0 by exactly eps/2 ||Y_i||^2 >= 0
+            assert np.all(gobs - gy >= -1e-12 * np.abs(gy).max())
 
 
 # --------------------------------------------------------------------------
