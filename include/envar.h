@@ -179,6 +179,19 @@ int envar_diagnostics(envar_handle h, double *max_div, long long *outer_its, lon
 int envar_reset_members(envar_handle h, const double *w_dev);
 int envar_advance(envar_handle h, int n_steps);
 
+/* Kernels launched by this library in this process so far: direct launches plus the
+ * kernel nodes of every CUDA-graph replay (h is unused and may be NULL). */
+int envar_kernel_launches(envar_handle h, long long *count);
+
+/* Time one hot-path kernel over all member slots: two untimed launches, then `reps`
+ * back-to-back launches on the handle's stream between CUDA events; *ms_per_launch
+ * receives the mean.  which: 0 momentum predictor, 1 level-0 pre-smoothing + restriction,
+ * 2 level-0 prolongation + post-smoothing + dot product, 3 inner SpMV, 4 inner AXPY,
+ * 5 outer FP64 residual, 6 projection correction with the Welford update, 7 coarse-level
+ * block kernel, 8 Poisson right-hand side.  Overwrites the members' state: call
+ * envar_reset_members or a forward run before using the state again. */
+int envar_time_kernel(envar_handle h, int which, int reps, double *ms_per_launch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,8 @@ def lib():
                               ctypes.POINTER(ctypes.c_longlong)],
         "envar_reset_members": [H, c_void_p],
         "envar_advance": [H, c_int],
+        "envar_kernel_launches": [H, ctypes.POINTER(ctypes.c_longlong)],
+        "envar_time_kernel": [H, c_int, c_int, ctypes.POINTER(c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -235,3 +237,18 @@ class Ensemble:
 
     def advance(self, n):
         self._check(lib().envar_advance(self._h, int(n)), "envar_advance")
+
+    def time_kernel(self, which: int, reps: int = 20) -> float:
+        ms = c_double()
+        self._check(lib().envar_time_kernel(self._h, int(which), int(reps), ctypes.byref(ms)), "envar_time_kernel")
+        return ms.value
+
+
+def kernel_launches() -> int:
+    n = ctypes.c_longlong()
+    lib().envar_kernel_launches(None, ctypes.byref(n))
+    return n.value
+
+
+KERNELS = {0: "predict", 1: "mg_presmooth_restrict_l0", 2: "mg_prolong_postsmooth_dot_l0", 3: "cg_spmv",
+           4: "cg_axpy", 5: "outer_residual_fp64", 6: "correct_welford", 7: "mg_coarse_block", 8: "poisson_rhs"}

@@ -6,6 +6,7 @@
 // iteration -- ensemble draws, forcings, the N+1 forward runs, costs, gradient and update -- runs
 // in the library's CUDA kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -24,7 +25,9 @@ using namespace envar;
 struct GraphSet {
     cudaGraphExec_t many = nullptr;   // steps_per_graph steps
     cudaGraphExec_t one = nullptr;    // one step
+    long long kernels_many = 0, kernels_one = 0;   // kernel nodes per replay
 };
+static std::atomic<long long> g_graph_kernels{0};
 
 struct envar_handle_s {
     envar_config cfg{};
@@ -406,16 +409,28 @@ static void enqueue_step(envar_handle h, int M)
                    h->pt, h->d_ctl, h->cfg.div_tol, h->nfluid, st);
 }
 
-static int capture(envar_handle h, int M, int nsteps, cudaGraphExec_t *out)
+static int capture(envar_handle h, int M, int nsteps, cudaGraphExec_t *out, long long *kernels)
 {
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    set_capturing(true);
     for (int s = 0; s < nsteps; ++s) enqueue_step(h, M);
+    set_capturing(false);
     cudaError_t e = cudaStreamEndCapture(h->st, &graph);
     if (e != cudaSuccess) {
         set_err(h, "graph capture failed: %s", cudaGetErrorString(e));
         return ENVAR_ECUDA;
     }
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+    long long nk = 0;
+    for (size_t k = 0; k < nn; ++k) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+    *kernels = nk;
     e = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
@@ -429,11 +444,17 @@ static int run_steps(envar_handle h, int M, int nsteps)
 {
     GraphSet &gs = h->graphs[M == h->Mall ? 0 : 1];
     const int K = h->cfg.steps_per_graph;
-    if (!gs.many) { int rc = capture(h, M, K, &gs.many); if (rc) return rc; }
-    if (!gs.one) { int rc = capture(h, M, 1, &gs.one); if (rc) return rc; }
+    if (!gs.many) { int rc = capture(h, M, K, &gs.many, &gs.kernels_many); if (rc) return rc; }
+    if (!gs.one) { int rc = capture(h, M, 1, &gs.one, &gs.kernels_one); if (rc) return rc; }
     int done = 0;
-    for (; done + K <= nsteps; done += K) CK(cudaGraphLaunch(gs.many, h->st));
-    for (; done < nsteps; ++done) CK(cudaGraphLaunch(gs.one, h->st));
+    for (; done + K <= nsteps; done += K) {
+        CK(cudaGraphLaunch(gs.many, h->st));
+        g_graph_kernels += gs.kernels_many;
+    }
+    for (; done < nsteps; ++done) {
+        CK(cudaGraphLaunch(gs.one, h->st));
+        g_graph_kernels += gs.kernels_one;
+    }
     return ENVAR_OK;
 }
 
@@ -768,5 +789,65 @@ extern "C" int envar_advance(envar_handle h, int n)
     CK(cudaMemcpyAsync(h->ctl_all.data(), h->d_ctl, sizeof(MemberCtl) * h->Mall, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+extern "C" int envar_kernel_launches(envar_handle h, long long *count)
+{
+    (void)h;
+    if (!count) return ENVAR_EINVAL;
+    *count = launches_so_far() + g_graph_kernels.load();
+    return ENVAR_OK;
+}
+
+extern "C" int envar_time_kernel(envar_handle h, int which, int reps, double *ms)
+{
+    if (!h || !ms || reps < 1 || which < 0 || which > 8) return ENVAR_EINVAL;
+    if (!h->have_ic) { set_err(h, "envar_time_kernel: no initial state"); return ENVAR_ESTATE; }
+    const int M = h->Mall;
+    std::vector<MemberCtl> c((size_t)M);
+    for (auto &x : c) { x = MemberCtl{}; x.step = h->cfg.n_steps; }
+    CK(cudaMemcpyAsync(h->d_ctl, c.data(), sizeof(MemberCtl) * M, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const int wf = h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0;
+    double *ser = h->cfg.n_window > 0 ? h->d_series_slot : nullptr;
+    auto launch = [&]() -> int {
+        const Grid &g = h->g;
+        switch (which) {
+        case 0:
+            if (h->mixed)
+                launch_predict<float>(g, M, h->d_u, h->d_v, h->d_p, (float *)h->d_Ru, (float *)h->d_Rv, h->d_us,
+                                      h->d_vs, h->d_ubc, h->d_frect, h->d_ctl, h->st);
+            else
+                launch_predict<double>(g, M, h->d_u, h->d_v, h->d_p, (double *)h->d_Ru, (double *)h->d_Rv, h->d_us,
+                                       h->d_vs, h->d_ubc, h->d_frect, h->d_ctl, h->st);
+            return 0;
+        case 6:
+            launch_correct(g, h->x0, h->y0, M, h->d_u, h->d_v, h->d_p, h->d_us, h->d_vs, h->pb.x, h->d_wf, wf, ser,
+                           h->pt, h->d_ctl, h->cfg.div_tol, h->nfluid, h->st);
+            return 0;
+        case 8:
+            launch_rhs(g, M, h->d_us, h->d_vs, h->pb.b, h->d_ctl, h->st);
+            return 0;
+        default:
+            return h->mixed ? launch_poisson_single<float>(which, g, h->lev, M, h->pb, h->pc, h->pt, h->d_ctl, h->st)
+                            : launch_poisson_single<double>(which, g, h->lev, M, h->pb, h->pc, h->pt, h->d_ctl, h->st);
+        }
+    };
+    if (launch() != 0) return ENVAR_EINVAL;
+    launch();
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, h->st));
+    for (int r = 0; r < reps; ++r) launch();
+    CK(cudaEventRecord(e1, h->st));
+    CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    *ms = (double)t / reps;
     return ENVAR_OK;
 }

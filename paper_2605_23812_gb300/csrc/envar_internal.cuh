@@ -129,6 +129,13 @@ template <> __device__ __forceinline__ const double *cs_of<double>(const Level &
 static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 static inline int round_up(int a, int b) { return cdiv(a, b) * b; }
 
+// ------------------------------------------------------------- launch accounting
+// Kernels launched directly on a stream (graph capture excluded; graph replays are counted by
+// the C ABI from the captured graphs' kernel nodes).
+void count_launches(long long n);
+long long launches_so_far();
+void set_capturing(bool on);
+
 // ------------------------------------------------------------- launchers
 // Flow kernels (k_flow.cu).  TR = tendency precision (float in mixed mode).
 template <class TR>
@@ -167,6 +174,12 @@ struct PoissonCfg {
     double rtol_abs;                // outer stop: max |r| <= rtol_abs (r = b - A x, FV form)
 };
 template <class TM> void prepare_poisson_kernels();
+// Launch ONE kernel of the pressure solve (for standalone timing):
+//   1 level-0 pre-smoothing + restriction, 2 level-0 prolongation + post-smoothing + dot,
+//   3 inner SpMV, 4 inner AXPY, 5 outer FP64 residual, 7 coarse-level block kernel.
+template <class TM>
+int launch_poisson_single(int which, const Grid &g, const Level *lev, int M, const PoissonBufs &B,
+                          const PoissonCfg &pc, const Partials &pt, MemberCtl *ctl, cudaStream_t st);
 template <class TM>
 void launch_pressure_solve(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc,
                            const Partials &pt, MemberCtl *ctl, cudaStream_t st);

@@ -52,6 +52,7 @@ void launch_normals(unsigned long long seed, unsigned long long stream, long lon
     if (n <= 0) return;
     long long nb = (n + 255) / 256;
     k_normals<<<(unsigned)(nb < 65535 ? nb : 65535), 256, 0, st>>>(seed, stream, first, n, out);
+    count_launches(1);
 }
 
 // 1-D factor G[r][k] = c exp(-2 (x_r - xi_k)^2 / a^2) on the lattice xi_k = x_first + (k - pad) eta.
@@ -70,6 +71,7 @@ void launch_axis_factor(double h, double a, int ncell, int m, int pad, int nxi, 
 {
     int n = ncell * nxi;
     k_axis_factor<<<(n + 255) / 256, 256, 0, st>>>(h, a, ncell, m, pad, nxi, G);
+    count_launches(1);
 }
 
 // T[k][c][ky][ix] = sum_kx Gx[ix][kx] Z[k][c][ky][kx]
@@ -118,6 +120,7 @@ void launch_conv_sampler(int N, int nrx, int nry, int nxix, int nxiy, const doub
                                                                                                    Gx, Z, tmp);
     k_contract_y<<<(unsigned)((n2 + 255) / 256 < 65535 ? (n2 + 255) / 256 : 65535), 256, 0, st>>>(
         NC, nrx, nry, nxiy, Gy, tmp, rect_ctrl, sigma, Erect);
+    count_launches(2);
 }
 
 // f[m][c][rect] = sum_k E[k][c][rect] w_k + (member > 0 ? eps E[member-1][c][rect] : 0)
@@ -141,6 +144,7 @@ void launch_member_forcing(int M, int first_member, int N, int nrect, const doub
 {
     long long n = (long long)M * 2 * nrect;
     k_member_forcing<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M, first_member, N, nrect, Erect, w, eps, frect);
+    count_launches(1);
 }
 
 __global__ void k_scatter(int N, int nrect, int ncc, const int *__restrict__ cidx, const double *__restrict__ E,
@@ -169,11 +173,13 @@ void launch_compact_to_rect(int N, int nrect, int ncc, const int *cidx, const do
     cudaMemsetAsync(Erect, 0, sizeof(double) * (size_t)N * 2 * nrect, st);
     long long n = (long long)N * 2 * ncc;
     if (n > 0) k_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(N, nrect, ncc, cidx, E, Erect);
+    count_launches(1);
 }
 void launch_rect_to_compact(int N, int nrect, int ncc, const int *cidx, const double *Erect, double *E, cudaStream_t st)
 {
     long long n = (long long)N * 2 * ncc;
     if (n > 0) k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(N, nrect, ncc, cidx, Erect, E);
+    count_launches(1);
 }
 
 // ---------------------------------------------------------------- gradients (K9)
@@ -194,6 +200,7 @@ void launch_scalar_gradient(int N, const double *J, const double *w, double eps,
                             cudaStream_t st)
 {
     k_scalar_gradient<<<1, 256, 0, st>>>(N, J, w, eps, g, jprior);
+    count_launches(1);
 }
 
 // Sensor form: h_m(t,s) = series_m(t,s) - mean_t series_m(., s);  Y_i = (h_i - h_0)/eps;
@@ -227,6 +234,7 @@ void launch_sensor_gradient(int N, int n_window, const double *series, double ep
                             cudaStream_t st)
 {
     if (N > 0) k_sensor_gradient<<<N, 256, 0, st>>>(N, n_window, series, eps, w, g);
+    count_launches(1);
 }
 
 // df = scale * E g   (E compact n_ctrl x N column-major)
@@ -242,6 +250,7 @@ __global__ void k_df(int N, int n_ctrl, const double *__restrict__ E, const doub
 void launch_df(int N, int n_ctrl, const double *E, const double *g, double scale, double *df, cudaStream_t st)
 {
     k_df<<<(n_ctrl + 255) / 256, 256, 0, st>>>(N, n_ctrl, E, g, scale, df);
+    count_launches(1);
 }
 
 __global__ void k_update_w(int N, double *w, const double *g, double step)
@@ -251,6 +260,7 @@ __global__ void k_update_w(int N, double *w, const double *g, double step)
 void launch_update_w(int N, double *w, const double *g, double step, cudaStream_t st)
 {
     k_update_w<<<1, 256, 0, st>>>(N, w, g, step);
+    count_launches(1);
 }
 
 } // namespace envar

@@ -20,7 +20,18 @@
 #include "envar_internal.cuh"
 #include "../../include/envar.h"
 
+#include <atomic>
+
 namespace envar {
+
+static std::atomic<long long> g_launches{0};
+static thread_local bool g_capturing = false;
+void count_launches(long long n)
+{
+    if (!g_capturing) g_launches += n;
+}
+long long launches_so_far() { return g_launches.load(); }
+void set_capturing(bool on) { g_capturing = on; }
 
 // ---------------------------------------------------------------------------- reset
 __global__ void k_broadcast(const double *__restrict__ src, double *__restrict__ dst, long long S, int M)
@@ -37,6 +48,7 @@ void launch_reset(const Grid &g, int M, const double *u0, const double *v0, doub
     size_t bytes = sizeof(double) * (size_t)g.S * M;
     k_broadcast<<<1024, 256, 0, st>>>(u0, u, g.S, M);
     k_broadcast<<<1024, 256, 0, st>>>(v0, v, g.S, M);
+    count_launches(2);
     cudaMemsetAsync(p, 0, bytes, st);
     cudaMemsetAsync(x, 0, bytes, st);
     cudaMemsetAsync(Ru, 0, tend_bytes, st);
@@ -80,6 +92,7 @@ __global__ void k_outflow(Grid g, const double *__restrict__ u, double *__restri
 void launch_outflow(const Grid &g, int M, const double *u, double *ubc, MemberCtl *ctl, cudaStream_t st)
 {
     k_outflow<<<M, 256, 0, st>>>(g, u, ubc, ctl);
+    count_launches(1);
 }
 
 // ---------------------------------------------------------------------------- predictor (K1)
@@ -165,6 +178,7 @@ void launch_predict(const Grid &g, int M, const double *u, const double *v, cons
 {
     dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), M);
     k_predict<TR><<<grd, blk, 0, st>>>(g, u, v, p, Ru, Rv, us, vs, ubc, frect, ctl);
+    count_launches(1);
 }
 template void launch_predict<float>(const Grid &, int, const double *, const double *, const double *, float *,
                                     float *, double *, double *, const double *, const double *,
@@ -194,6 +208,7 @@ void launch_rhs(const Grid &g, int M, const double *us, const double *vs, double
 {
     dim3 blk(32, 8), grd(cdiv(g.nx, 32), cdiv(g.ny, 8), M);
     k_rhs<<<grd, blk, 0, st>>>(g, us, vs, b);
+    count_launches(1);
 }
 
 // ---------------------------------------------------------------------------- correction (K6)
@@ -216,22 +231,29 @@ __device__ void sample_sensors(const Grid &g, double x0, double y0, const double
         {   // u: faces at (x0 + i dx, y0 + (j + 1/2) dy)
             double fi = (xs - x0) / g.dx, fj = (ys - y0) / g.dy - 0.5;
             int i0 = (int)floor(fi), j0 = (int)floor(fj);
-            if (i0 < 0 || i0 + 1 > g.nx || j0 < 0 || j0 + 1 > g.ny - 1) { out[2 * q] = nan(""); continue; }
-            double tx = fi - i0, ty = fj - j0;
-            long long c00 = (long long)j0 * g.P + i0;
-            double a = (1 - tx) * u_new(g, us, x, c00) + tx * u_new(g, us, x, c00 + 1);
-            double b = (1 - tx) * u_new(g, us, x, c00 + g.P) + tx * u_new(g, us, x, c00 + g.P + 1);
-            out[2 * q] = (1 - ty) * a + ty * b;
+            if (i0 < 0 || i0 + 1 > g.nx || j0 < 0 || j0 + 1 > g.ny - 1) {
+                out[2 * q] = nan("");
+            } else {
+                double tx = fi - i0, ty = fj - j0;
+                long long c00 = (long long)j0 * g.P + i0;
+                double a = (1 - tx) * u_new(g, us, x, c00) + tx * u_new(g, us, x, c00 + 1);
+                double b = (1 - tx) * u_new(g, us, x, c00 + g.P) + tx * u_new(g, us, x, c00 + g.P + 1);
+                out[2 * q] = (1 - ty) * a + ty * b;
+            }
         }
         {   // v: faces at (x0 + (i + 1/2) dx, y0 + j dy)
             double fi = (xs - x0) / g.dx - 0.5, fj = (ys - y0) / g.dy;
             int i0 = (int)floor(fi), j0 = (int)floor(fj);
-            if (i0 < 0 || i0 + 1 > g.nx - 1 || j0 < 0 || j0 + 1 > g.ny) { out[2 * q + 1] = nan(""); continue; }
-            double tx = fi - i0, ty = fj - j0;
-            long long c00 = (long long)j0 * g.P + i0;
-            double a = (1 - tx) * v_new(g, vs, x, c00) + tx * v_new(g, vs, x, c00 + 1);
-            double b = (ty > 0.0) ? (1 - tx) * v_new(g, vs, x, c00 + g.P) + tx * v_new(g, vs, x, c00 + g.P + 1) : 0.0;
-            out[2 * q + 1] = (1 - ty) * a + ty * b;
+            if (i0 < 0 || i0 + 1 > g.nx - 1 || j0 < 0 || j0 + 1 > g.ny) {
+                out[2 * q + 1] = nan("");
+            } else {
+                double tx = fi - i0, ty = fj - j0;
+                long long c00 = (long long)j0 * g.P + i0;
+                double a = (1 - tx) * v_new(g, vs, x, c00) + tx * v_new(g, vs, x, c00 + 1);
+                double b = (ty > 0.0) ? (1 - tx) * v_new(g, vs, x, c00 + g.P) + tx * v_new(g, vs, x, c00 + g.P + 1)
+                                      : 0.0;
+                out[2 * q + 1] = (1 - ty) * a + ty * b;
+            }
         }
     }
 }
@@ -313,6 +335,7 @@ void launch_correct(const Grid &g, double x0, double y0, int M, double *u, doubl
     dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), M);
     k_correct<<<grd, blk, 0, st>>>(g, x0, y0, u, v, p, us, vs, x, wf, want_welford, series, pt, ctl, div_tol,
                                    nfluid);
+    count_launches(1);
 }
 
 // ---------------------------------------------------------------------------- costs (K7)
@@ -369,8 +392,10 @@ void launch_cost(const Grid &g, int M, const double *wf, const double *series, d
     if (wf) {
         dim3 grd(nparts, M);
         k_domain_partial<<<grd, 256, 0, st>>>(g, wf, part);
+        count_launches(1);
     }
     k_cost_final<<<M, 256, 0, st>>>(g, wf ? part : nullptr, nparts, series, J_domain, J_sensor);
+    count_launches(1);
 }
 
 // ---------------------------------------------------------------------------- state export
@@ -391,6 +416,7 @@ void launch_export_state(const Grid &g, const double *u, const double *v, const 
 {
     dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), 1);
     k_export<<<grd, blk, 0, st>>>(g, u, v, p, uo, vo, po);
+    count_launches(1);
 }
 
 // Load raw initial fields (compact layouts) into the padded layout, applying the face rules.
@@ -414,6 +440,7 @@ void launch_load_ic(const Grid &g, const double *u0, const double *v0, double *u
 {
     dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), 1);
     k_load_ic<<<grd, blk, 0, st>>>(g, u0, v0, u, v);
+    count_launches(1);
 }
 
 } // namespace envar

@@ -477,6 +477,7 @@ static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B,
         T *e = (l == 0) ? z : (T *)B.lev_e[l];
         k_smooth<T, TILE_W, TILE_H><<<grid_of(L), TILE_THREADS, smooth_smem<T>(pc.nu_pre), st>>>(
             sa, f, e, nullptr, (T *)B.lev_f[l + 1], rc, ctl, inner_guard);
+        count_launches(1);
     }
     // coarse block
     {
@@ -500,6 +501,7 @@ static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B,
         const T *fin = (lc == 0) ? f0 : (const T *)B.lev_f[lc];
         T *eout = (lc == 0) ? z : (T *)B.lev_e[lc];
         k_coarse<T><<<M, 1024, sizeof(T) * off, st>>>(ca, fin, eout, ctl);
+        count_launches(1);
     }
     // ascend
     for (int l = lc - 1; l >= 0; --l) {
@@ -512,6 +514,7 @@ static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B,
         T *e = (l == 0) ? z : (T *)B.lev_e[l];
         k_smooth<T, TILE_W, TILE_H><<<grid_of(L), TILE_THREADS, smooth_smem<T>(pc.nu_post), st>>>(
             sa, f, e, (const T *)B.lev_e[l + 1], nullptr, rc, ctl, inner_guard);
+        count_launches(1);
     }
 }
 
@@ -546,18 +549,72 @@ void launch_pressure_solve(const Grid &g, const Level *lev, int M, const Poisson
     for (int o = 0; o <= pc.max_outer; ++o) {
         k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, r, e, rc, ctl, pc.rtol_abs,
                                                           o < pc.max_outer ? 1 : 0);
+        count_launches(1);
         if (o == pc.max_outer) break;
         vcycle<TM>(g, lev, M, B, pc, rc, ctl, 0, 0, 1, st);
         for (int k = 0; k < pc.max_inner; ++k) {
             k_spmv<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, z, pv[k & 1], pv[(k + 1) & 1], q, rc, ctl, k);
             k_axpy<TM><<<grd, TILE_THREADS, 0, st>>>(g, e, r, pv[(k + 1) & 1], q, rc, ctl, k);
+            count_launches(2);
             if (k + 1 == pc.max_inner) break;   // the last update needs no new preconditioned residual
             vcycle<TM>(g, lev, M, B, pc, rc, ctl, 1, k, 0, st);
             k_inner_check<<<cdiv(M, 32), 32, 0, st>>>(rc, ctl, k, pc.inner_rtol2);
+            count_launches(1);
         }
         k_outer_update<TM><<<grd, TILE_THREADS, 0, st>>>(g, B.x, e, ctl);
+        count_launches(1);
     }
 }
+
+template <class TM>
+int launch_poisson_single(int which, const Grid &g, const Level *lev, int M, const PoissonBufs &B,
+                          const PoissonCfg &pc, const Partials &pt, MemberCtl *ctl, cudaStream_t st)
+{
+    RedCtx rc = make_ctx(pt, M);
+    const Level &L0 = lev[0], &L1 = lev[1];
+    dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
+    TM *r = (TM *)B.r, *e = (TM *)B.e, *z = (TM *)B.z, *q = (TM *)B.q;
+    TM *pv[2] = {(TM *)B.pv, (TM *)B.pv + (size_t)g.S * M};
+    switch (which) {
+    case 1: {
+        SmoothArgs sa{L0, L1.P, L1.S, pc.nu_pre, 0, SF_ZERO_INIT | SF_RESTRICT, 0};
+        k_smooth<TM, TILE_W, TILE_H><<<grd, TILE_THREADS, smooth_smem<TM>(pc.nu_pre), st>>>(
+            sa, r, z, nullptr, (TM *)B.lev_f[1], rc, ctl, 0);
+        break;
+    }
+    case 2: {
+        SmoothArgs sa{L0, L1.P, L1.S, pc.nu_post, 1, SF_PROLONG | SF_DOT, 1};
+        k_smooth<TM, TILE_W, TILE_H><<<grd, TILE_THREADS, smooth_smem<TM>(pc.nu_post), st>>>(
+            sa, r, z, (const TM *)B.lev_e[1], nullptr, rc, ctl, 0);
+        break;
+    }
+    case 3: k_spmv<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, z, pv[1], pv[0], q, rc, ctl, 1); break;
+    case 4: k_axpy<TM><<<grd, TILE_THREADS, 0, st>>>(g, e, r, pv[0], q, rc, ctl, 1); break;
+    case 5: k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, r, e, rc, ctl, -1.0, 0); break;
+    case 7: {
+        PoissonCfg p2 = pc;
+        CoarseArgs ca;
+        int off = 0;
+        for (int l = 0; l < pc.nlev; ++l) {
+            ca.lev[l] = lev[l];
+            ca.off[l] = (l >= pc.ncoarse) ? off : 0;
+            if (l >= pc.ncoarse) off += 2 * lev[l].nx * lev[l].ny;
+        }
+        ca.lc = p2.ncoarse; ca.nlev = p2.nlev; ca.nu_pre = p2.nu_pre; ca.nu_post = p2.nu_post;
+        ca.coarse_sweeps = p2.coarse_sweeps; ca.inner_guard = 0;
+        k_coarse<TM><<<M, 1024, sizeof(TM) * off, st>>>(ca, (const TM *)B.lev_f[p2.ncoarse], (TM *)B.lev_e[p2.ncoarse],
+                                                        ctl);
+        break;
+    }
+    default: return -1;
+    }
+    count_launches(1);
+    return 0;
+}
+template int launch_poisson_single<float>(int, const Grid &, const Level *, int, const PoissonBufs &,
+                                          const PoissonCfg &, const Partials &, MemberCtl *, cudaStream_t);
+template int launch_poisson_single<double>(int, const Grid &, const Level *, int, const PoissonBufs &,
+                                           const PoissonCfg &, const Partials &, MemberCtl *, cudaStream_t);
 
 template void launch_pressure_solve<float>(const Grid &, const Level *, int, const PoissonBufs &, const PoissonCfg &,
                                            const Partials &, MemberCtl *, cudaStream_t);
