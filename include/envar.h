@@ -192,6 +192,13 @@ int envar_kernel_launches(envar_handle h, long long *count);
  * envar_reset_members or a forward run before using the state again. */
 int envar_time_kernel(envar_handle h, int which, int reps, double *ms_per_launch);
 
+/* Apply the pressure solve's multigrid preconditioner once, z = M r, to a level-0 cell field of
+ * member slot 0 (r_dev, z_dev: [ny][nx] float64, device; solid cells of r must be zero).  M is
+ * one symmetric V-cycle (red-black Gauss-Seidel, cell-sum restriction, piecewise-constant
+ * prolongation) and must be symmetric positive definite on mean-zero fields.  Overwrites the
+ * solver's work vectors of every member slot. */
+int envar_apply_preconditioner(envar_handle h, const double *r_dev, double *z_dev);
+
 #ifdef __cplusplus
 }
 #endif

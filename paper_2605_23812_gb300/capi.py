@@ -80,6 +80,7 @@ def lib():
         "envar_advance": [H, c_int],
         "envar_kernel_launches": [H, ctypes.POINTER(ctypes.c_longlong)],
         "envar_time_kernel": [H, c_int, c_int, ctypes.POINTER(c_double)],
+        "envar_apply_preconditioner": [H, c_void_p, c_void_p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -237,6 +238,14 @@ class Ensemble:
 
     def advance(self, n):
         self._check(lib().envar_advance(self._h, int(n)), "envar_advance")
+
+    def apply_preconditioner(self, r):
+        t = self.torch
+        rr = self._dev(r, (self.cfg.ny, self.cfg.nx))
+        z = t.empty_like(rr)
+        t.cuda.current_stream().synchronize()
+        self._check(lib().envar_apply_preconditioner(self._h, _ptr(rr), _ptr(z)), "envar_apply_preconditioner")
+        return z
 
     def time_kernel(self, which: int, reps: int = 20) -> float:
         ms = c_double()

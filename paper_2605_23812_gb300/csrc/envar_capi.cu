@@ -56,6 +56,10 @@ struct envar_handle_s {
     PoissonCfg pc{};
     Partials pt{};
     MemberCtl *d_ctl = nullptr;
+    // mixed-precision state (ENVAR_MIXED)
+    MixState ms{}, ic{};
+    MixConst mc{};
+    float *d_inh = nullptr, *d_inl = nullptr;
     // results
     double *d_Jd_slot = nullptr, *d_Js_slot = nullptr, *d_Jd = nullptr, *d_Js = nullptr, *d_costpart = nullptr;
     double *d_w = nullptr, *d_g = nullptr, *d_jprior = nullptr;
@@ -195,6 +199,16 @@ static int build_geometry(envar_handle h)
     CK(cudaMemcpy(dvk, vk.data(), S, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(duin, uin.data(), sizeof(double) * ny, cudaMemcpyHostToDevice));
     g.fluid = dF; g.uk = duk; g.vk = dvk; g.u_in = duin;
+    {
+        std::vector<float> ih((size_t)ny), il((size_t)ny);
+        for (int j = 0; j < ny; ++j) {
+            ih[j] = (float)uin[j];
+            il[j] = (float)(uin[j] - (double)ih[j]);
+        }
+        DA(h->d_inh, ny); DA(h->d_inl, ny);
+        CK(cudaMemcpy(h->d_inh, ih.data(), sizeof(float) * ny, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->d_inl, il.data(), sizeof(float) * ny, cudaMemcpyHostToDevice));
+    }
 
     // ---- multigrid hierarchy
     struct HostLevel { int nx, ny, P; long long S; std::vector<uint8_t> F; std::vector<double> cw, cs; };
@@ -252,7 +266,26 @@ static int build_geometry(envar_handle h)
         CK(cudaMemcpy(csf, f2.data(), sizeof(float) * L.S, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(cwd, L.cw.data(), sizeof(double) * L.S, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(csd, L.cs.data(), sizeof(double) * L.S, cudaMemcpyHostToDevice));
-        h->lev[l] = Level{L.nx, L.ny, L.P, L.S, dfl, cwf, csf, cwd, csd};
+        h->lev[l] = Level{L.nx, L.ny, L.P, L.S, dfl, cwf, csf, cwd, csd, nullptr, 0.0, 0.0};
+    }
+    {   // level-0 open-face bits (W 1, E 2, S 4, N 8) of fluid cells
+        std::vector<uint8_t> op((size_t)S, 0);
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                if (!F[(size_t)j * P + i]) continue;
+                uint8_t b = 0;
+                b |= (uk[(size_t)j * P + i] == FK_UNK) ? 1 : 0;
+                b |= (uk[(size_t)j * P + i + 1] == FK_UNK) ? 2 : 0;
+                b |= (vk[(size_t)j * P + i] == FK_UNK) ? 4 : 0;
+                b |= (vk[(size_t)(j + 1) * P + i] == FK_UNK) ? 8 : 0;
+                op[(size_t)j * P + i] = b;
+            }
+        uint8_t *dop;
+        DA(dop, S);
+        CK(cudaMemcpy(dop, op.data(), S, cudaMemcpyHostToDevice));
+        h->lev[0].open = dop;
+        h->lev[0].cx = g.cx;
+        h->lev[0].cy = g.cy;
     }
     // coarse block must fit in shared memory
     size_t coarse_elems = 0;
@@ -342,17 +375,29 @@ static int alloc_buffers(envar_handle h)
     const long long S = h->g.S;
     const size_t n0 = (size_t)S * M;
     const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
-    DA(h->d_u0, S); DA(h->d_v0, S);
-    DA(h->d_u, n0); DA(h->d_v, n0); DA(h->d_us, n0); DA(h->d_vs, n0); DA(h->d_p, n0);
-    DA(h->pb.x, n0); DA(h->pb.b, n0);
-    h->tend_bytes = tsz * n0;
-    {
+    if (h->mixed) {
+        MixState &ms = h->ms;
+        DA(ms.uh, n0); DA(ms.ul, n0); DA(ms.vh, n0); DA(ms.vl, n0);
+        DA(ms.ush, n0); DA(ms.usl, n0); DA(ms.vsh, n0); DA(ms.vsl, n0);
+        DA(ms.p, n0); DA(ms.Ru, n0); DA(ms.Rv, n0);
+        DA(ms.bh, n0); DA(ms.bl, n0); DA(ms.xh, n0); DA(ms.xl, n0);
+        if (h->cfg.cost_mode == ENVAR_COST_DOMAIN) DA(ms.wf, 6 * n0);
+        DA(ms.frect, (size_t)M * 2 * h->nrect);
+        DA(h->ic.uh, S); DA(h->ic.ul, S); DA(h->ic.vh, S); DA(h->ic.vl, S);
+        CK(cudaMemset(h->ic.uh, 0, sizeof(float) * S)); CK(cudaMemset(h->ic.ul, 0, sizeof(float) * S));
+        CK(cudaMemset(h->ic.vh, 0, sizeof(float) * S)); CK(cudaMemset(h->ic.vl, 0, sizeof(float) * S));
+        h->pb.ms = ms;
+    } else {
+        DA(h->d_u0, S); DA(h->d_v0, S);
+        DA(h->d_u, n0); DA(h->d_v, n0); DA(h->d_us, n0); DA(h->d_vs, n0); DA(h->d_p, n0);
+        DA(h->pb.x, n0); DA(h->pb.b, n0);
+        h->tend_bytes = tsz * n0;
         char *a, *b;
         DA(a, h->tend_bytes); DA(b, h->tend_bytes);
         h->d_Ru = a; h->d_Rv = b;
+        if (h->cfg.cost_mode == ENVAR_COST_DOMAIN) DA(h->d_wf, 3 * n0);
     }
     DA(h->d_ubc, (size_t)M * h->g.ny);
-    if (h->cfg.cost_mode == ENVAR_COST_DOMAIN) DA(h->d_wf, 3 * n0);
     const int nw = std::max(h->cfg.n_window, 1);
     DA(h->d_series_slot, (size_t)M * nw * 8);
     h->d_series = h->d_series_slot;
@@ -367,8 +412,13 @@ static int alloc_buffers(envar_handle h)
             DA(le, tsz * (size_t)h->lev[l].S * M); DA(lf, tsz * (size_t)h->lev[l].S * M);
             h->pb.lev_e[l] = le; h->pb.lev_f[l] = lf;
         }
+        for (int l = 0; l < h->ncoarse; ++l) {
+            char *lt;
+            DA(lt, tsz * (size_t)h->lev[l].S * M);
+            h->pb.lev_t[l] = lt;
+        }
     }
-    h->pt.nblk = cdiv(h->g.nx, TILE_W) * cdiv(h->g.ny, TILE_H);
+    h->pt.nblk = cdiv(h->g.nx, 32) * cdiv(h->g.ny, 16);   // capacity for every partial-producing tiling
     DA(h->pt.part, (size_t)RS_COUNT * M * h->pt.nblk);
     DA(h->pt.red, M);
     CK(cudaMemset(h->pt.red, 0, sizeof(MemberRed) * M));
@@ -392,6 +442,16 @@ static void enqueue_step(envar_handle h, int M)
 {
     const Grid &g = h->g;
     cudaStream_t st = h->st;
+    if (h->mixed) {
+        launch_outflow_mx(g, M, h->ms, h->d_ubc, h->d_ctl, st);
+        launch_predict_mx(g, h->mc, M, h->ms, h->d_ubc, h->d_inh, h->d_inl, h->d_ctl, st);
+        launch_rhs_mx(g, h->mc, M, h->ms, st);
+        launch_pressure_solve<float>(g, h->lev, M, h->pb, h->pc, h->pt, h->d_ctl, st);
+        launch_correct_mx(g, h->mc, M, h->ms, h->x0, h->y0, h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0,
+                          h->cfg.n_window > 0 ? h->d_series_slot : nullptr, h->pt, h->d_ctl, h->cfg.div_tol,
+                          h->nfluid, st);
+        return;
+    }
     launch_outflow(g, M, h->d_u, h->d_ubc, h->d_ctl, st);
     if (h->mixed)
         launch_predict<float>(g, M, h->d_u, h->d_v, h->d_p, (float *)h->d_Ru, (float *)h->d_Rv, h->d_us, h->d_vs,
@@ -460,9 +520,25 @@ static int run_steps(envar_handle h, int M, int nsteps)
 
 static void reset_members(envar_handle h, int M)
 {
+    if (h->mixed) {
+        launch_reset_mx(h->g, M, h->ic, h->ms, h->d_ctl, h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0, h->st);
+        return;
+    }
     launch_reset(h->g, M, h->d_u0, h->d_v0, h->d_u, h->d_v, h->d_p, h->pb.x, h->d_Ru, h->d_Rv,
                  h->tend_bytes / h->Mall * M, h->d_wf, h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0, h->d_ctl,
                  h->st);
+}
+
+static void enqueue_cost(envar_handle h, int M, double *Jd, double *Js)
+{
+    const double *ser = h->cfg.n_window > 0 ? h->d_series_slot : nullptr;
+    if (h->mixed) {
+        const int nparts = 64;
+        if (h->ms.wf) launch_domain_partial_mx(h->g, M, h->ms.wf, h->d_costpart, nparts, h->st);
+        launch_cost_final(h->g, M, h->ms.wf ? h->d_costpart : nullptr, nparts, ser, Jd, Js, h->st);
+    } else {
+        launch_cost(h->g, M, h->d_wf, ser, Jd, Js, h->d_costpart, h->st);
+    }
 }
 
 // One forward evaluation of all N+1 members (batched) or of member `only` (plain, slot 0).
@@ -472,21 +548,21 @@ static int forward_members(envar_handle h)
     const int nw = std::max(h->cfg.n_window, 1);
     h->ctl_all.assign(N + 1, MemberCtl{});
     if (h->batched) {
-        launch_member_forcing(h->Mall, 0, N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->st);
+        launch_member_forcing(h->Mall, 0, N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->ms.frect,
+                              h->st);
         reset_members(h, h->Mall);
         int rc = run_steps(h, h->Mall, h->cfg.n_steps);
         if (rc) return rc;
-        launch_cost(h->g, h->Mall, h->d_wf, h->cfg.n_window > 0 ? h->d_series_slot : nullptr, h->d_Jd, h->d_Js,
-                    h->d_costpart, h->st);
+        enqueue_cost(h, h->Mall, h->d_Jd, h->d_Js);
         CK(cudaMemcpyAsync(h->ctl_all.data(), h->d_ctl, sizeof(MemberCtl) * (N + 1), cudaMemcpyDeviceToHost, h->st));
     } else {
         for (int mm = 0; mm <= N; ++mm) {
-            launch_member_forcing(1, mm, N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->st);
+            launch_member_forcing(1, mm, N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->ms.frect,
+                                  h->st);
             reset_members(h, 1);
             int rc = run_steps(h, 1, h->cfg.n_steps);
             if (rc) return rc;
-            launch_cost(h->g, 1, h->d_wf, h->cfg.n_window > 0 ? h->d_series_slot : nullptr, h->d_Jd + mm,
-                        h->d_Js + mm, h->d_costpart, h->st);
+            enqueue_cost(h, 1, h->d_Jd + mm, h->d_Js + mm);
             CK(cudaMemcpyAsync(h->d_series + (size_t)mm * nw * 8, h->d_series_slot, sizeof(double) * nw * 8,
                                cudaMemcpyDeviceToDevice, h->st));
             CK(cudaMemcpyAsync(&h->ctl_all[mm], h->d_ctl, sizeof(MemberCtl), cudaMemcpyDeviceToHost, h->st));
@@ -552,6 +628,21 @@ extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda
         pc.max_outer = c.max_outer; pc.max_inner = c.max_inner;
         pc.inner_rtol2 = c.inner_rtol * c.inner_rtol;
         pc.rtol_abs = c.div_tol * h->g.hxy / h->g.dt;
+        {
+            const Grid &g = h->g;
+            auto split = [](double d, float *hi, float *lo) { *hi = (float)d; *lo = (float)(d - (double)*hi); };
+            MixConst &K = h->mc;
+            double gx = g.dt / g.dx, gy = g.dt / g.dy, kx = g.dy / g.dt, ky = g.dx / g.dt;
+            split(gx, &K.gxh, &K.gxl); split(gy, &K.gyh, &K.gyl);
+            split(kx, &K.kxh, &K.kxl); split(ky, &K.kyh, &K.kyl);
+            split(kx * gx, &K.cxh, &K.cxl); split(ky * gy, &K.cyh, &K.cyl);
+            K.dt = (float)g.dt; K.gxf = (float)gx; K.gyf = (float)gy;
+            K.i4dx = (float)(0.25 / g.dx); K.i4dy = (float)(0.25 / g.dy);
+            K.nudx2 = (float)(g.nu / (g.dx * g.dx)); K.nudy2 = (float)(g.nu / (g.dy * g.dy));
+            K.dxf = (float)g.dx; K.dyf = (float)g.dy;
+            pc.df_outer = h->mixed ? 1 : 0;
+            pc.mc = K;
+        }
         if (h->mixed) prepare_poisson_kernels<float>(); else prepare_poisson_kernels<double>();
         rc = generate_ensemble(h);
     }
@@ -593,9 +684,13 @@ extern "C" int envar_sizes(envar_handle h, int *n_ctrl, int *n_cc, int *n_levels
 extern "C" int envar_set_initial_state(envar_handle h, const double *u0, const double *v0)
 {
     if (!h || !u0 || !v0) return ENVAR_EINVAL;
-    CK(cudaMemsetAsync(h->d_u0, 0, sizeof(double) * h->g.S, h->st));
-    CK(cudaMemsetAsync(h->d_v0, 0, sizeof(double) * h->g.S, h->st));
-    launch_load_ic(h->g, u0, v0, h->d_u0, h->d_v0, h->st);
+    if (h->mixed) {
+        launch_load_ic_mx(h->g, u0, v0, h->ic, h->st);
+    } else {
+        CK(cudaMemsetAsync(h->d_u0, 0, sizeof(double) * h->g.S, h->st));
+        CK(cudaMemsetAsync(h->d_v0, 0, sizeof(double) * h->g.S, h->st));
+        launch_load_ic(h->g, u0, v0, h->d_u0, h->d_v0, h->st);
+    }
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
     h->have_ic = true;
@@ -702,11 +797,11 @@ extern "C" int envar_forward_control(envar_handle h, const double *f, double *J)
     if (!h || !f) return ENVAR_EINVAL;
     if (!h->have_ic) { set_err(h, "envar_forward_control: no initial state"); return ENVAR_ESTATE; }
     launch_compact_to_rect(1, h->nrect, h->ncc, h->d_cidx, f, h->d_frect, h->st);
+    if (h->mixed) launch_d2f(2 * (long long)h->nrect, h->d_frect, h->ms.frect, h->st);
     reset_members(h, 1);
     int rc = run_steps(h, 1, h->cfg.n_steps);
     if (rc) return rc;
-    launch_cost(h->g, 1, h->d_wf, h->cfg.n_window > 0 ? h->d_series_slot : nullptr, h->d_Jd_slot, h->d_Js_slot,
-                h->d_costpart, h->st);
+    enqueue_cost(h, 1, h->d_Jd_slot, h->d_Js_slot);
     const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js_slot : h->d_Jd_slot;
     if (J) CK(cudaMemcpyAsync(J, src, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -736,7 +831,10 @@ extern "C" int envar_get_state(envar_handle h, int member, double *u, double *v,
     }
     if (slot < 0 || slot >= h->Mall) return ENVAR_EINVAL;
     const long long off = (long long)slot * h->g.S;
-    launch_export_state(h->g, h->d_u + off, h->d_v + off, h->d_p + off, u, v, p, h->st);
+    if (h->mixed)
+        launch_export_mx(h->g, h->ms, off, u, v, p, h->st);
+    else
+        launch_export_state(h->g, h->d_u + off, h->d_v + off, h->d_p + off, u, v, p, h->st);
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
     return ENVAR_OK;
@@ -772,7 +870,7 @@ extern "C" int envar_reset_members(envar_handle h, const double *w)
     if (!h) return ENVAR_EINVAL;
     if (!h->have_ic) { set_err(h, "envar_reset_members: no initial state"); return ENVAR_ESTATE; }
     if (h->N > 0 && w) CK(cudaMemcpyAsync(h->d_w, w, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
-    launch_member_forcing(h->Mall, 0, h->N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->st);
+    launch_member_forcing(h->Mall, 0, h->N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->ms.frect, h->st);
     reset_members(h, h->Mall);
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
@@ -816,18 +914,23 @@ extern "C" int envar_time_kernel(envar_handle h, int which, int reps, double *ms
         switch (which) {
         case 0:
             if (h->mixed)
-                launch_predict<float>(g, M, h->d_u, h->d_v, h->d_p, (float *)h->d_Ru, (float *)h->d_Rv, h->d_us,
-                                      h->d_vs, h->d_ubc, h->d_frect, h->d_ctl, h->st);
+                launch_predict_mx(g, h->mc, M, h->ms, h->d_ubc, h->d_inh, h->d_inl, h->d_ctl, h->st);
             else
                 launch_predict<double>(g, M, h->d_u, h->d_v, h->d_p, (double *)h->d_Ru, (double *)h->d_Rv, h->d_us,
                                        h->d_vs, h->d_ubc, h->d_frect, h->d_ctl, h->st);
             return 0;
         case 6:
+            if (h->mixed) {
+                launch_correct_mx(g, h->mc, M, h->ms, h->x0, h->y0, wf, ser, h->pt, h->d_ctl, h->cfg.div_tol,
+                                  h->nfluid, h->st);
+                return 0;
+            }
             launch_correct(g, h->x0, h->y0, M, h->d_u, h->d_v, h->d_p, h->d_us, h->d_vs, h->pb.x, h->d_wf, wf, ser,
                            h->pt, h->d_ctl, h->cfg.div_tol, h->nfluid, h->st);
             return 0;
         case 8:
-            launch_rhs(g, M, h->d_us, h->d_vs, h->pb.b, h->d_ctl, h->st);
+            if (h->mixed) launch_rhs_mx(g, h->mc, M, h->ms, h->st);
+            else launch_rhs(g, M, h->d_us, h->d_vs, h->pb.b, h->d_ctl, h->st);
             return 0;
         default:
             return h->mixed ? launch_poisson_single<float>(which, g, h->lev, M, h->pb, h->pc, h->pt, h->d_ctl, h->st)
@@ -849,5 +952,25 @@ extern "C" int envar_time_kernel(envar_handle h, int which, int reps, double *ms
     cudaEventDestroy(e1);
     CK(cudaGetLastError());
     *ms = (double)t / reps;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_apply_preconditioner(envar_handle h, const double *r_dev, double *z_dev)
+{
+    if (!h || !r_dev || !z_dev) return ENVAR_EINVAL;
+    const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
+    CK(cudaMemsetAsync(h->d_ctl, 0, sizeof(MemberCtl) * h->Mall, h->st));
+    CK(cudaMemsetAsync(h->pb.r, 0, tsz * (size_t)h->g.S * h->Mall, h->st));
+    if (h->mixed) {
+        launch_cells_in<float>(h->g, r_dev, (float *)h->pb.r, h->st);
+        launch_vcycle<float>(h->g, h->lev, h->Mall, h->pb, h->pc, h->pt, h->d_ctl, h->st);
+        launch_cells_out<float>(h->g, (const float *)h->pb.z, z_dev, h->st);
+    } else {
+        launch_cells_in<double>(h->g, r_dev, (double *)h->pb.r, h->st);
+        launch_vcycle<double>(h->g, h->lev, h->Mall, h->pb, h->pc, h->pt, h->d_ctl, h->st);
+        launch_cells_out<double>(h->g, (const double *)h->pb.z, z_dev, h->st);
+    }
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
     return ENVAR_OK;
 }

@@ -32,6 +32,8 @@ struct Level {
     const float *csf;       // south-face conductance (j in 0..ny), [ny+1][P]
     const double *cwd;
     const double *csd;
+    const uint8_t *open;    // level 0 only: open-face bits (1 W, 2 E, 4 S, 8 N) of fluid cells
+    double cx, cy;          // level 0 only: conductance of an open x / y face
 };
 
 struct Grid {
@@ -68,9 +70,27 @@ struct MemberRed {
     double val[RS_COUNT];         // max |r| (outer residual), sum x, r^T z (start, ping, pong), p^T A p
 };
 struct Partials {
-    int nblk;               // level-0 tiles per member
+    int nblk;               // partial slots per member (>= blocks per member of any producing kernel)
     double *part;           // [RS_COUNT][M][nblk]
     MemberRed *red;         // [M]
+};
+
+// Mixed-precision (ENVAR_MIXED) member state: df64 quantities are hi/lo float planes.
+struct MixState {
+    float *uh, *ul, *vh, *vl;       // velocity u^n, v^n (df64)
+    float *ush, *usl, *vsh, *vsl;   // predictor u*, v* (df64)
+    float *p;                       // pressure (FP32)
+    float *Ru, *Rv;                 // previous tendency (FP32, AB2)
+    float *bh, *bl, *xh, *xl;       // Poisson right-hand side and solution (df64)
+    float *wf;                      // Welford per member: 6 planes (mean_u, mean_v, M2; hi/lo)
+    float *frect;                   // member forcing on the control rectangle (FP32)
+};
+// Constants of the mixed step; df64 pairs (h, l) where FP64-level accuracy is needed.
+struct MixConst {
+    float gxh, gxl, gyh, gyl;       // gamma = dt/dx, dt/dy       (velocity correction)
+    float kxh, kxl, kyh, kyl;       // kappa = dy/dt, dx/dt       (right-hand side)
+    float cxh, cxl, cyh, cyl;       // c = kappa * gamma         (Poisson operator)
+    float dt, gxf, gyf, i4dx, i4dy, nudx2, nudy2, dxf, dyf;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -119,6 +139,46 @@ __device__ __forceinline__ double warp_partials(const double *p, int n, bool is_
     return is_max ? warp_max(v) : warp_sum(v);
 }
 
+struct RedCtx {
+    int nblk;             // partial slots per member (capacity)
+    double *part;         // [RS_COUNT][M][nblk]
+    MemberRed *red;       // [M]
+    int M;
+};
+static inline RedCtx make_ctx(const Partials &pt, int M) { return RedCtx{pt.nblk, pt.part, pt.red, M}; }
+
+// Publish a block partial of a per-member scalar; the blocks of one member are the kernel's
+// blockIdx.x/y grid.  Returns true in the (single) last block to arrive, whose thread 0 then holds
+// the fixed-order total in *total (sum, or max when is_max).
+__device__ __forceinline__ bool publish_partial(const RedCtx &rc, int slot, int m, double v, bool is_max, double *total)
+{
+    __shared__ bool s_last;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nb = gridDim.x * gridDim.y;
+    double *p = rc.part + ((long long)slot * rc.M + m) * rc.nblk;
+    if (tid == 0) {
+        p[blockIdx.x + blockIdx.y * gridDim.x] = v;
+        __threadfence();
+        unsigned int t = atomicAdd(&rc.red[m].cnt[slot], 1u);
+        s_last = (t == (unsigned int)nb - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    if (tid < 32) {
+        double acc = 0.0;
+        for (int k = tid; k < nb; k += 32) {
+            double w = __ldcg(p + k);
+            acc = is_max ? fmax(acc, w) : acc + w;
+        }
+        acc = is_max ? warp_max(acc) : warp_sum(acc);
+        if (tid == 0) {
+            *total = acc;
+            rc.red[m].cnt[slot] = 0;
+        }
+    }
+    return true;
+}
+
 template <class T> __device__ __forceinline__ const T *cw_of(const Level &L);
 template <> __device__ __forceinline__ const float *cw_of<float>(const Level &L) { return L.cwf; }
 template <> __device__ __forceinline__ const double *cw_of<double>(const Level &L) { return L.cwd; }
@@ -160,10 +220,12 @@ void launch_export_state(const Grid &g, const double *u, const double *v, const 
 
 // Poisson kernels (k_poisson.cu).  TM = multigrid / inner-CG precision.
 struct PoissonBufs {
-    double *b, *x;                  // level-0 FP64 right-hand side and solution
+    MixState ms;                    // mixed mode: df64 b and x live here
+    double *b, *x;                  // level-0 FP64 right-hand side and solution (FP64 modes)
     void *r, *e, *z, *pv, *q;       // level-0 inner vectors (TM)
     void *lev_e[MAX_LEVELS];        // level >= 1 correction (TM)
     void *lev_f[MAX_LEVELS];        // level >= 1 right-hand side (TM)
+    void *lev_t[MAX_LEVELS];        // pre-smoothed guess of each tiled level (level 0 included)
 };
 struct PoissonCfg {
     int nlev;                       // number of levels
@@ -172,8 +234,17 @@ struct PoissonCfg {
     int max_outer, max_inner;
     double inner_rtol2;             // inner_rtol^2
     double rtol_abs;                // outer stop: max |r| <= rtol_abs (r = b - A x, FV form)
+    int df_outer;                   // 1: outer residual / update in df64 (mixed mode)
+    MixConst mc;
 };
 template <class TM> void prepare_poisson_kernels();
+template <class TM>
+void launch_vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc,
+                   const Partials &pt, MemberCtl *ctl, cudaStream_t st);
+template <class TM>
+void launch_cells_in(const Grid &g, const double *src, TM *dst, cudaStream_t st);
+template <class TM>
+void launch_cells_out(const Grid &g, const TM *src, double *dst, cudaStream_t st);
 // Launch ONE kernel of the pressure solve (for standalone timing):
 //   1 level-0 pre-smoothing + restriction, 2 level-0 prolongation + post-smoothing + dot,
 //   3 inner SpMV, 4 inner AXPY, 5 outer FP64 residual, 7 coarse-level block kernel.
@@ -184,6 +255,28 @@ template <class TM>
 void launch_pressure_solve(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc,
                            const Partials &pt, MemberCtl *ctl, cudaStream_t st);
 
+// Mixed-precision kernels (k_mixed.cu)
+void launch_load_ic_mx(const Grid &g, const double *u0, const double *v0, const MixState &s0, cudaStream_t st);
+void launch_reset_mx(const Grid &g, int M, const MixState &ic, const MixState &s, MemberCtl *ctl, int want_welford,
+                     cudaStream_t st);
+void launch_export_mx(const Grid &g, const MixState &s, long long off, double *uo, double *vo, double *po,
+                      cudaStream_t st);
+void launch_outflow_mx(const Grid &g, int M, const MixState &s, double *ubc, MemberCtl *ctl, cudaStream_t st);
+void launch_predict_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const double *ubc, const float *inh,
+                       const float *inl, const MemberCtl *ctl, cudaStream_t st);
+void launch_rhs_mx(const Grid &g, const MixConst &K, int M, const MixState &s, cudaStream_t st);
+void launch_outer_residual_mx(const Grid &g, const Level &L0, const MixConst &K, int M, const MixState &s, float *r,
+                              float *e, const RedCtx &rc, MemberCtl *ctl, double rtol_abs, int count_it,
+                              cudaStream_t st);
+void launch_outer_update_mx(const Grid &g, int M, const MixState &s, const float *e, const MemberCtl *ctl,
+                            cudaStream_t st);
+void launch_correct_mx(const Grid &g, const MixConst &K, int M, const MixState &s, double x0, double y0,
+                       int want_welford, double *series, const Partials &pt, MemberCtl *ctl, double div_tol,
+                       long long nfluid, cudaStream_t st);
+void launch_domain_partial_mx(const Grid &g, int M, const float *wf, double *part, int nparts, cudaStream_t st);
+void launch_cost_final(const Grid &g, int M, const double *part, int nparts, const double *series, double *J_domain,
+                       double *J_sensor, cudaStream_t st);
+
 // Ensemble kernels (k_ensemble.cu)
 void launch_normals(unsigned long long seed, unsigned long long stream, long long first, long long n, double *out,
                     cudaStream_t st);
@@ -191,7 +284,7 @@ void launch_conv_sampler(int N, int nrx, int nry, int nxix, int nxiy, const doub
                          const double *Z, const uint8_t *rect_ctrl, double sigma, double *Erect, double *tmp,
                          cudaStream_t st);
 void launch_member_forcing(int M, int first_member, int N, int nrect, const double *Erect, const double *w,
-                           double eps, double *frect, cudaStream_t st);
+                           double eps, double *frect, float *frect_f, cudaStream_t st);
 void launch_rect_to_compact(int N, int nrect, int ncc, const int *cidx, const double *Erect, double *E,
                             cudaStream_t st);
 void launch_compact_to_rect(int N, int nrect, int ncc, const int *cidx, const double *E, double *Erect,
@@ -202,5 +295,6 @@ void launch_scalar_gradient(int N, const double *J, const double *w, double eps,
                             cudaStream_t st);
 void launch_df(int N, int n_ctrl, const double *E, const double *g, double scale, double *df, cudaStream_t st);
 void launch_update_w(int N, double *w, const double *g, double step, cudaStream_t st);
+void launch_d2f(long long n, const double *a, float *b, cudaStream_t st);
 
 } // namespace envar

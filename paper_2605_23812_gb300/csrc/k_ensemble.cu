@@ -125,7 +125,8 @@ void launch_conv_sampler(int N, int nrx, int nry, int nxix, int nxiy, const doub
 
 // f[m][c][rect] = sum_k E[k][c][rect] w_k + (member > 0 ? eps E[member-1][c][rect] : 0)
 __global__ void k_member_forcing(int M, int first_member, int N, int nrect, const double *__restrict__ E,
-                                 const double *__restrict__ w, double eps, double *__restrict__ f)
+                                 const double *__restrict__ w, double eps, double *__restrict__ f,
+                                 float *__restrict__ ff)
 {
     long long n = (long long)M * 2 * nrect;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -136,14 +137,16 @@ __global__ void k_member_forcing(int M, int first_member, int N, int nrect, cons
         for (int k = 0; k < N; ++k) acc += E[(long long)k * 2 * nrect + r] * w[k];
         if (member > 0) acc += eps * E[(long long)(member - 1) * 2 * nrect + r];
         f[t] = acc;
+        if (ff) ff[t] = (float)acc;
     }
 }
 
 void launch_member_forcing(int M, int first_member, int N, int nrect, const double *Erect, const double *w,
-                           double eps, double *frect, cudaStream_t st)
+                           double eps, double *frect, float *frect_f, cudaStream_t st)
 {
     long long n = (long long)M * 2 * nrect;
-    k_member_forcing<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M, first_member, N, nrect, Erect, w, eps, frect);
+    k_member_forcing<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M, first_member, N, nrect, Erect, w, eps, frect,
+                                                                  frect_f);
     count_launches(1);
 }
 
@@ -252,6 +255,48 @@ void launch_df(int N, int n_ctrl, const double *E, const double *g, double scale
     k_df<<<(n_ctrl + 255) / 256, 256, 0, st>>>(N, n_ctrl, E, g, scale, df);
     count_launches(1);
 }
+
+__global__ void k_d2f(long long n, const double *__restrict__ a, float *__restrict__ b)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        b[t] = (float)a[t];
+}
+void launch_d2f(long long n, const double *a, float *b, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_d2f<<<(unsigned)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535), 256, 0, st>>>(n, a, b);
+    count_launches(1);
+}
+
+// compact [ny][nx] <-> padded level-0 cell layout (one member slot)
+template <class TM>
+__global__ void k_cells_in(int nx, int ny, int P, const double *__restrict__ src, TM *__restrict__ dst)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i < nx) dst[(long long)j * P + i] = (TM)src[(long long)j * nx + i];
+}
+template <class TM>
+__global__ void k_cells_out(int nx, int ny, int P, const TM *__restrict__ src, double *__restrict__ dst)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i < nx) dst[(long long)j * nx + i] = (double)src[(long long)j * P + i];
+}
+template <class TM>
+void launch_cells_in(const Grid &g, const double *src, TM *dst, cudaStream_t st)
+{
+    k_cells_in<TM><<<dim3(cdiv(g.nx, 128), g.ny), 128, 0, st>>>(g.nx, g.ny, g.P, src, dst);
+    count_launches(1);
+}
+template <class TM>
+void launch_cells_out(const Grid &g, const TM *src, double *dst, cudaStream_t st)
+{
+    k_cells_out<TM><<<dim3(cdiv(g.nx, 128), g.ny), 128, 0, st>>>(g.nx, g.ny, g.P, src, dst);
+    count_launches(1);
+}
+template void launch_cells_in<float>(const Grid &, const double *, float *, cudaStream_t);
+template void launch_cells_in<double>(const Grid &, const double *, double *, cudaStream_t);
+template void launch_cells_out<float>(const Grid &, const float *, double *, cudaStream_t);
+template void launch_cells_out<double>(const Grid &, const double *, double *, cudaStream_t);
 
 __global__ void k_update_w(int N, double *w, const double *g, double step)
 {

@@ -385,6 +385,13 @@ __global__ void k_cost_final(Grid g, const double *__restrict__ part, int nparts
     }
 }
 
+void launch_cost_final(const Grid &g, int M, const double *part, int nparts, const double *series, double *J_domain,
+                       double *J_sensor, cudaStream_t st)
+{
+    k_cost_final<<<M, 256, 0, st>>>(g, part, nparts, series, J_domain, J_sensor);
+    count_launches(1);
+}
+
 void launch_cost(const Grid &g, int M, const double *wf, const double *series, double *J_domain, double *J_sensor,
                  double *part, cudaStream_t st)
 {

@@ -1,0 +1,534 @@
+// k_mixed.cu -- mixed-precision time step (ENVAR_MIXED) of the forced Navier-Stokes solver.
+//
+// Same discretisation as k_flow.cu (Sec. 2, Eq. forced_NS on the MAC grid; AB2 + incremental
+// projection), with the precision split chosen for GB300, whose FP64 pipe runs at ~1/64 of FP32:
+//   * tendencies R (advection, diffusion) in FP32 from the high words of the velocity;
+//   * velocity state u, v, the Poisson right-hand side b and solution x, and the Welford
+//     accumulators in double-float (hi + lo floats, ~48 bits, df64.cuh), so that the FP64-level
+//     divergence tolerance (1e-10) is met without FP64 instructions per cell;
+//   * pressure p in FP32: u^{n+1} = P(u^n + dt R) does not depend on the accuracy of p^n, which
+//     only shifts the incremental solve's starting point.
+// The projection operators are built from df64 constants with dt*c = h*gamma, so the divergence
+// of the corrected field equals -dt (b - A x)/(dx dy) to df64 rounding.
+#include "df64.cuh"
+#include "envar_internal.cuh"
+#include "../../include/envar.h"
+
+namespace envar {
+
+// ---------------------------------------------------------------------------- IC / reset / export
+__global__ void k_load_ic_mx(Grid g, const double *__restrict__ u0, const double *__restrict__ v0, float *uh, float *ul,
+                             float *vh, float *vl)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    long long c = (long long)j * g.P + i;
+    if (j < g.ny) {
+        uint8_t k = g.uk[c];
+        double val = 0.0;
+        if (k == FK_UNK || k == FK_OUTLET) val = u0[(long long)j * (g.nx + 1) + i];
+        else if (k == FK_INLET) val = g.u_in[j];
+        f2 d = d_to_df(val);
+        uh[c] = d.h; ul[c] = d.l;
+    }
+    if (i < g.nx) {
+        f2 d = d_to_df((g.vk[c] == FK_UNK) ? v0[(long long)j * g.nx + i] : 0.0);
+        vh[c] = d.h; vl[c] = d.l;
+    }
+}
+
+void launch_load_ic_mx(const Grid &g, const double *u0, const double *v0, const MixState &s0, cudaStream_t st)
+{
+    dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), 1);
+    k_load_ic_mx<<<grd, blk, 0, st>>>(g, u0, v0, s0.uh, s0.ul, s0.vh, s0.vl);
+    count_launches(1);
+}
+
+__global__ void k_broadcast4(const float *__restrict__ a, const float *__restrict__ b, const float *__restrict__ c,
+                             const float *__restrict__ d, float *A, float *B, float *C, float *D, long long S, int M)
+{
+    long long n = S * (long long)M;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        long long k = t % S;
+        A[t] = a[k]; B[t] = b[k]; C[t] = c[k]; D[t] = d[k];
+    }
+}
+
+void launch_reset_mx(const Grid &g, int M, const MixState &ic, const MixState &s, MemberCtl *ctl, int want_welford,
+                     cudaStream_t st)
+{
+    size_t fb = sizeof(float) * (size_t)g.S * M;
+    k_broadcast4<<<1024, 256, 0, st>>>(ic.uh, ic.ul, ic.vh, ic.vl, s.uh, s.ul, s.vh, s.vl, g.S, M);
+    count_launches(1);
+    cudaMemsetAsync(s.p, 0, fb, st);
+    cudaMemsetAsync(s.xh, 0, fb, st);
+    cudaMemsetAsync(s.xl, 0, fb, st);
+    cudaMemsetAsync(s.Ru, 0, fb, st);
+    cudaMemsetAsync(s.Rv, 0, fb, st);
+    if (want_welford) cudaMemsetAsync(s.wf, 0, 6 * fb, st);
+    cudaMemsetAsync(ctl, 0, sizeof(MemberCtl) * M, st);
+}
+
+__global__ void k_export_mx(Grid g, const float *uh, const float *ul, const float *vh, const float *vl, const float *p,
+                            double *uo, double *vo, double *po)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    long long c = (long long)j * g.P + i;
+    if (uo && j < g.ny) uo[(long long)j * (g.nx + 1) + i] = (double)uh[c] + (double)ul[c];
+    if (vo && i < g.nx) vo[(long long)j * g.nx + i] = (double)vh[c] + (double)vl[c];
+    if (po && i < g.nx && j < g.ny) po[(long long)j * g.nx + i] = g.fluid[c] ? (double)p[c] : 0.0;
+}
+
+void launch_export_mx(const Grid &g, const MixState &s, long long off, double *uo, double *vo, double *po,
+                      cudaStream_t st)
+{
+    dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), 1);
+    k_export_mx<<<grd, blk, 0, st>>>(g, s.uh + off, s.ul + off, s.vh + off, s.vl + off, s.p + off, uo, vo, po);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------- outflow
+__global__ void k_outflow_mx(Grid g, const float *__restrict__ uh, const float *__restrict__ ul, double *__restrict__ ubc,
+                             MemberCtl *ctl)
+{
+    int m = blockIdx.x;
+    const long long off = (long long)m * g.S;
+    double qin = 0.0, qout = 0.0, nout = 0.0;
+    for (int j = threadIdx.x; j < g.ny; j += blockDim.x) {
+        long long c = (long long)j * g.P;
+        if (g.uk[c] == FK_INLET) qin += g.u_in[j] * g.dy;
+        if (g.uk[c + g.nx] == FK_OUTLET) {
+            double ub = (double)uh[off + c + g.nx] + (double)ul[off + c + g.nx];
+            double ui = (double)uh[off + c + g.nx - 1] + (double)ul[off + c + g.nx - 1];
+            double un = ub - g.dt * g.conv_speed * (ub - ui) / g.dx;
+            ubc[(long long)m * g.ny + j] = un;
+            qout += un * g.dy;
+            nout += 1.0;
+        } else {
+            ubc[(long long)m * g.ny + j] = 0.0;
+        }
+    }
+    qin = block_reduce(qin, false);
+    qout = block_reduce(qout, false);
+    nout = block_reduce(nout, false);
+    double shift = (nout > 0.0) ? (qin - qout) / (nout * g.dy) : 0.0;
+    for (int j = threadIdx.x; j < g.ny; j += blockDim.x)
+        if (g.uk[(long long)j * g.P + g.nx] == FK_OUTLET) ubc[(long long)m * g.ny + j] += shift;
+    if (threadIdx.x == 0) {
+        ctl[m].step += 1;
+        ctl[m].outer_done = 0;
+        ctl[m].inner_done = 0;
+    }
+}
+
+void launch_outflow_mx(const Grid &g, int M, const MixState &s, double *ubc, MemberCtl *ctl, cudaStream_t st)
+{
+    k_outflow_mx<<<M, 256, 0, st>>>(g, s.uh, s.ul, ubc, ctl);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------- predictor (K1)
+__device__ __forceinline__ float cell_forcing_f(const Grid &g, const float *__restrict__ fr, int comp, int i, int j)
+{
+    int a = i - g.ia, b = j - g.ja;
+    if (a < 0 || a >= g.nrx || b < 0 || b >= g.nry) return 0.f;
+    return fr[((long long)comp * g.nry + b) * g.nrx + a];
+}
+
+__global__ void __launch_bounds__(256) k_predict_mx(Grid g, MixConst K, MixState s, const double *__restrict__ ubc,
+                                                    const float *__restrict__ inh, const float *__restrict__ inl,
+                                                    const MemberCtl *__restrict__ ctl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int m = blockIdx.z;
+    if (i > g.nx || j > g.ny) return;
+    const long long off = (long long)m * g.S;
+    const int P = g.P;
+    const float *__restrict__ uh = s.uh + off;
+    const float *__restrict__ ul = s.ul + off;
+    const float *__restrict__ vh = s.vh + off;
+    const float *__restrict__ vl = s.vl + off;
+    const float *__restrict__ pm = s.p + off;
+    float *__restrict__ Ru = s.Ru + off;
+    float *__restrict__ Rv = s.Rv + off;
+    const float *__restrict__ fr = s.frect + (long long)m * 2 * g.nry * g.nrx;
+    const uint8_t *__restrict__ uk = g.uk;
+    const uint8_t *__restrict__ vk = g.vk;
+    const bool has_u = j < g.ny, has_v = i < g.nx;
+    // clamped neighbour indices: every load below is in bounds and independent of the others;
+    // values at clamped positions are used only where the face kind makes them the true neighbour
+    const int jn = min(j + 1, g.ny - 1), js = max(j - 1, 0), ie = min(i + 1, g.nx), iw = max(i - 1, 0);
+    const int ivw = max(i - 1, 0), ive = min(i + 1, g.nx - 1), jvn = min(j + 1, g.ny);
+    const long long c = (long long)j * P + i;
+    const long long cUN = (long long)jn * P + i, cUS = (long long)js * P + i;
+    const long long cE = (long long)j * P + ie, cW = (long long)j * P + iw;
+    const long long cVN = (long long)jvn * P + i;
+    // kinds
+    const uint8_t ku = has_u ? uk[c] : FK_ZERO, kuN = uk[cUN], kuS = uk[cUS];
+    const uint8_t kv = has_v ? vk[c] : FK_ZERO, kvE = vk[(long long)j * P + ive], kvW = vk[(long long)j * P + ivw];
+    // velocities (high words), pressure, previous tendencies
+    const float uc = uh[c], ue = uh[cE], uw = uh[cW], un0 = uh[cUN], us0 = uh[cUS];
+    const float usw = uh[(long long)js * P + i], use = uh[(long long)js * P + ie];
+    const float vc = vh[c], vn = vh[cVN], vs0 = vh[(long long)max(j - 1, 0) * P + i];
+    const float ve0 = vh[(long long)j * P + ive], vw0 = vh[(long long)j * P + ivw];
+    const float vnw = vh[(long long)jvn * P + iw], vsw = vh[cW];
+    const float ulc = ul[c], vlc = vl[c];
+    const float pc = pm[c], pw = pm[cW], ps = pm[(long long)max(j - 1, 0) * P + i];
+    const float Rup = Ru[c], Rvp = Rv[c];
+    const bool first = (ctl[m].step == 1);
+    const float c1 = first ? 1.f : 1.5f, c0 = first ? 0.f : -0.5f;
+
+    if (has_u) {  // u face (i, j)
+        f2 out{0.f, 0.f};
+        if (ku == FK_UNK) {
+            const float un = (j + 1 == g.ny) ? uc : (kuN == FK_SOLID ? -uc : un0);
+            const float usv = (j == 0) ? -uc : (kuS == FK_SOLID ? -uc : us0);
+            const float fe = uc + ue, fw = uw + uc;
+            const float adv = (fe * fe - fw * fw) * K.i4dx + ((uc + un) * (vnw + vn) - (usv + uc) * (vsw + vc)) * K.i4dy;
+            const float dif = K.nudx2 * (ue - 2.f * uc + uw) + K.nudy2 * (un - 2.f * uc + usv);
+            const float R = dif - adv;
+            Ru[c] = R;
+            const float du = K.dt * (c1 * R + c0 * Rup) - K.gxf * (pc - pw);
+            out = df_add_f(f2{uc, ulc}, du);
+            const float f = 0.5f * (cell_forcing_f(g, fr, 0, i - 1, j) + cell_forcing_f(g, fr, 0, i, j));
+            if (f != 0.f) out = df_add_f(out, K.dt * f);
+        } else if (ku == FK_INLET) {
+            out = f2{inh[j], inl[j]};
+        } else if (ku == FK_OUTLET) {
+            out = d_to_df(ubc[(long long)m * g.ny + j]);
+        }
+        s.ush[off + c] = out.h;
+        s.usl[off + c] = out.l;
+    }
+    if (has_v) {  // v face (i, j)
+        f2 out{0.f, 0.f};
+        if (kv == FK_UNK) {
+            const float ve = (i + 1 == g.nx) ? vc : (kvE == FK_SOLID ? -vc : ve0);
+            const float vw = (i == 0) ? -vc : (kvW == FK_SOLID ? -vc : vw0);
+            const float fn = vc + vn, fs = vs0 + vc;
+            const float adv = ((use + ue) * (vc + ve) - (usw + uc) * (vw + vc)) * K.i4dx + (fn * fn - fs * fs) * K.i4dy;
+            const float dif = K.nudx2 * (ve - 2.f * vc + vw) + K.nudy2 * (vn - 2.f * vc + vs0);
+            const float R = dif - adv;
+            Rv[c] = R;
+            const float dv = K.dt * (c1 * R + c0 * Rvp) - K.gyf * (pc - ps);
+            out = df_add_f(f2{vc, vlc}, dv);
+            const float f = 0.5f * (cell_forcing_f(g, fr, 1, i, j - 1) + cell_forcing_f(g, fr, 1, i, j));
+            if (f != 0.f) out = df_add_f(out, K.dt * f);
+        }
+        s.vsh[off + c] = out.h;
+        s.vsl[off + c] = out.l;
+    }
+}
+
+void launch_predict_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const double *ubc, const float *inh,
+                       const float *inl, const MemberCtl *ctl, cudaStream_t st)
+{
+    dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), M);
+    k_predict_mx<<<grd, blk, 0, st>>>(g, K, s, ubc, inh, inl, ctl);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------- rhs
+__global__ void __launch_bounds__(256) k_rhs_mx(Grid g, MixConst K, MixState s)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int m = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const long long off = (long long)m * g.S, c = off + (long long)j * g.P + i;
+    f2 b{0.f, 0.f};
+    if (g.fluid[c - off]) {
+        f2 dU = df_sub(f2{s.ush[c + 1], s.usl[c + 1]}, f2{s.ush[c], s.usl[c]});
+        f2 dV = df_sub(f2{s.vsh[c + g.P], s.vsl[c + g.P]}, f2{s.vsh[c], s.vsl[c]});
+        b = df_add(df_mul(dU, f2{K.kxh, K.kxl}), df_mul(dV, f2{K.kyh, K.kyl}));
+        b = f2{-b.h, -b.l};
+    }
+    s.bh[c] = b.h;
+    s.bl[c] = b.l;
+}
+
+void launch_rhs_mx(const Grid &g, const MixConst &K, int M, const MixState &s, cudaStream_t st)
+{
+    dim3 blk(32, 8), grd(cdiv(g.nx, 32), cdiv(g.ny, 8), M);
+    k_rhs_mx<<<grd, blk, 0, st>>>(g, K, s);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------- outer residual (df64)
+__global__ void __launch_bounds__(256) k_outer_residual_mx(Grid g, Level L0, MixConst K, const float *__restrict__ bh,
+                                                           const float *__restrict__ bl, const float *__restrict__ xh,
+                                                           const float *__restrict__ xl, float *__restrict__ r,
+                                                           float *__restrict__ e, RedCtx rc, MemberCtl *ctl,
+                                                           double rtol_abs, int count_it)
+{
+    const int m = blockIdx.z;
+    if (ctl[m].outer_done) return;
+    const long long off = (long long)m * g.S;
+    const int i0 = blockIdx.x * TILE_W, j0 = blockIdx.y * TILE_H;
+    float rmax = 0.f;
+    f2 xs{0.f, 0.f};
+#pragma unroll
+    for (int q = threadIdx.x; q < TILE_W * TILE_H; q += TILE_THREADS) {
+        int i = i0 + (q % TILE_W), j = j0 + (q / TILE_W);
+        if (i >= g.nx || j >= g.ny) continue;
+        long long c = (long long)j * g.P + i;
+        float rv = 0.f;
+        if (g.fluid[c]) {
+            const long long o = off + c;
+            f2 xc{xh[o], xl[o]};
+            f2 sx{0.f, 0.f}, sy{0.f, 0.f};
+            if (L0.cwf[c] != 0.f) sx = df_add(sx, df_sub(xc, f2{xh[o - 1], xl[o - 1]}));
+            if (L0.cwf[c + 1] != 0.f) sx = df_add(sx, df_sub(xc, f2{xh[o + 1], xl[o + 1]}));
+            if (L0.csf[c] != 0.f) sy = df_add(sy, df_sub(xc, f2{xh[o - g.P], xl[o - g.P]}));
+            if (L0.csf[c + g.P] != 0.f) sy = df_add(sy, df_sub(xc, f2{xh[o + g.P], xl[o + g.P]}));
+            f2 ax = df_add(df_mul(sx, f2{K.cxh, K.cxl}), df_mul(sy, f2{K.cyh, K.cyl}));
+            f2 res = df_sub(f2{bh[o], bl[o]}, ax);
+            rv = res.h;
+            rmax = fmaxf(rmax, fabsf(rv));
+            xs = df_add_f(xs, xc.h);
+        }
+        r[off + c] = rv;
+        e[off + c] = 0.f;
+    }
+    double rm = (double)block_max_f(rmax);
+    double xsum = block_sum_df(xs);
+    double tot;
+    bool last1 = publish_partial(rc, RS_RMAX, m, rm, true, &tot);
+    if (last1 && threadIdx.x == 0) {
+        rc.red[m].val[RS_RMAX] = tot;
+        int done = (tot <= rtol_abs) ? 1 : 0;
+        ctl[m].outer_done = done;
+        ctl[m].inner_done = done;
+        if (!done && count_it) ctl[m].outer_its += 1;
+    }
+    __syncthreads();
+    bool last2 = publish_partial(rc, RS_XSUM, m, xsum, false, &tot);
+    if (last2 && threadIdx.x == 0) rc.red[m].val[RS_XSUM] = tot;
+}
+
+__global__ void __launch_bounds__(256) k_outer_update_mx(Grid g, float *__restrict__ xh, float *__restrict__ xl,
+                                                         const float *__restrict__ e, const MemberCtl *ctl)
+{
+    const int m = blockIdx.z;
+    if (ctl[m].outer_done) return;
+    const long long off = (long long)m * g.S;
+    const int i0 = blockIdx.x * TILE_W, j0 = blockIdx.y * TILE_H;
+#pragma unroll
+    for (int q = threadIdx.x; q < TILE_W * TILE_H; q += TILE_THREADS) {
+        int i = i0 + (q % TILE_W), j = j0 + (q / TILE_W);
+        if (i >= g.nx || j >= g.ny) continue;
+        long long c = (long long)j * g.P + i;
+        if (!g.fluid[c]) continue;
+        f2 x = df_add_f(f2{xh[off + c], xl[off + c]}, e[off + c]);
+        xh[off + c] = x.h;
+        xl[off + c] = x.l;
+    }
+}
+
+void launch_outer_residual_mx(const Grid &g, const Level &L0, const MixConst &K, int M, const MixState &s, float *r,
+                              float *e, const RedCtx &rc, MemberCtl *ctl, double rtol_abs, int count_it,
+                              cudaStream_t st)
+{
+    dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
+    k_outer_residual_mx<<<grd, TILE_THREADS, 0, st>>>(g, L0, K, s.bh, s.bl, s.xh, s.xl, r, e, rc, ctl, rtol_abs,
+                                                     count_it);
+    count_launches(1);
+}
+
+void launch_outer_update_mx(const Grid &g, int M, const MixState &s, const float *e, const MemberCtl *ctl,
+                            cudaStream_t st)
+{
+    dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
+    k_outer_update_mx<<<grd, TILE_THREADS, 0, st>>>(g, s.xh, s.xl, e, ctl);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------- correction (K6)
+__device__ __forceinline__ f2 u_new_mx(const Grid &g, const MixConst &K, const float *ush, const float *usl,
+                                       const float *xh, const float *xl, long long c)
+{
+    f2 us{ush[c], usl[c]};
+    if (g.uk[c] != FK_UNK) return us;
+    f2 d = df_sub(f2{xh[c], xl[c]}, f2{xh[c - 1], xl[c - 1]});
+    return df_sub(us, df_mul(d, f2{K.gxh, K.gxl}));
+}
+__device__ __forceinline__ f2 v_new_mx(const Grid &g, const MixConst &K, const float *vsh, const float *vsl,
+                                       const float *xh, const float *xl, long long c)
+{
+    f2 vs{vsh[c], vsl[c]};
+    if (g.vk[c] != FK_UNK) return vs;
+    f2 d = df_sub(f2{xh[c], xl[c]}, f2{xh[c - g.P], xl[c - g.P]});
+    return df_sub(vs, df_mul(d, f2{K.gyh, K.gyl}));
+}
+
+__device__ void sample_sensors_mx(const Grid &g, const MixConst &K, double x0, double y0, const float *ush,
+                                  const float *usl, const float *vsh, const float *vsl, const float *xh,
+                                  const float *xl, double *out)
+{
+    for (int q = 0; q < 4; ++q) {
+        double xs = 0.2 * (q + 1), ys = 0.0;
+        {
+            double fi = (xs - x0) / g.dx, fj = (ys - y0) / g.dy - 0.5;
+            int i0 = (int)floor(fi), j0 = (int)floor(fj);
+            if (i0 < 0 || i0 + 1 > g.nx || j0 < 0 || j0 + 1 > g.ny - 1) {
+                out[2 * q] = nan("");
+            } else {
+                double tx = fi - i0, ty = fj - j0;
+                long long c00 = (long long)j0 * g.P + i0;
+                double a = (1 - tx) * df_to_d(u_new_mx(g, K, ush, usl, xh, xl, c00)) +
+                           tx * df_to_d(u_new_mx(g, K, ush, usl, xh, xl, c00 + 1));
+                double b = (1 - tx) * df_to_d(u_new_mx(g, K, ush, usl, xh, xl, c00 + g.P)) +
+                           tx * df_to_d(u_new_mx(g, K, ush, usl, xh, xl, c00 + g.P + 1));
+                out[2 * q] = (1 - ty) * a + ty * b;
+            }
+        }
+        {
+            double fi = (xs - x0) / g.dx - 0.5, fj = (ys - y0) / g.dy;
+            int i0 = (int)floor(fi), j0 = (int)floor(fj);
+            if (i0 < 0 || i0 + 1 > g.nx - 1 || j0 < 0 || j0 + 1 > g.ny) {
+                out[2 * q + 1] = nan("");
+            } else {
+                double tx = fi - i0, ty = fj - j0;
+                long long c00 = (long long)j0 * g.P + i0;
+                double a = (1 - tx) * df_to_d(v_new_mx(g, K, vsh, vsl, xh, xl, c00)) +
+                           tx * df_to_d(v_new_mx(g, K, vsh, vsl, xh, xl, c00 + 1));
+                double b = (ty > 0.0) ? (1 - tx) * df_to_d(v_new_mx(g, K, vsh, vsl, xh, xl, c00 + g.P)) +
+                                            tx * df_to_d(v_new_mx(g, K, vsh, vsl, xh, xl, c00 + g.P + 1))
+                                      : 0.0;
+                out[2 * q + 1] = (1 - ty) * a + ty * b;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ f2 corrected(bool unk, f2 us, f2 xa, f2 xb, f2 gam)
+{
+    return unk ? df_sub(us, df_mul(df_sub(xa, xb), gam)) : us;
+}
+
+__global__ void __launch_bounds__(256) k_correct_mx(Grid g, MixConst K, MixState s, double x0, double y0,
+                                                    int want_welford, double *__restrict__ series, Partials pt,
+                                                    MemberCtl *ctl, double div_tol, long long nfluid)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int m = blockIdx.z;
+    const long long off = (long long)m * g.S;
+    const int P = g.P;
+    const float *__restrict__ ush = s.ush + off;
+    const float *__restrict__ usl = s.usl + off;
+    const float *__restrict__ vsh = s.vsh + off;
+    const float *__restrict__ vsl = s.vsl + off;
+    const float *__restrict__ xh = s.xh + off;
+    const float *__restrict__ xl = s.xl + off;
+    __shared__ float s_mean;
+    __shared__ int s_t;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) {
+        s_mean = (float)(pt.red[m].val[RS_XSUM] / (double)nfluid);
+        s_t = ctl[m].step - (g.n_steps - g.n_window);
+    }
+    __syncthreads();
+    const float xmean = s_mean;
+    const int t = (s_t > 0 && s_t <= g.n_window) ? s_t : 0;
+    int bad = 0;
+    if (i <= g.nx && j <= g.ny) {
+        const bool has_u = j < g.ny, has_v = i < g.nx, cell = has_u && has_v;
+        const int iw = max(i - 1, 0), ie = min(i + 1, g.nx), js = max(j - 1, 0), jn = min(j + 1, g.ny);
+        const long long c = (long long)j * P + i;
+        const long long cW = (long long)j * P + iw, cE = (long long)j * P + ie;
+        const long long cS = (long long)js * P + i, cN = (long long)jn * P + i;
+        // independent loads (clamped neighbours are used only where the face kind allows)
+        const bool uk0 = g.uk[c] == FK_UNK, ukE = g.uk[cE] == FK_UNK;
+        const bool vk0 = g.vk[c] == FK_UNK, vkN = g.vk[cN] == FK_UNK;
+        const f2 x0v{xh[c], xl[c]}, xW{xh[cW], xl[cW]}, xE{xh[cE], xl[cE]}, xS{xh[cS], xl[cS]}, xN{xh[cN], xl[cN]};
+        const f2 u0s{ush[c], usl[c]}, uEs{ush[cE], usl[cE]}, v0s{vsh[c], vsl[c]}, vNs{vsh[cN], vsl[cN]};
+        const f2 gx{K.gxh, K.gxl}, gy{K.gyh, K.gyl};
+        const f2 un = corrected(uk0, u0s, x0v, xW, gx);
+        const f2 vn = corrected(vk0, v0s, x0v, xS, gy);
+        if (has_u) {
+            s.uh[off + c] = un.h;
+            s.ul[off + c] = un.l;
+            bad |= !isfinite(un.h) ? ENVAR_ST_NONFINITE : 0;
+            bad |= (fabsf(un.h) * K.dt > K.dxf) ? ENVAR_ST_CFL : 0;
+        }
+        if (has_v) {
+            s.vh[off + c] = vn.h;
+            s.vl[off + c] = vn.l;
+            bad |= !isfinite(vn.h) ? ENVAR_ST_NONFINITE : 0;
+            bad |= (fabsf(vn.h) * K.dt > K.dyf) ? ENVAR_ST_CFL : 0;
+        }
+        if (cell && g.fluid[c]) {
+            s.p[off + c] += x0v.h - xmean;
+            if (want_welford && t > 0) {
+                const f2 uE = corrected(ukE, uEs, xE, x0v, gx);
+                const f2 vN = corrected(vkN, vNs, xN, x0v, gy);
+                const f2 uc = df_scale_half(df_add(un, uE));
+                const f2 vc = df_scale_half(df_add(vn, vN));
+                float *__restrict__ w = s.wf + 6 * off;
+                const long long S = g.S;
+                const f2 inv_n = df_recip_int(t);
+                const f2 mu{w[c], w[S + c]}, mv{w[2 * S + c], w[3 * S + c]};
+                f2 m2{w[4 * S + c], w[5 * S + c]};
+                const f2 du = df_sub(uc, mu);
+                const f2 mun = df_add(mu, df_mul(du, inv_n));
+                const f2 dv = df_sub(vc, mv);
+                const f2 mvn = df_add(mv, df_mul(dv, inv_n));
+                m2 = df_add(m2, df_add(df_mul(du, df_sub(uc, mun)), df_mul(dv, df_sub(vc, mvn))));
+                w[c] = mun.h; w[S + c] = mun.l;
+                w[2 * S + c] = mvn.h; w[3 * S + c] = mvn.l;
+                w[4 * S + c] = m2.h; w[5 * S + c] = m2.l;
+            }
+        }
+    }
+    bad = __syncthreads_or(bad);
+    if (tid == 0 && bad) atomicOr(&ctl[m].status, bad);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+        double dv = g.dt * pt.red[m].val[RS_RMAX] / g.hxy;
+        if (dv > ctl[m].max_div) ctl[m].max_div = dv;
+        if (!(dv <= div_tol)) ctl[m].status |= ENVAR_ST_DIVERGENCE;
+        if (t > 0 && series) {
+            double sv[8];
+            sample_sensors_mx(g, K, x0, y0, ush, usl, vsh, vsl, xh, xl, sv);
+            double *dst = series + ((long long)m * g.n_window + (t - 1)) * 8;
+            for (int q = 0; q < 8; ++q) dst[q] = sv[q];
+        }
+    }
+}
+
+void launch_correct_mx(const Grid &g, const MixConst &K, int M, const MixState &s, double x0, double y0,
+                       int want_welford, double *series, const Partials &pt, MemberCtl *ctl, double div_tol,
+                       long long nfluid, cudaStream_t st)
+{
+    dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), M);
+    k_correct_mx<<<grd, blk, 0, st>>>(g, K, s, x0, y0, want_welford, series, pt, ctl, div_tol, nfluid);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------- cost
+__global__ void k_domain_partial_mx(Grid g, const float *__restrict__ wf, double *__restrict__ part)
+{
+    int m = blockIdx.y;
+    const float *m2h = wf + 6LL * m * g.S + 4LL * g.S, *m2l = m2h + g.S;
+    long long ncell = (long long)g.ny * g.P;
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(c % g.P);
+        if (i < g.nx && g.fluid[c]) acc += (double)m2h[c] + (double)m2l[c];
+    }
+    acc = block_reduce(acc, false);
+    if (threadIdx.x == 0) part[(long long)m * gridDim.x + blockIdx.x] = acc;
+}
+
+void launch_domain_partial_mx(const Grid &g, int M, const float *wf, double *part, int nparts, cudaStream_t st)
+{
+    dim3 grd(nparts, M);
+    k_domain_partial_mx<<<grd, 256, 0, st>>>(g, wf, part);
+    count_launches(1);
+}
+
+} // namespace envar

@@ -17,48 +17,24 @@
 // partial, and the last block to arrive (atomic ticket) sums the partials in a fixed order and
 // publishes the scalar and the convergence flags in the member's control block.  Every loop is a
 // fixed number of launches (graph friendly); converged members' blocks exit at once.
+#include "df64.cuh"
 #include "envar_internal.cuh"
 
 namespace envar {
 
-struct RedCtx {
-    int nblk;             // partial-producing blocks per member (level-0 tiles)
-    double *part;         // [RS_COUNT][M][nblk]
-    MemberRed *red;       // [M]
-    int M;
+// Dot-product accumulation: FP64-accurate in both precisions -- df64 on the FP32 pipe for float
+// vectors (no FP64 instruction per cell), plain FP64 for double vectors.
+template <class T> struct DotAcc;
+template <> struct DotAcc<float> {
+    f2 v{0.f, 0.f};
+    __device__ __forceinline__ void add(float a, float b) { v = df_add(v, two_prod(a, b)); }
+    __device__ __forceinline__ double total() { return block_sum_df(v); }
 };
-
-__device__ __forceinline__ int tile_id() { return blockIdx.x + blockIdx.y * gridDim.x; }
-
-// Publish a block partial; returns true in the (single) last block, whose thread 0 then holds
-// the fixed-order total in *total (sum, or max when is_max).
-__device__ bool publish_partial(const RedCtx &rc, int slot, int m, double v, bool is_max, double *total)
-{
-    __shared__ bool s_last;
-    int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    double *p = rc.part + ((long long)slot * rc.M + m) * rc.nblk;
-    if (tid == 0) {
-        p[tile_id()] = v;
-        __threadfence();
-        unsigned int t = atomicAdd(&rc.red[m].cnt[slot], 1u);
-        s_last = (t == (unsigned int)rc.nblk - 1);
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    if (tid < 32) {
-        double acc = 0.0;
-        for (int k = tid; k < rc.nblk; k += 32) {
-            double w = __ldcg(p + k);
-            acc = is_max ? fmax(acc, w) : acc + w;
-        }
-        acc = is_max ? warp_max(acc) : warp_sum(acc);
-        if (tid == 0) {
-            *total = acc;
-            rc.red[m].cnt[slot] = 0;
-        }
-    }
-    return true;
-}
+template <> struct DotAcc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ double total() { return block_reduce(v, false); }
+};
 
 // ------------------------------------------------------------------------------------------------
 // outer FP64 residual:  r = b - A x  (written in TM as the inner right-hand side), e = 0,
@@ -75,6 +51,7 @@ __global__ void __launch_bounds__(256) k_outer_residual(Grid g, Level L0, const 
     const int i0 = blockIdx.x * TILE_W, j0 = blockIdx.y * TILE_H;
     const int tid = threadIdx.x;
     double rmax = 0.0, xs = 0.0;
+#pragma unroll
     for (int q = tid; q < TILE_W * TILE_H; q += TILE_THREADS) {
         int i = i0 + (q % TILE_W), j = j0 + (q / TILE_W);
         if (i >= g.nx || j >= g.ny) continue;
@@ -119,6 +96,7 @@ __global__ void __launch_bounds__(256) k_outer_update(Grid g, double *__restrict
     if (ctl[m].outer_done) return;
     const long long off = (long long)m * g.S;
     const int i0 = blockIdx.x * TILE_W, j0 = blockIdx.y * TILE_H;
+#pragma unroll
     for (int q = threadIdx.x; q < TILE_W * TILE_H; q += TILE_THREADS) {
         int i = i0 + (q % TILE_W), j = j0 + (q / TILE_W);
         if (i >= g.nx || j >= g.ny) continue;
@@ -146,7 +124,8 @@ __global__ void __launch_bounds__(256) k_spmv(Grid g, Level L0, const TM *__rest
     const TM bt = (TM)beta;
     const int i0 = blockIdx.x * TILE_W, j0 = blockIdx.y * TILE_H;
     const TM *zm = z + off, *pm = pold + off;
-    double pq = 0.0;
+    DotAcc<TM> pq;
+#pragma unroll
     for (int qq = threadIdx.x; qq < TILE_W * TILE_H; qq += TILE_THREADS) {
         int i = i0 + (qq % TILE_W), j = j0 + (qq / TILE_W);
         if (i >= g.nx || j >= g.ny) continue;
@@ -162,14 +141,14 @@ __global__ void __launch_bounds__(256) k_spmv(Grid g, Level L0, const TM *__rest
             if (csS != (TM)0) acc -= csS * ((k > 0) ? zm[c - g.P] + bt * pm[c - g.P] : zm[c - g.P]);
             if (csN != (TM)0) acc -= csN * ((k > 0) ? zm[c + g.P] + bt * pm[c + g.P] : zm[c + g.P]);
             qv = acc;
-            pq += (double)pc * (double)qv;
+            pq.add(pc, qv);
         }
         pnew[off + c] = pc;
         q[off + c] = qv;
     }
-    pq = block_reduce(pq, false);
+    double pqt = pq.total();
     double tot;
-    if (publish_partial(rc, RS_PQ, m, pq, false, &tot) && threadIdx.x == 0) {
+    if (publish_partial(rc, RS_PQ, m, pqt, false, &tot) && threadIdx.x == 0) {
         rc.red[m].val[RS_PQ] = tot;
         if (!(tot > 0.0)) ctl[m].inner_done = 1;   // breakdown: stop this member's inner loop
     }
@@ -186,6 +165,7 @@ __global__ void __launch_bounds__(256) k_axpy(Grid g, TM *__restrict__ e, TM *__
     const double alpha = rc.red[m].val[(k & 1) ? RS_RZB : RS_RZA] / rc.red[m].val[RS_PQ];
     const TM a = (TM)alpha;
     const int i0 = blockIdx.x * TILE_W, j0 = blockIdx.y * TILE_H;
+#pragma unroll
     for (int qq = threadIdx.x; qq < TILE_W * TILE_H; qq += TILE_THREADS) {
         int i = i0 + (qq % TILE_W), j = j0 + (qq / TILE_W);
         if (i >= g.nx || j >= g.ny) continue;
@@ -197,10 +177,17 @@ __global__ void __launch_bounds__(256) k_axpy(Grid g, TM *__restrict__ e, TM *__
 }
 
 // ------------------------------------------------------------------------------------------------
-// Tiled red-black Gauss-Seidel on one level.  The tile (TW x TH cells) is loaded with a halo of
-// H = 2*nsweep + 1 cells; sub-sweep s (0 .. 2 nsweep - 1) updates its colour on cells within
-// distance H - 1 - s of the tile interior, so after all sub-sweeps the interior and its first
-// ring hold exactly the values of a global red-black sweep sequence.
+// Red-black Gauss-Seidel smoothing of one multigrid level, nsweep red-black sweep pairs per launch.
+// A block owns a tile of TW x TH cells and loads it with a halo of H = 2*nsweep + 1 cells, i.e. a
+// 64 x 42 region.  Each of its 384 threads owns one 7-cell column segment of the region: the cell
+// values, right-hand side, inverse diagonal and face conductances (on level 0, four open-face bits)
+// stay in registers; only the east / west neighbours (and the segment ends) go through shared
+// memory.  Every sub-sweep updates every cell of the region except its outer ring; a cell's value
+// agrees with the global sweep sequence while it lies within H - 1 - s of the tile after sub-sweep
+// s, because its neighbours lie within H - s and agreed after sub-sweep s - 1.  After 2*nsweep
+// sub-sweeps the tile and its first ring therefore hold exactly the values of a global red-black
+// sweep sequence, which the optional restriction (residual of the tile, summed over 2x2 children)
+// and the optional FP64-accurate dot product r^T z use.
 enum SmoothFlags { SF_ZERO_INIT = 1, SF_PROLONG = 2, SF_RESTRICT = 4, SF_DOT = 8, SF_INIT_DOT = 16 };
 
 struct SmoothArgs {
@@ -213,115 +200,148 @@ struct SmoothArgs {
     int k;                // inner iteration (for the dot slot)
 };
 
-template <class T>
-__device__ __forceinline__ int cell_dist(int a, int b, int H, int TW, int TH)
-{
-    int d = 0;
-    d = max(d, H - a);
-    d = max(d, a - (H + TW - 1));
-    d = max(d, H - b);
-    d = max(d, b - (H + TH - 1));
-    return d;
-}
+// Thread layout: a block of 384 threads covers a 64 x 42 region (tile + halo); each thread owns a
+// 7-cell column segment.  The cell values, right-hand side, inverse diagonal and face
+// conductances (on level 0, four open-face bits) stay in registers; only east / west neighbours
+// and the segment ends go through shared memory.
+constexpr int SC_COLS = 64, SC_SEG = 6, SC_R = 7, SC_THREADS = SC_COLS * SC_SEG;
+__host__ __device__ constexpr int sc_tw(int ns) { return SC_COLS - 2 * (2 * ns + 1); }
+__host__ __device__ constexpr int sc_th(int ns) { return SC_SEG * SC_R - 2 * (2 * ns + 1); }
 
-template <class T, int TW, int TH>
-__global__ void __launch_bounds__(256) k_smooth(SmoothArgs sa, const T *__restrict__ f, T *__restrict__ e,
-                                                const T *__restrict__ ec, T *__restrict__ fc, RedCtx rc,
-                                                MemberCtl *ctl, int inner_guard)
+template <class T, int NS, bool BIN>
+__global__ void __launch_bounds__(SC_THREADS, sizeof(T) == 4 ? 2 : 1) k_smooth(SmoothArgs sa, const T *__restrict__ f,
+                                                       const T *__restrict__ ein, T *__restrict__ e,
+                                                       const T *__restrict__ ec, T *__restrict__ fc, RedCtx rc,
+                                                       MemberCtl *ctl, int inner_guard)
 {
-    extern __shared__ unsigned char smem_raw[];
+    constexpr int H = 2 * NS + 1, NW = SC_COLS, NH = SC_SEG * SC_R, TW = sc_tw(NS), TH = sc_th(NS);
+    constexpr int SWP = NW + 1;
+    __shared__ T se[NH * SWP];
+    __shared__ T sr[NH * SWP];
     const int m = blockIdx.z;
     if (ctl[m].outer_done) return;
     if (inner_guard && ctl[m].inner_done) return;
     const Level &L = sa.L;
-    const int H = 2 * sa.nsweep + 1;
-    const int SW = TW + 2 * H + 1, SH = TH + 2 * H + 1;
-    T *se = reinterpret_cast<T *>(smem_raw);
-    T *sf = se + SW * SH;
-    T *scw = sf + SW * SH;
-    T *scs = scw + SW * SH;
     const long long off = (long long)m * L.S;
+    const int tid = threadIdx.x;
+    const int a = tid % NW, b0 = (tid / NW) * SC_R;
     const int i0 = blockIdx.x * TW, j0 = blockIdx.y * TH;
     const int gi0 = i0 - H, gj0 = j0 - H;
-    const T *cw = cw_of<T>(L), *cs = cs_of<T>(L);
-    const int tid = threadIdx.x;
+    const int i = gi0 + a;
+    // The input guess (ein) and the output (e) are different buffers: a block reads its halo from
+    // cells that neighbouring blocks overwrite, so an in-place update would race.
+    const T *__restrict__ fm = f + off;
+    const T *__restrict__ eim = ein + off;
+    T *__restrict__ em = e + off;
+    const T *__restrict__ ecm = ec + (long long)m * sa.Sc;
+    const T *__restrict__ cw = cw_of<T>(L);
+    const T *__restrict__ cs = cs_of<T>(L);
+    const uint8_t *__restrict__ opn = L.open;
+    const uint8_t *__restrict__ fl = L.fluid;
+    const T cx = (T)L.cx, cy = (T)L.cy;
     const bool zero = (sa.flags & SF_ZERO_INIT) != 0;
     const bool prolong = (sa.flags & SF_PROLONG) != 0;
 
-    for (int q = tid; q < SW * SH; q += blockDim.x) {
-        int a = q % SW, b = q / SW;
-        int i = gi0 + a, j = gj0 + b;
-        T vw = (T)0, vs = (T)0, ve = (T)0, vf = (T)0;
-        if (i >= 0 && j >= 0) {
-            long long c = (long long)j * L.P + i;
-            if (j < L.ny && i <= L.nx) vw = cw[c];
-            if (i < L.nx && j <= L.ny) vs = cs[c];
-            if (i < L.nx && j < L.ny) {
-                vf = f[off + c];
-                if (!zero) ve = e[off + c];
-                if (prolong && L.fluid[c]) ve += ec[(long long)m * sa.Sc + (long long)(j >> 1) * sa.Pc + (i >> 1)];
+    // face conductances: four open-face bits per cell on level 0, four values per cell elsewhere
+    constexpr int NK = BIN ? 1 : SC_R;
+    T ev[SC_R], fv[SC_R], iv[SC_R];
+    T kw[NK], ke[NK], ks[NK], kn[NK];
+    int mk[BIN ? SC_R : 1];
+#define KW(r) (BIN ? ((mk[BIN ? (r) : 0] & 1) ? cx : (T)0) : kw[BIN ? 0 : (r)])
+#define KE(r) (BIN ? ((mk[BIN ? (r) : 0] & 2) ? cx : (T)0) : ke[BIN ? 0 : (r)])
+#define KS(r) (BIN ? ((mk[BIN ? (r) : 0] & 4) ? cy : (T)0) : ks[BIN ? 0 : (r)])
+#define KN(r) (BIN ? ((mk[BIN ? (r) : 0] & 8) ? cy : (T)0) : kn[BIN ? 0 : (r)])
+#pragma unroll
+    for (int r = 0; r < SC_R; ++r) {
+        const int j = gj0 + b0 + r;
+        const bool cell = (i >= 0 && i < L.nx && j >= 0 && j < L.ny);
+        const long long c = (long long)j * L.P + i;
+        T w_ = 0, e_ = 0, s_ = 0, n_ = 0;
+        bool act = false;
+        if (BIN) {
+            const int bits = cell ? (int)opn[c] : 0;
+            mk[BIN ? r : 0] = bits;
+            w_ = (bits & 1) ? cx : (T)0;
+            e_ = (bits & 2) ? cx : (T)0;
+            s_ = (bits & 4) ? cy : (T)0;
+            n_ = (bits & 8) ? cy : (T)0;
+            act = bits != 0;
+        } else {
+            if (cell) {
+                w_ = cw[c]; e_ = cw[c + 1]; s_ = cs[c]; n_ = cs[c + L.P];
+                act = fl[c] != 0;
             }
+            kw[BIN ? 0 : r] = w_; ke[BIN ? 0 : r] = e_; ks[BIN ? 0 : r] = s_; kn[BIN ? 0 : r] = n_;
         }
-        scw[q] = vw;
-        scs[q] = vs;
-        sf[q] = vf;
-        se[q] = ve;
+        const T d = w_ + e_ + s_ + n_;
+        iv[r] = (d != (T)0) ? (T)1 / d : (T)0;
+        fv[r] = cell ? fm[c] : (T)0;
+        T v = (cell && !zero) ? eim[c] : (T)0;
+        if (cell && prolong && act) v += ecm[(long long)(j >> 1) * sa.Pc + (i >> 1)];
+        ev[r] = v;
     }
+#pragma unroll
+    for (int r = 0; r < SC_R; ++r) se[(b0 + r) * SWP + a] = ev[r];
     __syncthreads();
 
-    const int NW = TW + 2 * H, NH = TH + 2 * H;
-    for (int s = 0; s < 2 * sa.nsweep; ++s) {
-        const int colour = ((s & 1) ^ sa.order);          // 0 = red ((i+j) even)
-        const int lim = H - 1 - s;
-        for (int q = tid; q < NW * NH; q += blockDim.x) {
-            int a = q % NW, b = q / NW;
-            int i = gi0 + a, j = gj0 + b;
-            if (((i + j) & 1) != colour) continue;
-            if (cell_dist<T>(a, b, H, TW, TH) > lim) continue;
-            int sq = b * SW + a;
-            T cW = scw[sq], cE = scw[sq + 1], cS = scs[sq], cN = scs[sq + SW];
-            T d = cW + cE + cS + cN;
-            if (d == (T)0) continue;
-            T acc = sf[sq] + cW * se[sq - 1] + cE * se[sq + 1] + cS * se[sq - SW] + cN * se[sq + SW];
-            se[sq] = acc / d;
+#pragma unroll
+    for (int s = 0; s < 2 * NS; ++s) {
+        const int col = (s & 1) ^ sa.order;           // 0 = red ((i + j) even)
+#pragma unroll
+        for (int r = 0; r < SC_R; ++r) {
+            const int b = b0 + r;
+            if (b < 1 || b > NH - 2 || a < 1 || a > NW - 2) continue;
+            if (((gi0 + a + gj0 + b) & 1) != col || iv[r] == (T)0) continue;
+            const T eW = se[b * SWP + a - 1], eE = se[b * SWP + a + 1];
+            const T eS = (r > 0) ? ev[r > 0 ? r - 1 : 0] : se[(b - 1) * SWP + a];
+            const T eN = (r < SC_R - 1) ? ev[r < SC_R - 1 ? r + 1 : 0] : se[(b + 1) * SWP + a];
+            const T v = iv[r] * (fv[r] + KW(r) * eW + KE(r) * eE + KS(r) * eS + KN(r) * eN);
+            ev[r] = v;
+            se[b * SWP + a] = v;
         }
         __syncthreads();
     }
 
-    // write the interior
-    double dot = 0.0;
-    for (int q = tid; q < TW * TH; q += blockDim.x) {
-        int a = H + q % TW, b = H + q / TW;
-        int i = i0 + q % TW, j = j0 + q / TW;
-        if (i >= L.nx || j >= L.ny) continue;
-        int sq = b * SW + a;
-        e[off + (long long)j * L.P + i] = se[sq];
-        if (sa.flags & (SF_DOT | SF_INIT_DOT)) dot += (double)sf[sq] * (double)se[sq];
+    // write the tile interior, dot product, residual for the restriction
+    const bool restrict_ = (sa.flags & SF_RESTRICT) != 0;
+    DotAcc<T> dot;
+#pragma unroll
+    for (int r = 0; r < SC_R; ++r) {
+        const int b = b0 + r;
+        const int j = gj0 + b;
+        const bool inner = (a >= H && a < H + TW && b >= H && b < H + TH && i < L.nx && j < L.ny);
+        if (inner) {
+            em[(long long)j * L.P + i] = ev[r];
+            if (sa.flags & (SF_DOT | SF_INIT_DOT)) dot.add(fv[r], ev[r]);
+        }
+        if (restrict_) {
+            T res = (T)0;
+            if (inner) {
+                const T eW = se[b * SWP + a - 1], eE = se[b * SWP + a + 1];
+                const T eS = (r > 0) ? ev[r > 0 ? r - 1 : 0] : se[(b - 1) * SWP + a];
+                const T eN = (r < SC_R - 1) ? ev[r < SC_R - 1 ? r + 1 : 0] : se[(b + 1) * SWP + a];
+                const T d = KW(r) + KE(r) + KS(r) + KN(r);
+                res = fv[r] - (d * ev[r] - KW(r) * eW - KE(r) * eE - KS(r) * eS - KN(r) * eN);
+            }
+            sr[b * SWP + a] = res;
+        }
     }
-    if (sa.flags & SF_RESTRICT) {
-        // residual of the interior cells, summed over 2x2 children into the coarse right-hand side
-        for (int q = tid; q < (TW / 2) * (TH / 2); q += blockDim.x) {
-            int qa = q % (TW / 2), qb = q / (TW / 2);
-            int I = (i0 >> 1) + qa, J = (j0 >> 1) + qb;
+    if (restrict_) {
+        __syncthreads();
+        for (int q = tid; q < (TW / 2) * (TH / 2); q += SC_THREADS) {
+            const int qa = q % (TW / 2), qb = q / (TW / 2);
+            const int I = (i0 >> 1) + qa, J = (j0 >> 1) + qb;
             if (2 * I >= L.nx || 2 * J >= L.ny) continue;
-            T sum = (T)0;
-            for (int dj = 0; dj < 2; ++dj)
-                for (int di = 0; di < 2; ++di) {
-                    int a = H + 2 * qa + di, b = H + 2 * qb + dj;
-                    int sq = b * SW + a;
-                    T cW = scw[sq], cE = scw[sq + 1], cS = scs[sq], cN = scs[sq + SW];
-                    T ax = (cW + cE + cS + cN) * se[sq] - cW * se[sq - 1] - cE * se[sq + 1] - cS * se[sq - SW] -
-                           cN * se[sq + SW];
-                    sum += sf[sq] - ax;
-                }
+            const int bb = H + 2 * qb, aa = H + 2 * qa;
+            const T sum = sr[bb * SWP + aa] + sr[bb * SWP + aa + 1] + sr[(bb + 1) * SWP + aa] + sr[(bb + 1) * SWP + aa + 1];
             fc[(long long)m * sa.Sc + (long long)J * sa.Pc + I] = sum;
         }
     }
     if (sa.flags & (SF_DOT | SF_INIT_DOT)) {
-        dot = block_reduce(dot, false);
+        double dtot = dot.total();
         double tot;
         int slot = (sa.flags & SF_INIT_DOT) ? RS_RZA : (((sa.k + 1) & 1) ? RS_RZB : RS_RZA);
-        if (publish_partial(rc, slot, m, dot, false, &tot) && threadIdx.x == 0) {
+        if (publish_partial(rc, slot, m, dtot, false, &tot) && threadIdx.x == 0) {
             rc.red[m].val[slot] = tot;
             if (sa.flags & SF_INIT_DOT) {
                 rc.red[m].val[RS_RZ0] = tot;
@@ -330,6 +350,10 @@ __global__ void __launch_bounds__(256) k_smooth(SmoothArgs sa, const T *__restri
         }
     }
 }
+#undef KW
+#undef KE
+#undef KS
+#undef KN
 
 // ------------------------------------------------------------------------------------------------
 // Coarse levels (lc .. nlev-1): one block per member runs the rest of the V-cycle in shared memory.
@@ -452,11 +476,37 @@ __global__ void k_inner_check(RedCtx rc, MemberCtl *ctl, int k, double rtol2)
 }
 
 // ------------------------------------------------------------------------------------------------
-template <class T>
-static size_t smooth_smem(int nsweep)
+template <class T, bool BIN>
+static void launch_smooth_b(int M, int nsweep, cudaStream_t st, const SmoothArgs &sa, const T *f, const T *ein, T *e,
+                            const T *ec, T *fc, const RedCtx &rc, MemberCtl *ctl, int inner_guard)
 {
-    int H = 2 * nsweep + 1;
-    return sizeof(T) * 4 * (size_t)(TILE_W + 2 * H + 1) * (TILE_H + 2 * H + 1);
+    const Level &L = sa.L;
+    switch (nsweep) {
+    case 1: {
+        dim3 grd(cdiv(L.nx, sc_tw(1)), cdiv(L.ny, sc_th(1)), M);
+        k_smooth<T, 1, BIN><<<grd, SC_THREADS, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+        break;
+    }
+    case 2: {
+        dim3 grd(cdiv(L.nx, sc_tw(2)), cdiv(L.ny, sc_th(2)), M);
+        k_smooth<T, 2, BIN><<<grd, SC_THREADS, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+        break;
+    }
+    default: {
+        dim3 grd(cdiv(L.nx, sc_tw(3)), cdiv(L.ny, sc_th(3)), M);
+        k_smooth<T, 3, BIN><<<grd, SC_THREADS, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+        break;
+    }
+    }
+    count_launches(1);
+}
+
+template <class T>
+static void launch_smooth(int M, int nsweep, cudaStream_t st, const SmoothArgs &sa, const T *f, const T *ein, T *e,
+                          const T *ec, T *fc, const RedCtx &rc, MemberCtl *ctl, int inner_guard)
+{
+    if (sa.L.open) launch_smooth_b<T, true>(M, nsweep, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+    else launch_smooth_b<T, false>(M, nsweep, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
 }
 
 template <class T>
@@ -467,17 +517,15 @@ static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B,
     const T *f0 = (const T *)B.r;
     T *z = (T *)B.z;
     const int lc = pc.ncoarse;
-    auto grid_of = [&](const Level &L) { return dim3(cdiv(L.nx, TILE_W), cdiv(L.ny, TILE_H), M); };
     // descend
     for (int l = 0; l < lc; ++l) {
         const Level &L = lev[l];
         const Level &Lc = lev[l + 1];
         SmoothArgs sa{L, Lc.P, Lc.S, pc.nu_pre, 0, SF_ZERO_INIT | SF_RESTRICT, k};
         const T *f = (l == 0) ? f0 : (const T *)B.lev_f[l];
-        T *e = (l == 0) ? z : (T *)B.lev_e[l];
-        k_smooth<T, TILE_W, TILE_H><<<grid_of(L), TILE_THREADS, smooth_smem<T>(pc.nu_pre), st>>>(
-            sa, f, e, nullptr, (T *)B.lev_f[l + 1], rc, ctl, inner_guard);
-        count_launches(1);
+        T *et = (T *)B.lev_t[l];     // pre-smoothed guess, read by the post-smoothing below
+        launch_smooth<T>(M, pc.nu_pre, st, sa, f, (const T *)nullptr, et, (const T *)nullptr, (T *)B.lev_f[l + 1], rc,
+                         ctl, inner_guard);
     }
     // coarse block
     {
@@ -512,26 +560,27 @@ static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B,
         SmoothArgs sa{L, Lc.P, Lc.S, pc.nu_post, 1, flags, k};
         const T *f = (l == 0) ? f0 : (const T *)B.lev_f[l];
         T *e = (l == 0) ? z : (T *)B.lev_e[l];
-        k_smooth<T, TILE_W, TILE_H><<<grid_of(L), TILE_THREADS, smooth_smem<T>(pc.nu_post), st>>>(
-            sa, f, e, (const T *)B.lev_e[l + 1], nullptr, rc, ctl, inner_guard);
-        count_launches(1);
+        launch_smooth<T>(M, pc.nu_post, st, sa, f, (const T *)B.lev_t[l], e, (const T *)B.lev_e[l + 1], (T *)nullptr,
+                         rc, ctl, inner_guard);
     }
 }
 
-static RedCtx make_ctx(const Partials &pt, int M)
+// One application of the multigrid preconditioner z = M r (level-0 arrays of every member slot).
+template <class TM>
+void launch_vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc,
+                   const Partials &pt, MemberCtl *ctl, cudaStream_t st)
 {
-    RedCtx rc;
-    rc.nblk = pt.nblk;
-    rc.part = pt.part;
-    rc.red = pt.red;
-    rc.M = M;
-    return rc;
+    RedCtx rc = make_ctx(pt, M);
+    vcycle<TM>(g, lev, M, B, pc, rc, ctl, 0, 0, 1, st);
 }
+template void launch_vcycle<float>(const Grid &, const Level *, int, const PoissonBufs &, const PoissonCfg &,
+                                   const Partials &, MemberCtl *, cudaStream_t);
+template void launch_vcycle<double>(const Grid &, const Level *, int, const PoissonBufs &, const PoissonCfg &,
+                                    const Partials &, MemberCtl *, cudaStream_t);
 
 template <class TM>
 void prepare_poisson_kernels()
 {
-    cudaFuncSetAttribute(k_smooth<TM, TILE_W, TILE_H>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     cudaFuncSetAttribute(k_coarse<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
 }
 template void prepare_poisson_kernels<float>();
@@ -547,9 +596,14 @@ void launch_pressure_solve(const Grid &g, const Level *lev, int M, const Poisson
     TM *r = (TM *)B.r, *e = (TM *)B.e, *z = (TM *)B.z, *q = (TM *)B.q;
     TM *pv[2] = {(TM *)B.pv, (TM *)B.pv + (size_t)g.S * M};
     for (int o = 0; o <= pc.max_outer; ++o) {
-        k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, r, e, rc, ctl, pc.rtol_abs,
-                                                          o < pc.max_outer ? 1 : 0);
-        count_launches(1);
+        if (pc.df_outer) {
+            launch_outer_residual_mx(g, L0, pc.mc, M, B.ms, (float *)r, (float *)e, rc, ctl, pc.rtol_abs,
+                                     o < pc.max_outer ? 1 : 0, st);
+        } else {
+            k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, r, e, rc, ctl, pc.rtol_abs,
+                                                              o < pc.max_outer ? 1 : 0);
+            count_launches(1);
+        }
         if (o == pc.max_outer) break;
         vcycle<TM>(g, lev, M, B, pc, rc, ctl, 0, 0, 1, st);
         for (int k = 0; k < pc.max_inner; ++k) {
@@ -561,8 +615,12 @@ void launch_pressure_solve(const Grid &g, const Level *lev, int M, const Poisson
             k_inner_check<<<cdiv(M, 32), 32, 0, st>>>(rc, ctl, k, pc.inner_rtol2);
             count_launches(1);
         }
-        k_outer_update<TM><<<grd, TILE_THREADS, 0, st>>>(g, B.x, e, ctl);
-        count_launches(1);
+        if (pc.df_outer) {
+            launch_outer_update_mx(g, M, B.ms, (const float *)e, ctl, st);
+        } else {
+            k_outer_update<TM><<<grd, TILE_THREADS, 0, st>>>(g, B.x, e, ctl);
+            count_launches(1);
+        }
     }
 }
 
@@ -578,19 +636,25 @@ int launch_poisson_single(int which, const Grid &g, const Level *lev, int M, con
     switch (which) {
     case 1: {
         SmoothArgs sa{L0, L1.P, L1.S, pc.nu_pre, 0, SF_ZERO_INIT | SF_RESTRICT, 0};
-        k_smooth<TM, TILE_W, TILE_H><<<grd, TILE_THREADS, smooth_smem<TM>(pc.nu_pre), st>>>(
-            sa, r, z, nullptr, (TM *)B.lev_f[1], rc, ctl, 0);
-        break;
+        launch_smooth<TM>(M, pc.nu_pre, st, sa, r, (const TM *)nullptr, (TM *)B.lev_t[0], (const TM *)nullptr,
+                          (TM *)B.lev_f[1], rc, ctl, 0);
+        return 0;
     }
     case 2: {
         SmoothArgs sa{L0, L1.P, L1.S, pc.nu_post, 1, SF_PROLONG | SF_DOT, 1};
-        k_smooth<TM, TILE_W, TILE_H><<<grd, TILE_THREADS, smooth_smem<TM>(pc.nu_post), st>>>(
-            sa, r, z, (const TM *)B.lev_e[1], nullptr, rc, ctl, 0);
-        break;
+        launch_smooth<TM>(M, pc.nu_post, st, sa, r, (const TM *)B.lev_t[0], z, (const TM *)B.lev_e[1], (TM *)nullptr,
+                          rc, ctl, 0);
+        return 0;
     }
     case 3: k_spmv<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, z, pv[1], pv[0], q, rc, ctl, 1); break;
     case 4: k_axpy<TM><<<grd, TILE_THREADS, 0, st>>>(g, e, r, pv[0], q, rc, ctl, 1); break;
-    case 5: k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, r, e, rc, ctl, -1.0, 0); break;
+    case 5:
+        if (pc.df_outer) {
+            launch_outer_residual_mx(g, L0, pc.mc, M, B.ms, (float *)r, (float *)e, rc, ctl, -1.0, 0, st);
+            return 0;
+        }
+        k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, r, e, rc, ctl, -1.0, 0);
+        break;
     case 7: {
         PoissonCfg p2 = pc;
         CoarseArgs ca;
