@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark: EnVar gradient iterations of the open-cavity ensemble on GB300.
+
+Workload (quasi-periodic regime): 512 x 256 MAC grid on [-1.2, 2.5] x [-1, 1], Re = 7500,
+N = 32 ensemble perturbations (33 forced Navier-Stokes runs per iteration), each run 20 000
+warm-up + 10 000 window time steps, domain fluctuation-energy cost, prior-preconditioned weight
+update with step 0.5.  One bench step = one EnVar iteration: the 33 forward runs, the costs, the
+EnVar gradient and the weight update, all in the sm_103a kernels of libenvar_gb300.so.  The
+default --warmup 3 --steps 1 plus the end-to-end step make the five EnVar iterations of the
+workload; the JSON line reports the cost after each.
+
+Metric: ensemble cell-updates per second (33 members x 131 072 cells x 30 000 steps per
+iteration, all cells counted, fluid fraction 0.635) and the EnVar iteration time, for the
+batched mixed-precision path; the one-member-at-a-time FP64 GPU path is timed on a bounded
+sample beside it, and the FP64 CPU oracle on the host cores (cpu_baseline).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY, RE, NENS = 512, 256, 7500.0, 32
+N_WARM, N_WINDOW = 20000, 10000
+ALPHA = 0.5
+METRIC = "ensemble cell-updates/s and EnVar iter time, FP32-batched vs FP64-plain"
+WORKLOAD = ("open cavity 512x256 MAC grid, Re 7500, N_ens 32 (33 forced NS runs), 20k warm-up + 10k window "
+            "steps per run, domain fluctuation-energy cost, mixed-precision batched")
+# L2 is 129 MB; the mixed path's resident working set at this workload is ~0.5 GB (inputs larger than L2)
+L2_NOTE = "working set 0.5 GB > 129 MB L2 (no flush needed)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+# distributed helpers (replicas: every rank runs its own independent EnVar problem)
+class Dist:
+    def __init__(self, backend):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+def cpu_baseline(target_s: float, kind: str = "oracle"):
+    """The FP64 CPU oracle as it stands, on the host cores: one thread per member of the workload,
+    each advancing the bench grid for a bounded number of time steps."""
+    import concurrent.futures as cf
+
+    import oracle
+    from paper_2605_23812_gb300 import synth
+    cores = os.cpu_count() or 1
+    threads = min(cores, NENS + 1)
+    P = oracle.cavity_params(NX, NY, RE)
+    u0, v0 = synth.cavity_ic(NX, NY)
+    # calibrate: one member, one step
+    t0 = time.perf_counter()
+    oracle.trajectory(P, u0, v0, 1)
+    t1 = time.perf_counter() - t0
+    steps = max(1, int(target_s / max(t1, 1e-3)))
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda _: oracle.trajectory(P, u0, v0, steps), range(threads)))
+    el = time.perf_counter() - t0
+    cu = threads * NX * NY * steps / el
+    return {"value": cu, "unit": "cell-updates/s", "cores": threads, "kind": kind,
+            "sample": f"{threads} members x {steps} time steps of the 512x256 Re 7500 workload "
+                      f"(FP64, Jacobi-CG to 1e-13), {el:.1f} s; the EnVar iteration is 33 x 30000 steps"}
+
+
+def reference_arm(args, dist):
+    """--impl reference: the oracle on the host cores, each step a bounded sample of the workload."""
+    if dist.rank != 0:
+        return
+    import oracle
+    oracle.build()
+    W, K = args.warmup, args.steps
+    per_step = max(2.0, 60.0 / max(W + K, 1))
+    for _ in range(W):
+        cpu_baseline(per_step / 4)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(K):
+        vals.append(cpu_baseline(per_step))
+    el = time.perf_counter() - t0
+    v = statistics.mean(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * el / max(K, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [NX, NY], "members": NENS + 1,
+                       "time_steps": N_WARM + N_WINDOW},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2605_23812_gb300", "csrc", rec["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec["dram_bytes_per_launch"] if sha == rec["source_sha256_16"] else None
+
+
+def gb300_arm(args, dist):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2605_23812_gb300 as pkg
+    from paper_2605_23812_gb300 import capi, synth
+
+    torch.cuda.set_device(dist.local)
+    cfg = pkg.default_config(NX, NY, Re=RE, n_steps=N_WARM + N_WINDOW, n_window=N_WINDOW, n_members=NENS,
+                             precision=pkg.MIXED, cost_mode=pkg.COST_DOMAIN, div_tol=1e-10)
+    stream = torch.cuda.Stream()
+    ens = pkg.Ensemble(cfg, stream=stream)
+    u0, v0 = synth.cavity_ic(NX, NY, seed=1234 + dist.rank)
+    ens.set_initial_state(u0, v0)
+    M = NENS + 1
+    cells_per_iter = M * NX * NY * (N_WARM + N_WINDOW)
+
+    w_dev = torch.zeros(NENS, dtype=torch.float64, device="cuda")
+    J0_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    J_hist = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ens.step_device(ALPHA, w_dev, J0_dev)
+            J_hist.append(float(J0_dev.item()))
+
+        clocks = ClockSampler(dist.local)
+        dist.barrier()
+        torch.cuda.synchronize()
+        L0 = capi.kernel_launches()
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ens.step_device(ALPHA, w_dev, J0_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        dist.barrier()
+        launches = capi.kernel_launches() - L0
+        t_dev = e0.elapsed_time(e1) / 1e3
+        J_hist.append(float(J0_dev.item()))
+        diag = ens.diagnostics()
+        status = ens.member_status()
+    t = dist.max(t_dev)
+    value = dist.world * cells_per_iter * args.steps / t
+
+    # end to end through the public call with host buffers: w in pinned host memory copied in,
+    # w and J0 read back, every step
+    import ctypes
+    w_host = w_dev.cpu().pin_memory()
+    J0_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    rc = capi.lib().envar_step(ens._h, ALPHA, ctypes.c_void_p(w_host.data_ptr()), ctypes.c_void_p(J0_host.data_ptr()))
+    t_e2e = dist.max(time.perf_counter() - t0)
+    if rc != 0:
+        raise RuntimeError(capi.lib().envar_last_error(ens._h).decode())
+    J_hist.append(float(J0_host[0]))
+    e2e = {"value": dist.world * cells_per_iter / t_e2e, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": 8 * NENS, "d2h_bytes_per_step": 8 * NENS + 8,
+           "envar_iter_s": t_e2e}
+
+    out = None
+    if dist.rank == 0:
+        # roofline of the dominant kernel (level-0 multigrid prolongation + post-smoothing + dot), timed
+        # live on the handle's stream; algorithmic bytes: f, input guess, output (4 B each) and the
+        # coarse correction (1 B per fine cell) per cell and member, plus the open-face bits (1 B per
+        # cell, shared by the members)
+        with torch.cuda.stream(stream):
+            ms = ens.time_kernel(2, 20)
+        algo_bytes = 13.0 * NX * NY * M + 1.0 * NX * NY
+        achieved = algo_bytes / (ms * 1e-3) / 1e9
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except (OSError, ValueError):
+            pass
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "k_smooth<float,2,true> (level-0 prolongation + post-smoothing + r.z)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "traffic": kernel_traffic("k_smooth_l0_post"), "launch_ms": ms}
+        # the plain one-member-at-a-time FP64 GPU path, bounded sample (1 member x 600 steps)
+        cfg64 = pkg.default_config(NX, NY, Re=RE, n_steps=600, n_window=300, n_members=0,
+                                   precision=pkg.FP64_PLAIN, div_tol=1e-10)
+        ens.close()
+        e64 = pkg.Ensemble(cfg64, stream=stream)
+        e64.set_initial_state(u0, v0)
+        e64.forward_ensemble(np.zeros(0))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e64.forward_ensemble(np.zeros(0))
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / 1e3
+        plain = NX * NY * 600 / t64
+        e64.close()
+        cb = cpu_baseline(args.cpu_sample_s)
+        out = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64 (mixed)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [NX, NY], "Re": RE, "members": M,
+                       "time_steps": N_WARM + N_WINDOW, "precision": "mixed (FP32 stencil/MG, df64 state)",
+                       "l2": L2_NOTE, "parallelism": "replicas" if dist.world > 1 else "1 GPU"},
+            "envar_iter_s": t / args.steps, "envar_iters_per_hour": 3600.0 * args.steps / t,
+            "fp64_plain": {"value": plain, "unit": "cell-updates/s", "sample": "1 member x 600 steps, FP64_PLAIN",
+                           "envar_iter_s_extrapolated": cells_per_iter / plain},
+            "speedup_vs_fp64_plain": value / dist.world / plain,
+            "J_history": J_hist, "energy_reduction": (J_hist[-1] / J_hist[0]) if J_hist and J_hist[0] else None,
+            "max_div": diag["max_div"], "member_status_nonzero": int((status != 0).sum()),
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+        }
+    else:
+        ens.close()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # rank 0 alone runs the oracle; other ranks exit without work (no process group needed)
+        reference_arm(args, type("R", (), {"rank": int(os.environ.get("RANK", "0"))})())
+        return
+    dist = Dist("nccl")
+    try:
+        out = gb300_arm(args, dist)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -152,6 +152,10 @@ int envar_gradient(envar_handle h, double *g_host, double *df_dev);
  * total cost J(w) = J_obs(member 0) + J_prior before the update. */
 int envar_step(envar_handle h, double alpha, double *w_inout_host, double *J0_out_host);
 
+/* envar_step with device-resident w_inout_dev (N doubles) and J0_out_dev (nullable, 1 double):
+ * no host copy of the step's inputs or results. */
+int envar_step_device(envar_handle h, double alpha, double *w_inout_dev, double *J0_out_dev);
+
 /* Run ONE member with a given control vector f (n_ctrl doubles, device) over
  * n_steps and return its observation cost (host).  Member slot 0 is used. */
 int envar_forward_control(envar_handle h, const double *f_dev, double *J_host);

@@ -70,6 +70,7 @@ def lib():
         "envar_cost": [H, c_void_p, c_void_p],
         "envar_gradient": [H, c_void_p, c_void_p],
         "envar_step": [H, c_double, c_void_p, c_void_p],
+        "envar_step_device": [H, c_double, c_void_p, c_void_p],
         "envar_forward_control": [H, c_void_p, c_void_p],
         "envar_member_status": [H, c_void_p],
         "envar_get_state": [H, c_int, c_void_p, c_void_p, c_void_p],
@@ -198,6 +199,10 @@ class Ensemble:
         J0 = np.zeros(1)
         self._check(lib().envar_step(self._h, float(alpha), _np_ptr(w), _np_ptr(J0)), "envar_step")
         return w, float(J0[0])
+
+    def step_device(self, alpha, w_dev, J0_dev=None):
+        """envar_step on device-resident tensors (w_dev updated in place)."""
+        self._check(lib().envar_step_device(self._h, float(alpha), _ptr(w_dev), _ptr(J0_dev)), "envar_step_device")
 
     def forward_control(self, f):
         ft = self._dev(f, (self.n_ctrl,))

@@ -792,6 +792,25 @@ extern "C" int envar_step(envar_handle h, double alpha, double *w_inout, double 
     return ENVAR_OK;
 }
 
+extern "C" int envar_step_device(envar_handle h, double alpha, double *w_inout, double *J0_out)
+{
+    if (!h || !w_inout) return ENVAR_EINVAL;
+    if (!h->have_ic) { set_err(h, "envar_step_device: no initial state"); return ENVAR_ESTATE; }
+    if (h->N < 1) { set_err(h, "envar_step_device: ensemble is empty"); return ENVAR_ESTATE; }
+    CK(cudaMemcpyAsync(h->d_w, w_inout, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
+    int rc = forward_members(h);
+    if (rc) return rc;
+    compute_gradient(h);
+    if (J0_out) {
+        const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js : h->d_Jd;
+        launch_total_cost(src, h->d_jprior, J0_out, h->st);
+    }
+    launch_update_w(h->N, h->d_w, h->d_g, alpha / std::max(h->N - 1, 1), h->st);
+    CK(cudaMemcpyAsync(w_inout, h->d_w, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
 extern "C" int envar_forward_control(envar_handle h, const double *f, double *J)
 {
     if (!h || !f) return ENVAR_EINVAL;

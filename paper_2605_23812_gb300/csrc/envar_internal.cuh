@@ -296,5 +296,6 @@ void launch_scalar_gradient(int N, const double *J, const double *w, double eps,
 void launch_df(int N, int n_ctrl, const double *E, const double *g, double scale, double *df, cudaStream_t st);
 void launch_update_w(int N, double *w, const double *g, double step, cudaStream_t st);
 void launch_d2f(long long n, const double *a, float *b, cudaStream_t st);
+void launch_total_cost(const double *J, const double *jp, double *out, cudaStream_t st);
 
 } // namespace envar

@@ -1,0 +1,52 @@
+"""Profiling driver: run time steps of the bench workload with the hot kernels in an NVTX range.
+
+    python -m paper_2605_23812_gb300.profile_step [--steps 20] [--kernels 1,2]
+
+Builds the library, runs one forward evaluation of the 512x256 / Re 7500 / 33-member ensemble
+over --steps time steps to warm up (graph capture), then a second one inside the NVTX range
+"timed" (for ncu --nvtx --nvtx-include "timed/").  --kernels additionally launches the listed
+hot kernels standalone (envar_time_kernel, one launch each) inside the range "kernels", for
+targeted captures of a single launch.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--members", type=int, default=32)
+    ap.add_argument("--kernels", default="")
+    args = ap.parse_args()
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2605_23812_gb300 as pkg
+    from paper_2605_23812_gb300 import synth
+    cfg = pkg.default_config(512, 256, Re=7500.0, n_steps=args.steps, n_window=max(1, args.steps // 2),
+                             n_members=args.members, precision=pkg.MIXED)
+    ens = pkg.Ensemble(cfg, stream=torch.cuda.Stream())
+    ens.set_initial_state(*synth.cavity_ic(512, 256))
+    w = synth.weights(args.members)
+    ens.forward_ensemble(w)
+    torch.cuda.nvtx.range_push("timed")
+    ens.forward_ensemble(w)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    if args.kernels:
+        torch.cuda.nvtx.range_push("kernels")
+        for k in [int(x) for x in args.kernels.split(",")]:
+            print(k, ens.time_kernel(k, 1))
+        torch.cuda.nvtx.range_pop()
+    print("diagnostics", ens.diagnostics())
+    ens.close()
+
+
+if __name__ == "__main__":
+    main()
