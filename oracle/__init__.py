@@ -112,6 +112,8 @@ def lib():
                                    ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
         "orc_gradient_from_costs": (None, [c_int, _dp, _dp, c_double, _dp, ctypes.POINTER(c_double)]),
         "orc_sensor_gradient": (None, [c_int, c_int, _dp, c_double, _dp, _dp]),
+        "orc_adjoint_gradient": (c_int, [P, _dp, _dp, _dp, _dp, c_int, c_int, ctypes.POINTER(c_double), _dp, _dp]),
+        "orc_faces_to_control": (None, [P, _dp, _dp, _dp, _dp]),
         "orc_envar_gradient": (c_int, [P, _dp, _dp, _dp, c_int, c_int, _dp, _dp, c_double,
                                        c_int, c_int, c_int, c_int, _dp, _dp,
                                        ctypes.POINTER(c_double), c_void_p]),
@@ -381,6 +383,29 @@ def sensor_gradient(series, w, eps: float):
     g = np.zeros(N)
     lib().orc_sensor_gradient(N, series.shape[1], series.reshape(-1), eps,
                               np.ascontiguousarray(w, dtype=np.float64), g)
+    return g
+
+
+def adjoint_gradient(P: Params, u0, v0, n_steps: int, n_window: int, fu=None, fv=None):
+    """Discrete adjoint (Sec. 3.2, Eq. adjoint_discrete / gradient_forcing): DOMAIN cost J and dJ/dF on faces."""
+    su, sv, _ = shapes(P)
+    fu = np.zeros(su) if fu is None else np.ascontiguousarray(fu, dtype=np.float64).reshape(su)
+    fv = np.zeros(sv) if fv is None else np.ascontiguousarray(fv, dtype=np.float64).reshape(sv)
+    gu, gv, J = np.zeros(su), np.zeros(sv), c_double()
+    rc = lib().orc_adjoint_gradient(ctypes.byref(P), np.ascontiguousarray(u0, dtype=np.float64).reshape(su),
+                                    np.ascontiguousarray(v0, dtype=np.float64).reshape(sv), fu, fv, int(n_steps),
+                                    int(n_window), ctypes.byref(J), gu, gv)
+    if rc != 0:
+        raise RuntimeError(f"oracle adjoint failed ({rc})")
+    return J.value, gu, gv
+
+
+def faces_to_control(P: Params, gu, gv, region=CAVITY_REGION):
+    """Transpose of control_to_faces: control-space gradient from a face gradient."""
+    n = len(control_cells(P, region)[0])
+    g = np.zeros(2 * n)
+    lib().orc_faces_to_control(ctypes.byref(P), np.asarray(region, dtype=np.float64),
+                               np.ascontiguousarray(gu, dtype=np.float64), np.ascontiguousarray(gv, dtype=np.float64), g)
     return g
 
 

@@ -1220,3 +1220,319 @@ int orc_envar_gradient(const orc_params *P, const double *region, const double *
     orc_gradient_from_costs(N, J, w, eps, g, J_prior);
     return 0;
 }
+
+/* ------------------------------- adjoint ------------------------------- */
+/* Discrete adjoint of the time stepper above (Sec. 3.2, Eq. adjoint_discrete and
+ * Eq. gradient_forcing in their discrete form): the gradient of the DOMAIN observation cost with
+ * respect to a steady face forcing F (a vector on the unknown faces).
+ *
+ * One step maps X^n = (u^n on unknown and outlet faces) and the stored tendency R^{n-1} to
+ *   v      = u^n + dt (c1 R(X^n) + c0 R^{n-1}) + dt F                (unknown faces)
+ *   u_b'   = C(X^n)     (convective outlet + uniform flux shift)
+ *   u^{n+1} = v - G psi,  L psi = D(v, u_b')    (projection; the p^n term drops out of u^{n+1})
+ * so with mu = adjoint of u^{n+1} on unknown faces and nu on outlet faces:
+ *   psi'   = L^{-1} D_u mu,  wbar = mu - G psi',  ubbar = nu + D_b^T psi'  (D_b: outlet columns)
+ * and the adjoint of u^n collects wbar, J_R^T Rbar with Rbar = dt c1 wbar + dt c0' wbar' (the
+ * next step's AB2 use of R^n), C^T ubbar, and the cost gradient at the window samples.  The
+ * forcing gradient is dJ/dF = sum_n dt wbar.  Tendency transposes are taken by reverse mode of
+ * explicit_rhs on the ghost-padded arrays, then the adjoint of the ghost filling. */
+
+/* adjoint of fill_ghosts: padded adjoints -> compact adjoints (accumulated) */
+static void fill_ghosts_adjoint(orc_sim *s, double *Ub, double *Vb, double *lu, double *lv)
+{
+    int nx = s->nx, ny = s->ny;
+#define UB(i, j) (Ub[(size_t)((j) + 1) * (size_t)(nx + 3) + (size_t)((i) + 1)])
+#define VB(i, j) (Vb[(size_t)((j) + 1) * (size_t)(nx + 2) + (size_t)((i) + 1)])
+    /* reverse order of fill_ghosts: y edges, x edges, buried faces, interior copy */
+    for (int i = nx; i >= -1; --i) {
+        if (s->P.bc_y == 1) {
+            VB(i, 1) += VB(i, ny + 1); VB(i, ny + 1) = 0.0;
+            VB(i, ny - 1) += VB(i, -1); VB(i, -1) = 0.0;
+            VB(i, 0) += VB(i, ny); VB(i, ny) = 0.0;
+        } else {
+            VB(i, -1) = 0.0; VB(i, ny + 1) = 0.0;
+        }
+    }
+    for (int i = nx + 1; i >= -1; --i) {
+        if (s->P.bc_y == 1) {
+            UB(i, 0) += UB(i, ny); UB(i, ny) = 0.0;
+            UB(i, ny - 1) += UB(i, -1); UB(i, -1) = 0.0;
+        } else if (s->P.bc_y == 2) {
+            UB(i, ny - 1) -= UB(i, ny); UB(i, ny) = 0.0;
+            UB(i, 0) -= UB(i, -1); UB(i, -1) = 0.0;
+        } else {
+            UB(i, ny - 1) += UB(i, ny); UB(i, ny) = 0.0;
+            UB(i, 0) -= UB(i, -1); UB(i, -1) = 0.0;
+        }
+    }
+    for (int j = ny; j >= 0; --j) {
+        if (s->P.bc_x == 1) {
+            VB(0, j) += VB(nx, j); VB(nx, j) = 0.0;
+            VB(nx - 1, j) += VB(-1, j); VB(-1, j) = 0.0;
+        } else {
+            VB(nx - 1, j) += VB(nx, j); VB(nx, j) = 0.0;
+            VB(0, j) -= VB(-1, j); VB(-1, j) = 0.0;
+        }
+    }
+    for (int j = ny - 1; j >= 0; --j) {
+        if (s->P.bc_x == 1) {
+            UB(1, j) += UB(nx + 1, j); UB(nx + 1, j) = 0.0;
+            UB(nx - 1, j) += UB(-1, j); UB(-1, j) = 0.0;
+            UB(0, j) += UB(nx, j); UB(nx, j) = 0.0;
+        } else {
+            UB(-1, j) = 0.0; UB(nx + 1, j) = 0.0;
+        }
+    }
+    for (int j = ny; j >= 0; --j)
+        for (int i = nx - 1; i >= 0; --i) {
+            if (s->vk[IV(s, i, j)] != FK_SOLID) continue;
+            int rt = (i + 1 < nx) && s->vk[IV(s, i + 1, j)] == FK_UNKNOWN;
+            int lt = (i - 1 >= 0) && s->vk[IV(s, i - 1, j)] == FK_UNKNOWN;
+            if (rt) lv[IV(s, i + 1, j)] -= VB(i, j);
+            else if (lt) lv[IV(s, i - 1, j)] -= VB(i, j);
+            VB(i, j) = 0.0;
+        }
+    for (int j = ny - 1; j >= 0; --j)
+        for (int i = nx; i >= 0; --i) {
+            if (s->uk[IU(s, i, j)] != FK_SOLID) continue;
+            int up = (j + 1 < ny) && s->uk[IU(s, i, j + 1)] == FK_UNKNOWN;
+            int dn = (j - 1 >= 0) && s->uk[IU(s, i, j - 1)] == FK_UNKNOWN;
+            if (up) lu[IU(s, i, j + 1)] -= UB(i, j);
+            else if (dn) lu[IU(s, i, j - 1)] -= UB(i, j);
+            UB(i, j) = 0.0;
+        }
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i) lu[IU(s, i, j)] += UB(i, j);
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) lv[IV(s, i, j)] += VB(i, j);
+#undef UB
+#undef VB
+}
+
+/* lu, lv += (dR/du)^T Rbu, (dR/dv)^T Rbv at the state held in s (reverse mode of explicit_rhs) */
+static void explicit_rhs_adjoint(orc_sim *s, const double *Rbu, const double *Rbv, double *lu, double *lv)
+{
+    int nx = s->nx, ny = s->ny;
+    double dx = s->dx, dy = s->dy, nu = s->nu;
+    int adv = s->P.advection;
+    size_t nug = (size_t)(nx + 3) * (ny + 2), nvg = (size_t)(nx + 2) * (ny + 3);
+    double *Ub = (double *)xcalloc(nug, sizeof(double)), *Vb = (double *)xcalloc(nvg, sizeof(double));
+#define UB(i, j) (Ub[(size_t)((j) + 1) * (size_t)(nx + 3) + (size_t)((i) + 1)])
+#define VB(i, j) (Vb[(size_t)((j) + 1) * (size_t)(nx + 2) + (size_t)((i) + 1)])
+    fill_ghosts(s, s->u, s->v);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+            size_t k = IU(s, i, j);
+            if (s->uk[k] != FK_UNKNOWN) continue;
+            double rb = Rbu[k];
+            if (rb == 0.0) continue;
+            double uc = UG(s, i, j), ue = UG(s, i + 1, j), uw = UG(s, i - 1, j);
+            double un = UG(s, i, j + 1), us = UG(s, i, j - 1);
+            /* diffusion */
+            double cxx = nu / (dx * dx), cyy = nu / (dy * dy);
+            UB(i, j) += rb * (-2.0 * cxx - 2.0 * cyy);
+            UB(i + 1, j) += rb * cxx; UB(i - 1, j) += rb * cxx;
+            UB(i, j + 1) += rb * cyy; UB(i, j - 1) += rb * cyy;
+            if (adv) {
+                /* R = -A: A = (fe^2 - fw^2)/dx + (un_c vn_c - us_c vs_c)/dy */
+                double fe = 0.5 * (uc + ue), fw = 0.5 * (uw + uc);
+                double un_c = 0.5 * (uc + un), vn_c = 0.5 * (VG(s, i - 1, j + 1) + VG(s, i, j + 1));
+                double us_c = 0.5 * (us + uc), vs_c = 0.5 * (VG(s, i - 1, j) + VG(s, i, j));
+                double a = -rb;   /* adjoint of A */
+                double bfe = a * 2.0 * fe / dx, bfw = -a * 2.0 * fw / dx;
+                double bun = a * vn_c / dy, bvn = a * un_c / dy;
+                double bus = -a * vs_c / dy, bvs = -a * us_c / dy;
+                UB(i, j) += 0.5 * bfe + 0.5 * bfw + 0.5 * bun + 0.5 * bus;
+                UB(i + 1, j) += 0.5 * bfe;
+                UB(i - 1, j) += 0.5 * bfw;
+                UB(i, j + 1) += 0.5 * bun;
+                UB(i, j - 1) += 0.5 * bus;
+                VB(i - 1, j + 1) += 0.5 * bvn; VB(i, j + 1) += 0.5 * bvn;
+                VB(i - 1, j) += 0.5 * bvs; VB(i, j) += 0.5 * bvs;
+            }
+        }
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t k = IV(s, i, j);
+            if (s->vk[k] != FK_UNKNOWN) continue;
+            double rb = Rbv[k];
+            if (rb == 0.0) continue;
+            double vc = VG(s, i, j), ve = VG(s, i + 1, j), vw = VG(s, i - 1, j);
+            double vn = VG(s, i, j + 1), vs = VG(s, i, j - 1);
+            double cxx = nu / (dx * dx), cyy = nu / (dy * dy);
+            VB(i, j) += rb * (-2.0 * cxx - 2.0 * cyy);
+            VB(i + 1, j) += rb * cxx; VB(i - 1, j) += rb * cxx;
+            VB(i, j + 1) += rb * cyy; VB(i, j - 1) += rb * cyy;
+            if (adv) {
+                /* A = (ue_c ve_c - uw_c vw_c)/dx + (fn^2 - fs^2)/dy */
+                double ue_c = 0.5 * (UG(s, i + 1, j - 1) + UG(s, i + 1, j)), ve_c = 0.5 * (vc + ve);
+                double uw_c = 0.5 * (UG(s, i, j - 1) + UG(s, i, j)), vw_c = 0.5 * (vw + vc);
+                double fn = 0.5 * (vc + vn), fs = 0.5 * (vs + vc);
+                double a = -rb;
+                double bue = a * ve_c / dx, bve = a * ue_c / dx;
+                double buw = -a * vw_c / dx, bvw = -a * uw_c / dx;
+                double bfn = a * 2.0 * fn / dy, bfs = -a * 2.0 * fs / dy;
+                UB(i + 1, j - 1) += 0.5 * bue; UB(i + 1, j) += 0.5 * bue;
+                UB(i, j - 1) += 0.5 * buw; UB(i, j) += 0.5 * buw;
+                VB(i, j) += 0.5 * bve + 0.5 * bvw + 0.5 * bfn + 0.5 * bfs;
+                VB(i + 1, j) += 0.5 * bve;
+                VB(i - 1, j) += 0.5 * bvw;
+                VB(i, j + 1) += 0.5 * bfn;
+                VB(i, j - 1) += 0.5 * bfs;
+            }
+        }
+#undef UB
+#undef VB
+    fill_ghosts_adjoint(s, Ub, Vb, lu, lv);
+    free(Ub); free(Vb);
+}
+
+/* Adjoint gradient of the DOMAIN cost with respect to the face forcing (fu, fv), and the cost.
+ * gu / gv: dJ/dF on unknown faces (zero elsewhere).  Stores all n_steps + 1 states. */
+int orc_adjoint_gradient(const orc_params *P, const double *u0, const double *v0, const double *fu, const double *fv,
+                         int n_steps, int n_window, double *J_out, double *gu, double *gv)
+{
+    if (P->bc_x != 0 || n_window < 1 || n_window > n_steps) return -1;
+    orc_sim *s = orc_create(P);
+    if (!s) return -2;
+    int nx = s->nx, ny = s->ny;
+    size_t nc = (size_t)nx * ny, nu_ = (size_t)(nx + 1) * ny, nv_ = (size_t)nx * (ny + 1);
+    double *U = (double *)xcalloc(nu_ * (size_t)(n_steps + 1), sizeof(double));
+    double *V = (double *)xcalloc(nv_ * (size_t)(n_steps + 1), sizeof(double));
+    orc_set_state(s, u0, v0, NULL);
+    orc_set_face_forcing(s, fu, fv);
+    memcpy(U, s->u, nu_ * sizeof(double));
+    memcpy(V, s->v, nv_ * sizeof(double));
+    for (int n = 0; n < n_steps; ++n) {
+        step_once(s);
+        memcpy(U + nu_ * (size_t)(n + 1), s->u, nu_ * sizeof(double));
+        memcpy(V + nv_ * (size_t)(n + 1), s->v, nv_ * sizeof(double));
+    }
+    /* window means and the cost (two-pass on the stored samples) */
+    int k0 = n_steps - n_window + 1;
+    double *mu = (double *)xcalloc(nc, sizeof(double)), *mv = (double *)xcalloc(nc, sizeof(double));
+    for (int k = k0; k <= n_steps; ++k) {
+        const double *u = U + nu_ * (size_t)k, *v = V + nv_ * (size_t)k;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = IC(s, i, j);
+                if (!s->F[c]) continue;
+                mu[c] += 0.5 * (u[IU(s, i, j)] + u[IU(s, i + 1, j)]);
+                mv[c] += 0.5 * (v[IV(s, i, j)] + v[IV(s, i, j + 1)]);
+            }
+    }
+    for (size_t c = 0; c < nc; ++c) { mu[c] /= n_window; mv[c] /= n_window; }
+    double J = 0.0, wgt = s->dx * s->dy / (double)n_window;
+    for (int k = k0; k <= n_steps; ++k) {
+        const double *u = U + nu_ * (size_t)k, *v = V + nv_ * (size_t)k;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = IC(s, i, j);
+                if (!s->F[c]) continue;
+                double a = 0.5 * (u[IU(s, i, j)] + u[IU(s, i + 1, j)]) - mu[c];
+                double b = 0.5 * (v[IV(s, i, j)] + v[IV(s, i, j + 1)]) - mv[c];
+                J += 0.5 * wgt * (a * a + b * b);
+            }
+    }
+    /* reverse sweep */
+    double *lu = (double *)xcalloc(nu_, sizeof(double)), *lv = (double *)xcalloc(nv_, sizeof(double));
+    double *wu = (double *)xcalloc(nu_, sizeof(double)), *wv = (double *)xcalloc(nv_, sizeof(double));
+    double *cu = (double *)xcalloc(nu_, sizeof(double)), *cv = (double *)xcalloc(nv_, sizeof(double));
+    double *Rbu = (double *)xcalloc(nu_, sizeof(double)), *Rbv = (double *)xcalloc(nv_, sizeof(double));
+    double *psi = (double *)xcalloc(nc, sizeof(double)), *rhs = (double *)xcalloc(nc, sizeof(double));
+    double *ubb = (double *)xcalloc((size_t)ny, sizeof(double));
+    double dt = s->P.dt, kap = dt * s->P.conv_speed / s->dx;
+    for (size_t k = 0; k < nu_; ++k) gu[k] = 0.0;
+    for (size_t k = 0; k < nv_; ++k) gv[k] = 0.0;
+    int nout = 0;
+    for (int j = 0; j < ny; ++j) nout += (s->uk[IU(s, nx, j)] == FK_OUTLET);
+    for (int n = n_steps; n >= 0; --n) {
+        /* cost gradient at sample n: d/du_face of sum_c wgt/2 |u_c - mean|^2 */
+        if (n >= k0) {
+            const double *u = U + nu_ * (size_t)n, *v = V + nv_ * (size_t)n;
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    size_t c = IC(s, i, j);
+                    if (!s->F[c]) continue;
+                    double a = 0.5 * (u[IU(s, i, j)] + u[IU(s, i + 1, j)]) - mu[c];
+                    double b = 0.5 * (v[IV(s, i, j)] + v[IV(s, i, j + 1)]) - mv[c];
+                    lu[IU(s, i, j)] += 0.5 * wgt * a; lu[IU(s, i + 1, j)] += 0.5 * wgt * a;
+                    lv[IV(s, i, j)] += 0.5 * wgt * b; lv[IV(s, i, j + 1)] += 0.5 * wgt * b;
+                }
+        }
+        if (n == 0) break;
+        /* reverse the step (n-1) -> n */
+        int m = n - 1;
+        double c1 = (m == 0) ? 1.0 : 1.5, c0 = (m == 0) ? 0.0 : -0.5;
+        /* psi = L^{-1} D_u mu  <=>  (-L) psi = -D_u mu (mu on unknown faces only) */
+        for (size_t k = 0; k < nu_; ++k) wu[k] = (s->uk[k] == FK_UNKNOWN) ? lu[k] : 0.0;
+        for (size_t k = 0; k < nv_; ++k) wv[k] = (s->vk[k] == FK_UNKNOWN) ? lv[k] : 0.0;
+        divergence(s, wu, wv, -1.0, rhs);
+        remove_mean(s, rhs);
+        for (size_t k = 0; k < nc; ++k) psi[k] = 0.0;
+        pcg_solve(s, rhs, psi);
+        /* wbar = mu - G psi (unknown faces) */
+        grad_correct(s, wu, wv, psi, 1.0);
+        /* outlet: ubbar_j = nu_j + psi(nx-1, j)/dx */
+        for (int j = 0; j < ny; ++j)
+            ubb[j] = (s->uk[IU(s, nx, j)] == FK_OUTLET) ? lu[IU(s, nx, j)] + psi[IC(s, nx - 1, j)] / s->dx : 0.0;
+        /* Rbar = dt c1 wbar + carry; carry = dt c0 wbar; forcing gradient */
+        for (size_t k = 0; k < nu_; ++k) {
+            Rbu[k] = dt * c1 * wu[k] + cu[k];
+            cu[k] = dt * c0 * wu[k];
+            gu[k] += dt * wu[k];
+        }
+        for (size_t k = 0; k < nv_; ++k) {
+            Rbv[k] = dt * c1 * wv[k] + cv[k];
+            cv[k] = dt * c0 * wv[k];
+            gv[k] += dt * wv[k];
+        }
+        /* lambda^m = wbar + J_R(X^m)^T Rbar + C^T ubbar */
+        for (size_t k = 0; k < nu_; ++k) lu[k] = wu[k];
+        for (size_t k = 0; k < nv_; ++k) lv[k] = wv[k];
+        memcpy(s->u, U + nu_ * (size_t)m, nu_ * sizeof(double));
+        memcpy(s->v, V + nv_ * (size_t)m, nv_ * sizeof(double));
+        explicit_rhs_adjoint(s, Rbu, Rbv, lu, lv);
+        /* C: ub_j = (1-kap) u_nx,j + kap u_nx-1,j + shift, shift = (Qin/dy - sum_k ub'_k)/nout */
+        double sb = 0.0;
+        for (int j = 0; j < ny; ++j) sb += ubb[j];
+        for (int j = 0; j < ny; ++j) {
+            if (s->uk[IU(s, nx, j)] != FK_OUTLET) continue;
+            double bp = ubb[j] - sb / nout;
+            lu[IU(s, nx, j)] += (1.0 - kap) * bp;
+            lu[IU(s, nx - 1, j)] += kap * bp;
+        }
+    }
+    if (J_out) *J_out = J;
+    free(U); free(V); free(mu); free(mv); free(lu); free(lv); free(wu); free(wv); free(cu); free(cv);
+    free(Rbu); free(Rbv); free(psi); free(rhs); free(ubb);
+    orc_destroy(s);
+    return 0;
+}
+
+/* Control-space gradient: g[c] = P^T dJ/dF, the transpose of orc_control_to_faces. */
+void orc_faces_to_control(const orc_params *P, const double *region, const double *gu, const double *gv, double *g)
+{
+    int nx = P->nx, ny = P->ny;
+    int nc = orc_control_cells(P, region, NULL, NULL);
+    int *ci = (int *)xcalloc((size_t)nc, sizeof(int)), *cj = (int *)xcalloc((size_t)nc, sizeof(int));
+    orc_control_cells(P, region, ci, cj);
+    orc_sim *s = orc_create(P);
+    for (int q = 0; q < nc; ++q) {
+        int i = ci[q], j = cj[q];
+        double ax = 0.0, ay = 0.0;
+        for (int f = i; f <= i + 1; ++f) {
+            size_t k = (size_t)j * (nx + 1) + f;
+            if (s->uk[k] == FK_UNKNOWN) ax += 0.5 * gu[k];
+        }
+        for (int f = j; f <= j + 1; ++f) {
+            size_t k = (size_t)f * nx + i;
+            if (s->vk[k] == FK_UNKNOWN) ay += 0.5 * gv[k];
+        }
+        g[q] = ax;
+        g[nc + q] = ay;
+    }
+    orc_destroy(s);
+    free(ci); free(cj);
+    (void)ny;
+}

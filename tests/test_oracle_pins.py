@@ -525,3 +525,47 @@ def test_sensors_exact_for_bilinear_field():
         x = 0.2 * (q + 1)
         assert got[2 * q] == pytest.approx(0.3 + 0.7 * x, abs=1e-14)
         assert got[2 * q + 1] == pytest.approx(-0.2 + 0.5 * x, abs=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Discrete adjoint (Sec. 3.2, Eq. adjoint_discrete / gradient_forcing): brute force.
+# --------------------------------------------------------------------------
+def test_adjoint_gradient_matches_central_differences():
+    """The oracle's reverse sweep gives dJ/dF for the DOMAIN cost; directional derivatives along
+    random face-forcing directions must equal central differences of the oracle's own cost."""
+    P = oracle.cavity_params(32, 16, 300.0)
+    u0, v0 = synth.cavity_ic(32, 16)
+    rng = np.random.default_rng(0)
+    s = oracle.Sim(P)
+    uk, vk = s.face_kinds()
+    fu = 0.05 * rng.standard_normal(uk.shape) * (uk == oracle.FK_UNKNOWN)
+    fv = 0.05 * rng.standard_normal(vk.shape) * (vk == oracle.FK_UNKNOWN)
+    n_steps, n_window = 60, 30
+    J, gu, gv = oracle.adjoint_gradient(P, u0, v0, n_steps, n_window, fu, fv)
+    # J is the same cost the forward two-pass evaluation reports
+    assert J == pytest.approx(oracle.member_run(P, u0, v0, n_steps, n_window, fu, fv)["J_domain"], rel=1e-12)
+    assert np.all(gu[uk != oracle.FK_UNKNOWN] == 0) and np.all(gv[vk != oracle.FK_UNKNOWN] == 0)
+    h = 1e-4
+    for _ in range(3):
+        du = rng.standard_normal(uk.shape) * (uk == oracle.FK_UNKNOWN)
+        dv = rng.standard_normal(vk.shape) * (vk == oracle.FK_UNKNOWN)
+        Jp = oracle.adjoint_gradient(P, u0, v0, n_steps, n_window, fu + h * du, fv + h * dv)[0]
+        Jm = oracle.adjoint_gradient(P, u0, v0, n_steps, n_window, fu - h * du, fv - h * dv)[0]
+        fd = (Jp - Jm) / (2 * h)
+        ad = (gu * du).sum() + (gv * dv).sum()
+        assert abs(ad - fd) <= 1e-5 * abs(fd), (ad, fd)
+
+
+def test_faces_to_control_is_transpose_of_control_to_faces():
+    P = oracle.cavity_params(32, 16, 1000.0)
+    rng = np.random.default_rng(1)
+    n = len(oracle.control_cells(P)[0])
+    f = rng.standard_normal(2 * n)
+    s = oracle.Sim(P)
+    uk, vk = s.face_kinds()
+    gu = rng.standard_normal(uk.shape)
+    gv = rng.standard_normal(vk.shape)
+    fu, fv = oracle.control_to_faces(P, f)
+    lhs = (fu * gu).sum() + (fv * gv).sum()
+    rhs = f @ oracle.faces_to_control(P, gu, gv)
+    assert lhs == pytest.approx(rhs, rel=1e-13)
