@@ -203,6 +203,36 @@ int envar_time_kernel(envar_handle h, int which, int reps, double *ms_per_launch
  * solver's work vectors of every member slot. */
 int envar_apply_preconditioner(envar_handle h, const double *r_dev, double *z_dev);
 
+/* Reference gradient by the discrete adjoint (Sec. 3.2, Eq. adjoint_discrete and
+ * Eq. gradient_forcing, in their discrete form): the exact gradient of the DOMAIN cost J(f) of one
+ * forward run from the handle's initial state, with the steady forcing f on the control cells,
+ * with respect to f.  The reverse sweep transposes every step of the FP64 stepper -- AB2
+ * predictor with its boundary rules, convective outlet with the flux shift, projection (one
+ * adjoint Poisson solve per step, the same multigrid-preconditioned CG) -- and accumulates
+ * dJ/dF = sum_n dt lambda_n on the forced faces, then maps it to the control cells (each cell
+ * takes half of each of its forced faces, the transpose of the forcing map).
+ * f_dev: n_ctrl float64 on the device, [fx over control cells | fy over control cells], the layout
+ * of one column of E.  gf_dev: n_ctrl float64 on the device (written).  J_host: the cost, or NULL.
+ * max_snapshots >= 1: forward states kept on the device (about 6 (nx+1)(ny+1) doubles each); with
+ * fewer than n_steps, the binomial checkpoint schedule recomputes the forward in between (at most
+ * r forward passes for n_steps <= C(max_snapshots + r, r)).  Needs an FP64 handle
+ * (ENVAR_FP64_PLAIN or ENVAR_FP64_BATCHED), the DOMAIN cost, n_window >= 1 and an initial state.
+ * Uses and overwrites member slot 0 (state, Welford planes, cost).  Errors: ENVAR_EINVAL for a
+ * wrong handle kind or argument, ENVAR_ENOMEM when the checkpoints do not fit, ENVAR_ESTATE when a
+ * forward step or an adjoint solve failed (non-finite state, CFL, unconverged solve). */
+int envar_adjoint_gradient(envar_handle h, const double *f_dev, double *gf_dev, int max_snapshots, double *J_host);
+
+/* Counters of the last envar_adjoint_gradient call: forward steps run (initial sweep included),
+ * reverse steps, checkpoint stores and restores. */
+int envar_adjoint_stats(envar_handle h, long long *forward_steps, long long *reverse_steps, long long *stores,
+                        long long *restores);
+
+/* Host only, no device needed: the checkpoint schedule envar_adjoint_gradient uses for n_steps
+ * steps and n_slots snapshots (clamped to n_steps), run dry and checked (every step reversed once,
+ * in order, each from its own forward state).  recompute: forward steps beyond the initial sweep;
+ * stores, restores: checkpoint copies.  Returns ENVAR_ESTATE if the check fails. */
+int envar_revolve_plan(long long n_steps, int n_slots, long long *recompute, long long *stores, long long *restores);
+
 #ifdef __cplusplus
 }
 #endif

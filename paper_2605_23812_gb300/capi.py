@@ -82,6 +82,9 @@ def lib():
         "envar_kernel_launches": [H, ctypes.POINTER(ctypes.c_longlong)],
         "envar_time_kernel": [H, c_int, c_int, ctypes.POINTER(c_double)],
         "envar_apply_preconditioner": [H, c_void_p, c_void_p],
+        "envar_adjoint_gradient": [H, c_void_p, c_void_p, c_int, c_void_p],
+        "envar_adjoint_stats": [H] + [ctypes.POINTER(ctypes.c_longlong)] * 4,
+        "envar_revolve_plan": [ctypes.c_longlong, c_int] + [ctypes.POINTER(ctypes.c_longlong)] * 3,
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -256,6 +259,59 @@ class Ensemble:
         ms = c_double()
         self._check(lib().envar_time_kernel(self._h, int(which), int(reps), ctypes.byref(ms)), "envar_time_kernel")
         return ms.value
+
+    # ---- discrete adjoint (FP64 handles)
+    def adjoint_gradient(self, f, max_snapshots: int = 64):
+        """(J, dJ/df) of one forward run with control forcing f, by the discrete adjoint."""
+        ft = self._dev(f, (self.n_ctrl,))
+        g = self.torch.empty_like(ft)
+        J = np.zeros(1)
+        self.torch.cuda.current_stream().synchronize()
+        self._check(lib().envar_adjoint_gradient(self._h, _ptr(ft), _ptr(g), int(max_snapshots), _np_ptr(J)),
+                    "envar_adjoint_gradient")
+        return float(J[0]), g
+
+    def adjoint_stats(self):
+        v = [ctypes.c_longlong() for _ in range(4)]
+        self._check(lib().envar_adjoint_stats(self._h, *[ctypes.byref(x) for x in v]), "envar_adjoint_stats")
+        return dict(zip(("forward_steps", "reverse_steps", "stores", "restores"), (x.value for x in v)))
+
+
+def revolve_plan(n_steps: int, n_slots: int):
+    """Dry run of the adjoint's checkpoint schedule (host only): recompute, stores, restores."""
+    v = [ctypes.c_longlong() for _ in range(3)]
+    rc = lib().envar_revolve_plan(int(n_steps), int(n_slots), *[ctypes.byref(x) for x in v])
+    if rc != 0:
+        raise EnvarError(f"envar_revolve_plan: {ERRORS.get(rc, rc)}")
+    return dict(zip(("recompute", "stores", "restores"), (x.value for x in v)))
+
+
+def _adjoint_cost_function():
+    import torch
+
+    class AdjointCost(torch.autograd.Function):
+        """J(f) with backward by the discrete adjoint: forward runs envar_forward_control, backward
+        envar_adjoint_gradient (which reruns the forward with checkpoints)."""
+
+        @staticmethod
+        def forward(ctx, f, ens, max_snapshots):
+            ctx.ens, ctx.max_snapshots = ens, max_snapshots
+            ctx.save_for_backward(f)
+            J = ens.forward_control(f.detach())
+            return torch.tensor(J, dtype=torch.float64, device=f.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (f,) = ctx.saved_tensors
+            _, g = ctx.ens.adjoint_gradient(f.detach(), ctx.max_snapshots)
+            return gJ * g, None, None
+
+    return AdjointCost
+
+
+def adjoint_cost(f, ens: "Ensemble", max_snapshots: int = 64):
+    """Differentiable DOMAIN cost of one forward run with control forcing f (float64, n_ctrl)."""
+    return _adjoint_cost_function().apply(f, ens, max_snapshots)
 
 
 def kernel_launches() -> int:

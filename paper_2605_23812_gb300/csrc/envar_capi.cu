@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "envar_internal.cuh"
+#include "revolve.h"
 #include "../../include/envar.h"
 
 namespace envar {
@@ -68,6 +69,12 @@ struct envar_handle_s {
     int last_member_slot0 = -1;       // member held in slot 0 after a plain-mode run
     std::vector<void *> allocs;
     GraphSet graphs[2];               // [0]: all slots, [1]: one slot
+    // discrete adjoint (FP64 handles): work planes, checkpoint slots, reverse-step graphs
+    double *d_adj = nullptr;
+    double *d_snap = nullptr;
+    int n_snap = 0;
+    cudaGraphExec_t adj_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [first step][in window]
+    long long adj_fwd_steps = 0, adj_rev_steps = 0, adj_stores = 0, adj_restores = 0;
     char err[512] = {0};
 };
 
@@ -663,7 +670,11 @@ extern "C" int envar_destroy(envar_handle h)
         if (gs.many) cudaGraphExecDestroy(gs.many);
         if (gs.one) cudaGraphExecDestroy(gs.one);
     }
+    for (auto &row : h->adj_graph)
+        for (auto &ge : row)
+            if (ge) cudaGraphExecDestroy(ge);
     for (void *p : h->allocs) cudaFree(p);
+    if (h->d_snap) cudaFree(h->d_snap);
     if (h->own_stream) cudaStreamDestroy(h->st);
     delete h;
     return ENVAR_OK;
@@ -991,5 +1002,226 @@ extern "C" int envar_apply_preconditioner(envar_handle h, const double *r_dev, d
     }
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+// ------------------------------------------------------------------------------------ adjoint (a9)
+// Discrete adjoint of the FP64 stepper for member slot 0 (Sec. 3.2): the kernels are in
+// k_adjoint.cu, the checkpoint schedule in revolve.h.  The forward state of a checkpoint is
+// (u, v, p, dp, R_u, R_v): the pressure and last increment make a recomputed step bitwise equal
+// to the original (the increment is the solve's initial guess), the tendencies carry AB2.
+namespace envar {
+void launch_adj_rhs(const Grid &g, const double *lu, const double *lv, double *b, unsigned long long *mx,
+                    MemberCtl *ctl, cudaStream_t st);
+void launch_adj_set_step(MemberCtl *ctl, int k, cudaStream_t st);
+void launch_adj_post(const Grid &g, double *lu, double *lv, const double *x, const unsigned long long *mx,
+                     const MemberRed *red, double res_tol, MemberCtl *ctl, double *ubb, double *Rbu, double *Rbv,
+                     double *cu, double *cv, double *gu, double *gv, double c1, double c0, cudaStream_t st);
+void launch_adj_tend(const Grid &g, const double *u, const double *v, const double *Rbu, const double *Rbv,
+                     double *lu, double *lv, cudaStream_t st);
+void launch_adj_outlet(const Grid &g, const double *ubb, double *lu, cudaStream_t st);
+void launch_adj_cost(const Grid &g, const double *u, const double *v, const double *mu, const double *mv, double wgt,
+                     double *lu, double *lv, cudaStream_t st);
+void launch_faces_to_control(const Grid &g, int ncc, const int *cidx, const double *gu, const double *gv,
+                             double *out, cudaStream_t st);
+}
+
+static constexpr int kAdjPlanes = 10;          // lu lv cu cv Rbu Rbv gu gv mu mv, then ubb and the scale
+static constexpr int kSnapPlanes = 6;          // u v p dp Ru Rv
+static constexpr double kAdjResTol = 1e-12;    // max |b - A x| relative to max |b|
+
+struct AdjointExec {
+    envar_handle h;
+    long long S;
+    double *lu, *lv, *cu, *cv, *Rbu, *Rbv, *gu, *gv, *mu, *mv, *ubb;
+    unsigned long long *mx;
+    int k0;
+    double wgt;
+    long long cur = -1;   // forward state in the working buffers, -1 if clobbered
+
+    double *plane(int p) const
+    {
+        switch (p) {
+        case 0: return h->d_u;
+        case 1: return h->d_v;
+        case 2: return h->d_p;
+        case 3: return h->pb.x;
+        case 4: return (double *)h->d_Ru;
+        default: return (double *)h->d_Rv;
+        }
+    }
+    int copy_slot(int slot, bool to_slot)
+    {
+        double *base = h->d_snap + (size_t)slot * kSnapPlanes * S;
+        for (int p = 0; p < kSnapPlanes; ++p) {
+            double *w = plane(p), *s = base + (size_t)p * S;
+            CK(cudaMemcpyAsync(to_slot ? s : w, to_slot ? w : s, sizeof(double) * S, cudaMemcpyDeviceToDevice, h->st));
+        }
+        return ENVAR_OK;
+    }
+    int advance(long long from, long long to)
+    {
+        int rc = run_steps(h, 1, (int)(to - from));
+        if (rc) return rc;
+        h->adj_fwd_steps += to - from;
+        cur = to;
+        return ENVAR_OK;
+    }
+    int store(int slot, long long k)
+    {
+        ++h->adj_stores;
+        (void)k;
+        return copy_slot(slot, true);
+    }
+    int restore(int slot, long long k)
+    {
+        if (cur == k) return ENVAR_OK;
+        ++h->adj_restores;
+        int rc = copy_slot(slot, false);
+        if (rc) return rc;
+        launch_adj_set_step(h->d_ctl, (int)k, h->st);
+        cur = k;
+        return ENVAR_OK;
+    }
+    void enqueue_reverse(bool first, bool in_window)
+    {
+        const Grid &g = h->g;
+        PoissonCfg pa = h->pc;
+        pa.rtol_abs = kAdjResTol;
+        pa.max_outer = std::max(pa.max_outer, 4);
+        launch_adj_rhs(g, lu, lv, h->pb.b, mx, h->d_ctl, h->st);
+        cudaMemsetAsync(h->pb.x, 0, sizeof(double) * S, h->st);
+        launch_pressure_solve<double>(g, h->lev, 1, h->pb, pa, h->pt, h->d_ctl, h->st);
+        launch_adj_post(g, lu, lv, h->pb.x, mx, h->pt.red, kAdjResTol, h->d_ctl, ubb, Rbu, Rbv, cu, cv, gu, gv,
+                        first ? 1.0 : 1.5, first ? 0.0 : -0.5, h->st);
+        launch_adj_tend(g, h->d_u, h->d_v, Rbu, Rbv, lu, lv, h->st);
+        launch_adj_outlet(g, ubb, lu, h->st);
+        if (in_window) launch_adj_cost(g, h->d_u, h->d_v, mu, mv, wgt, lu, lv, h->st);
+    }
+    // reverse step a (a -> a+1) about the working state a, then add the cost gradient at sample a
+    int reverse(long long a)
+    {
+        const int fi = (a == 0) ? 1 : 0, wi = (a >= k0) ? 1 : 0;
+        cudaGraphExec_t &ge = h->adj_graph[fi][wi];
+        if (!ge) {
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+            set_capturing(true);
+            enqueue_reverse(fi != 0, wi != 0);
+            set_capturing(false);
+            cudaError_t e = cudaStreamEndCapture(h->st, &graph);
+            if (e != cudaSuccess) {
+                set_err(h, "adjoint graph capture failed: %s", cudaGetErrorString(e));
+                return ENVAR_ECUDA;
+            }
+            e = cudaGraphInstantiate(&ge, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                ge = nullptr;
+                set_err(h, "adjoint graph instantiate failed: %s", cudaGetErrorString(e));
+                return ENVAR_ECUDA;
+            }
+        }
+        CK(cudaGraphLaunch(ge, h->st));
+        ++h->adj_rev_steps;
+        cur = -1;   // the solve used the increment buffer
+        return ENVAR_OK;
+    }
+};
+
+extern "C" int envar_revolve_plan(long long n_steps, int n_slots, long long *recompute, long long *stores,
+                                  long long *restores)
+{
+    if (n_steps < 1 || n_slots < 1) return ENVAR_EINVAL;
+    long long st = 0, rs = 0;
+    long long f = revolve_dry_run(n_steps, (int)std::min<long long>(n_slots, n_steps), &st, &rs);
+    if (f < 0) return ENVAR_ESTATE;
+    if (recompute) *recompute = f;
+    if (stores) *stores = st;
+    if (restores) *restores = rs;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_adjoint_gradient(envar_handle h, const double *f, double *gf, int max_snapshots, double *J)
+{
+    if (!h || !f || !gf) return ENVAR_EINVAL;
+    if (h->mixed || h->cfg.cost_mode != ENVAR_COST_DOMAIN || h->cfg.n_window < 1 || max_snapshots < 1) {
+        set_err(h, "envar_adjoint_gradient: needs an FP64 handle, the DOMAIN cost, n_window >= 1, max_snapshots >= 1");
+        return ENVAR_EINVAL;
+    }
+    if (!h->have_ic) { set_err(h, "envar_adjoint_gradient: no initial state"); return ENVAR_ESTATE; }
+    const long long n = h->cfg.n_steps;
+    const int Sl = (int)std::min<long long>(max_snapshots, n);
+    const long long S = h->g.S;
+    if (!h->d_adj) DA(h->d_adj, (size_t)kAdjPlanes * S + h->g.ny + 2);
+    if (h->n_snap < Sl) {
+        if (h->d_snap) { CK(cudaStreamSynchronize(h->st)); cudaFree(h->d_snap); h->d_snap = nullptr; h->n_snap = 0; }
+        void *q = nullptr;
+        size_t bytes = sizeof(double) * (size_t)Sl * kSnapPlanes * S;
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) {
+            set_err(h, "envar_adjoint_gradient: %d checkpoints need %zu bytes: %s", Sl, bytes, cudaGetErrorString(e));
+            return ENVAR_ENOMEM;
+        }
+        h->d_snap = (double *)q;
+        h->n_snap = Sl;
+    }
+    AdjointExec ex;
+    ex.h = h;
+    ex.S = S;
+    double *a = h->d_adj;
+    ex.lu = a; ex.lv = a + S; ex.cu = a + 2 * S; ex.cv = a + 3 * S; ex.Rbu = a + 4 * S; ex.Rbv = a + 5 * S;
+    ex.gu = a + 6 * S; ex.gv = a + 7 * S; ex.mu = a + 8 * S; ex.mv = a + 9 * S;
+    ex.ubb = a + (size_t)kAdjPlanes * S;
+    ex.mx = (unsigned long long *)(ex.ubb + h->g.ny);
+    ex.k0 = (int)(n - h->cfg.n_window + 1);
+    ex.wgt = h->g.hxy / (double)h->cfg.n_window;
+    h->adj_fwd_steps = h->adj_rev_steps = h->adj_stores = h->adj_restores = 0;
+
+    // initial sweep 0 -> n with the forcing f, storing the schedule's first checkpoints
+    launch_compact_to_rect(1, h->nrect, h->ncc, h->d_cidx, f, h->d_frect, h->st);
+    reset_members(h, 1);
+    ex.cur = 0;
+    int rc = ex.store(0, 0);
+    if (rc) return rc;
+    std::vector<long long> pos;
+    std::vector<int> slot;
+    revolve_spine(n, Sl, &pos, &slot);
+    long long at = 0;
+    for (size_t k = 0; k < pos.size(); ++k) {
+        if ((rc = ex.advance(at, pos[k]))) return rc;
+        if ((rc = ex.store(slot[k], pos[k]))) return rc;
+        at = pos[k];
+    }
+    if ((rc = ex.advance(at, n))) return rc;
+    enqueue_cost(h, 1, h->d_Jd_slot, h->d_Js_slot);
+    // window means of the cell-centred velocity (member 0's Welford planes), then lambda^n
+    CK(cudaMemcpyAsync(ex.mu, h->d_wf, sizeof(double) * 2 * S, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemsetAsync(a, 0, sizeof(double) * 8 * S, h->st));
+    launch_adj_cost(h->g, h->d_u, h->d_v, ex.mu, ex.mv, ex.wgt, ex.lu, ex.lv, h->st);
+    if ((rc = revolve_rev(ex, 0, n, Sl - 1, 0, Sl, true))) return rc;
+    launch_faces_to_control(h->g, h->ncc, h->d_cidx, ex.gu, ex.gv, gf, h->st);
+    MemberCtl c0{};
+    CK(cudaMemcpyAsync(&c0, h->d_ctl, sizeof(MemberCtl), cudaMemcpyDeviceToHost, h->st));
+    if (J) CK(cudaMemcpyAsync(J, h->d_Jd_slot, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    h->have_forward = false;
+    h->last_member_slot0 = -2;
+    if (c0.status) {
+        set_err(h, "envar_adjoint_gradient: status 0x%x (non-finite state, CFL, or an unconverged solve)", c0.status);
+        return ENVAR_ESTATE;
+    }
+    return ENVAR_OK;
+}
+
+extern "C" int envar_adjoint_stats(envar_handle h, long long *forward_steps, long long *reverse_steps,
+                                   long long *stores, long long *restores)
+{
+    if (!h) return ENVAR_EINVAL;
+    if (forward_steps) *forward_steps = h->adj_fwd_steps;
+    if (reverse_steps) *reverse_steps = h->adj_rev_steps;
+    if (stores) *stores = h->adj_stores;
+    if (restores) *restores = h->adj_restores;
     return ENVAR_OK;
 }
