@@ -233,6 +233,20 @@ int envar_adjoint_stats(envar_handle h, long long *forward_steps, long long *rev
  * stores, restores: checkpoint copies.  Returns ENVAR_ESTATE if the check fails. */
 int envar_revolve_plan(long long n_steps, int n_slots, long long *recompute, long long *stores, long long *restores);
 
+/* Draw the ensemble matrix E without allocating device memory.  The paper has no counterpart:
+ * this is for callers that cannot let a library call cudaMalloc (a framework whose caching
+ * allocator owns the device, a fixed memory budget, code that must avoid the synchronisation of
+ * cudaFree).  It writes the same E as envar_init + envar_get_ensemble for the same configuration
+ * (n_ctrl x N column-major, E_dev caller-owned device memory) and uses as scratch a file-scope
+ * device array of ENVAR_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until exit.
+ * No cudaMalloc / cudaFree or allocating library routine is called.  The first call on a device
+ * (with that device current) looks up the array's device address; make it before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.  Configurations needing
+ * more scratch than the maximum are rejected (ENVAR_EINVAL); the message of a failure is returned
+ * by envar_last_error(NULL).  Runs on cuda_stream (NULL = legacy default) and synchronises it. */
+#define ENVAR_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+int envar_draw_ensemble_noalloc(const envar_config *cfg, double *E_dev, int n_ctrl, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,7 @@ def lib():
         "envar_adjoint_gradient": [H, c_void_p, c_void_p, c_int, c_void_p],
         "envar_adjoint_stats": [H] + [ctypes.POINTER(ctypes.c_longlong)] * 4,
         "envar_revolve_plan": [ctypes.c_longlong, c_int] + [ctypes.POINTER(ctypes.c_longlong)] * 3,
+        "envar_draw_ensemble_noalloc": [ctypes.POINTER(Config), c_void_p, c_int, c_void_p],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -79,6 +79,9 @@ struct envar_handle_s {
 };
 
 static char g_init_err[512];
+namespace envar {
+void set_global_error(const char *msg) { std::snprintf(g_init_err, sizeof(g_init_err), "%s", msg); }
+}
 
 static void set_err(envar_handle h, const char *fmt, ...)
 {
