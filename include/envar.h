@@ -69,7 +69,8 @@ enum {
 enum {
     ENVAR_ST_NONFINITE = 1,     /* NaN or Inf met in the velocity */
     ENVAR_ST_DIVERGENCE = 2,    /* pressure solve ended above div_tol */
-    ENVAR_ST_CFL = 4            /* |u| dt / h exceeded 1 */
+    ENVAR_ST_CFL = 4,           /* |u| dt / h exceeded 1 */
+    ENVAR_ST_ADJOINT = 8        /* an adjoint Poisson solve ended above its tolerance */
 };
 
 typedef struct envar_config {

@@ -19,7 +19,7 @@ c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 
 FP64_PLAIN, FP64_BATCHED, MIXED = 0, 1, 2
 COST_DOMAIN, COST_SENSORS = 0, 1
-ST_NONFINITE, ST_DIVERGENCE, ST_CFL = 1, 2, 4
+ST_NONFINITE, ST_DIVERGENCE, ST_CFL, ST_ADJOINT = 1, 2, 4, 8
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESTATE", -5: "EDEVICE"}
 
 

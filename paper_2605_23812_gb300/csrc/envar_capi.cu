@@ -477,6 +477,7 @@ static void enqueue_step(envar_handle h, int M)
     launch_correct(g, h->x0, h->y0, M, h->d_u, h->d_v, h->d_p, h->d_us, h->d_vs, h->pb.x, h->d_wf,
                    h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0, h->cfg.n_window > 0 ? h->d_series_slot : nullptr,
                    h->pt, h->d_ctl, h->cfg.div_tol, h->nfluid, st);
+    launch_recenter(g, M, h->pb.x, h->pt, h->nfluid, st);
 }
 
 static int capture(envar_handle h, int M, int nsteps, cudaGraphExec_t *out, long long *kernels)

@@ -208,6 +208,7 @@ void launch_reset(const Grid &g, int M, const double *u0, const double *v0, doub
 void launch_outflow(const Grid &g, int M, const double *u, double *ubc, MemberCtl *ctl, cudaStream_t st);
 void launch_rhs(const Grid &g, int M, const double *us, const double *vs, double *b, MemberCtl *ctl,
                 cudaStream_t st);
+void launch_recenter(const Grid &g, int M, double *x, const Partials &pt, long long nfluid, cudaStream_t st);
 void launch_correct(const Grid &g, double x0, double y0, int M, double *u, double *v, double *p,
                     const double *us, const double *vs, const double *x, double *wf, int want_welford,
                     double *series, const Partials &pt, MemberCtl *ctl, double div_tol, long long nfluid,

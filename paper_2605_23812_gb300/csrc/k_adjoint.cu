@@ -68,7 +68,7 @@ __global__ void k_adj_post(Grid g, double *__restrict__ lu, double *__restrict__
                            double *__restrict__ gv, double c1, double c0)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i == 0 && j == 0 && !(red[0].val[RS_RMAX] <= res_tol)) atomicOr(&ctl[0].status, ENVAR_ST_DIVERGENCE);
+    if (i == 0 && j == 0 && !(red[0].val[RS_RMAX] <= res_tol)) atomicOr(&ctl[0].status, ENVAR_ST_ADJOINT);
     if (i > g.nx || j > g.ny) return;
     const long long c = (long long)j * g.P + i;
     const double dt = g.dt;

@@ -338,6 +338,25 @@ void launch_correct(const Grid &g, double x0, double y0, int M, double *u, doubl
     count_launches(1);
 }
 
+// The increment dp is also the next step's initial guess.  The Neumann problem fixes it only up
+// to a constant, which the solves leave to drift; a large constant costs accuracy in A x (rounding
+// scales with |x|), so the guess is re-centred on the fluid mean once the step has used it.
+__global__ void k_recenter(Grid g, double *__restrict__ x, Partials pt, long long nfluid)
+{
+    const int m = blockIdx.z;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const long long c = (long long)j * g.P + i;
+    if (g.fluid[c]) x[(long long)m * g.S + c] -= pt.red[m].val[RS_XSUM] / (double)nfluid;
+}
+
+void launch_recenter(const Grid &g, int M, double *x, const Partials &pt, long long nfluid, cudaStream_t st)
+{
+    dim3 blk(32, 8), grd(cdiv(g.nx, 32), cdiv(g.ny, 8), M);
+    k_recenter<<<grd, blk, 0, st>>>(g, x, pt, nfluid);
+    count_launches(1);
+}
+
 // ---------------------------------------------------------------------------- costs (K7)
 __global__ void k_domain_partial(Grid g, const double *__restrict__ wf, double *__restrict__ part)
 {

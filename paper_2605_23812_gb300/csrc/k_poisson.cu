@@ -356,6 +356,188 @@ __global__ void __launch_bounds__(SC_THREADS, sizeof(T) == 4 ? 2 : 1) k_smooth(S
 #undef KN
 
 // ------------------------------------------------------------------------------------------------
+// Fine-level (level 0) smoother.  On level 0 every open face has the same conductance (cx for x
+// faces, cy for y faces) and a closed face always separates a fluid cell from a solid or outside
+// cell, whose value is zero in every vector the solver smooths (right-hand sides and guesses are
+// zero there and the update leaves a cell with no open face at zero).  The Gauss-Seidel update of
+// a fluid cell is therefore e_c = (f_c + cx (e_W + e_E) + cy (e_S + e_N)) / d_c, with
+// d_c = cx (#open x faces) + cy (#open y faces); a cell with no open face gets 1/d_c = 0.
+//
+// Layout: a block's region is 64 columns x (S0_WARPS * R) rows; warp w owns R consecutive rows and
+// lane l the cell pair (2l, 2l+1) of each: one red and one black cell per row, so a half-sweep
+// updates exactly one cell per lane and row, chosen by the row's parity (the region starts on an
+// even column and row).  East / west neighbours come from the neighbouring lane by shuffle,
+// north / south ones from the lane's own registers, except across warps, where the boundary rows
+// go through shared memory (double-buffered, one barrier per half-sweep).  The halo is
+// H = 2 nsweep + 2 cells (even, for the alignment): the outermost ring is never updated (its
+// inverse diagonal is zeroed), so after the 2 nsweep half-sweeps the tile and its first ring hold
+// exactly the values of the global red-black sweep sequence (a wrong value moves one cell inward
+// per half-sweep), which the restriction and the dot product use.
+constexpr int S0_COLS = 64, S0_WARPS = 12;
+template <class T> struct S0 {
+    static constexpr int R = sizeof(T) == 4 ? 8 : 4;   // rows per warp
+};
+__host__ __device__ constexpr int s0_halo(int ns) { return 2 * ns + 2; }
+template <class T> __host__ __device__ constexpr int s0_tw(int ns) { return S0_COLS - 2 * s0_halo(ns); }
+template <class T> __host__ __device__ constexpr int s0_th(int ns) { return S0_WARPS * S0<T>::R - 2 * s0_halo(ns); }
+
+template <class T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
+template <class T, int NS>
+__global__ void __launch_bounds__(S0_WARPS * 32, 2) k_smooth0(SmoothArgs sa, const T *__restrict__ f,
+                                                             const T *__restrict__ ein, T *__restrict__ e,
+                                                             const T *__restrict__ ec, T *__restrict__ fc, RedCtx rc,
+                                                             MemberCtl *ctl, int inner_guard)
+{
+    using T2 = typename Pair2<T>::type;
+    constexpr int R = S0<T>::R, H = s0_halo(NS), NH = S0_WARPS * R, TW = S0_COLS - 2 * H, TH = NH - 2 * H;
+    static_assert(R % 2 == 0, "rows per warp come in pairs (restriction)");
+    __shared__ T2 xb[2][S0_WARPS][2][32];   // [buffer][warp][0: bottom row, 1: top row][lane]
+    const int m = blockIdx.z;
+    if (ctl[m].outer_done) return;
+    if (inner_guard && ctl[m].inner_done) return;
+    const Level &L = sa.L;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i0 = blockIdx.x * TW, j0 = blockIdx.y * TH;
+    const int gi0 = i0 - H, gj0 = j0 - H;
+    const int iL = gi0 + 2 * lane;                              // left cell of the pair (even)
+    const bool colok = (iL >= 0 && iL + 1 < L.nx);              // nx is even: a pair is all in or all out
+    const long long off = (long long)m * L.S;
+    const T *__restrict__ fm = f + off;
+    const T *__restrict__ eim = ein + off;
+    T *__restrict__ em = e + off;
+    const T *__restrict__ ecm = ec + (long long)m * sa.Sc;
+    const T cx = (T)L.cx, cy = (T)L.cy;
+    const bool zero = (sa.flags & SF_ZERO_INIT) != 0;
+    const bool prolong = (sa.flags & SF_PROLONG) != 0;
+
+    // diagonal and its inverse per open-face pattern (W 1, E 2, S 4, N 8): 16 entries
+    __shared__ T dtab[16], ivtab[16];
+    if (threadIdx.x < 16) {
+        const unsigned int q = threadIdx.x;
+        const T d = ((q & 1u) ? cx : (T)0) + ((q & 2u) ? cx : (T)0) + ((q & 4u) ? cy : (T)0) + ((q & 8u) ? cy : (T)0);
+        dtab[q] = d;
+        ivtab[q] = (d != (T)0) ? (T)1 / d : (T)0;
+    }
+    __syncthreads();
+
+    T e0[R], e1[R], f0[R], f1[R], v0[R], v1[R];
+    unsigned int bits[(R + 3) / 4];                             // 8 bits (two cells) per row, 4 rows per word
+#pragma unroll
+    for (int q = 0; q < (R + 3) / 4; ++q) bits[q] = 0u;
+    const long long c0 = (long long)(gj0 + w * R) * L.P + iL;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = gj0 + w * R + r;
+        const bool ok = colok && j >= 0 && j < L.ny;
+        const long long c = c0 + (long long)r * L.P;
+        T2 fv = {(T)0, (T)0}, ev = {(T)0, (T)0};
+        unsigned int b2 = 0u;
+        if (ok) {
+            b2 = *reinterpret_cast<const unsigned short *>(L.open + c);   // left cell low byte
+            fv = *reinterpret_cast<const T2 *>(fm + c);
+            if (!zero) ev = *reinterpret_cast<const T2 *>(eim + c);
+            if (prolong) {
+                const T cv = ecm[(long long)(j >> 1) * sa.Pc + (iL >> 1)];
+                if (b2 & 0x00ffu) ev.x += cv;
+                if (b2 & 0xff00u) ev.y += cv;
+            }
+        }
+        const unsigned int bl = b2 & 15u, br = (b2 >> 8) & 15u;
+        bits[r >> 2] |= (bl | (br << 4)) << ((r & 3) * 8);
+        const bool ring_row = (w == 0 && r == 0) || (w == S0_WARPS - 1 && r == R - 1);
+        v0[r] = (ring_row || lane == 0) ? (T)0 : ivtab[bl];
+        v1[r] = (ring_row || lane == 31) ? (T)0 : ivtab[br];
+        f0[r] = fv.x; f1[r] = fv.y;
+        e0[r] = ev.x; e1[r] = ev.y;
+    }
+    xb[1][w][0][lane] = T2{e0[0], e1[0]};
+    xb[1][w][1][lane] = T2{e0[R - 1], e1[R - 1]};
+    __syncthreads();
+
+    const int wb = (w > 0) ? w - 1 : 0, wa = (w < S0_WARPS - 1) ? w + 1 : S0_WARPS - 1;
+#pragma unroll
+    for (int s = 0; s < 2 * NS; ++s) {
+        const int col = (s & 1) ^ sa.order;                     // colour updated: (i + j) & 1 == col
+        const int rbuf = (s & 1) ^ 1, wbuf = s & 1;
+        const T2 below = xb[rbuf][wb][1][lane];                  // top row of the warp below
+        const T2 above = xb[rbuf][wa][0][lane];                  // bottom row of the warp above
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            // the left cell (even column) of row r has colour r & 1 (gj0 and w R are even)
+            if ((r & 1) == col) {
+                const T sS = (r > 0) ? e0[r > 0 ? r - 1 : 0] : below.x;
+                const T sN = (r < R - 1) ? e0[r < R - 1 ? r + 1 : 0] : above.x;
+                const T eW = __shfl_up_sync(0xffffffffu, e1[r], 1);
+                e0[r] = v0[r] * (f0[r] + cx * (eW + e1[r]) + cy * (sS + sN));
+            } else {
+                const T sS = (r > 0) ? e1[r > 0 ? r - 1 : 0] : below.y;
+                const T sN = (r < R - 1) ? e1[r < R - 1 ? r + 1 : 0] : above.y;
+                const T eE = __shfl_down_sync(0xffffffffu, e0[r], 1);
+                e1[r] = v1[r] * (f1[r] + cx * (e0[r] + eE) + cy * (sS + sN));
+            }
+        }
+        xb[wbuf][w][0][lane] = T2{e0[0], e1[0]};
+        xb[wbuf][w][1][lane] = T2{e0[R - 1], e1[R - 1]};
+        __syncthreads();
+    }
+
+    // tile interior: output, dot product, residual restricted to the coarse level
+    constexpr int fb = (2 * NS - 1) & 1;                        // buffer of the last half-sweep
+    const T2 below = xb[fb][wb][1][lane], above = xb[fb][wa][0][lane];
+    const bool tile_col = colok && iL >= i0 && iL < i0 + TW;
+    const bool restrict_ = (sa.flags & SF_RESTRICT) != 0;
+    const bool want_dot = (sa.flags & (SF_DOT | SF_INIT_DOT)) != 0;
+    DotAcc<T> dot;
+    T racc = (T)0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int b = w * R + r, j = gj0 + b;
+        const bool tile = tile_col && b >= H && b < H + TH && j < L.ny;
+        const long long c = (long long)j * L.P + iL;
+        if (tile) {
+            *reinterpret_cast<T2 *>(em + c) = T2{e0[r], e1[r]};
+            if (want_dot) { dot.add(f0[r], e0[r]); dot.add(f1[r], e1[r]); }
+        }
+        if (restrict_) {
+            const T sS0 = (r > 0) ? e0[r > 0 ? r - 1 : 0] : below.x, sN0 = (r < R - 1) ? e0[r < R - 1 ? r + 1 : 0] : above.x;
+            const T sS1 = (r > 0) ? e1[r > 0 ? r - 1 : 0] : below.y, sN1 = (r < R - 1) ? e1[r < R - 1 ? r + 1 : 0] : above.y;
+            const T eW = __shfl_up_sync(0xffffffffu, e1[r], 1), eE = __shfl_down_sync(0xffffffffu, e0[r], 1);
+            const unsigned int bb = bits[r >> 2] >> ((r & 3) * 8);
+            // residual f - A e.  A fluid cell's closed faces have zero-valued neighbours, as in the
+            // sweep; a cell with no open face has the residual f (zero in a solid cell), whatever
+            // its neighbours hold.
+            const unsigned int ql = bb & 15u, qr = (bb >> 4) & 15u;
+            const T res0 = ql ? f0[r] - (dtab[ql] * e0[r] - cx * (eW + e1[r]) - cy * (sS0 + sN0)) : f0[r];
+            const T res1 = qr ? f1[r] - (dtab[qr] * e1[r] - cx * (e0[r] + eE) - cy * (sS1 + sN1)) : f1[r];
+            const T res = res0 + res1;
+            if (r & 1) {
+                if (tile) {
+                    const int I = iL >> 1, J = j >> 1;
+                    fc[(long long)m * sa.Sc + (long long)J * sa.Pc + I] = racc + res;
+                }
+            } else {
+                racc = res;
+            }
+        }
+    }
+    if (want_dot) {
+        double dtot = dot.total();
+        double tot;
+        int slot = (sa.flags & SF_INIT_DOT) ? RS_RZA : (((sa.k + 1) & 1) ? RS_RZB : RS_RZA);
+        if (publish_partial(rc, slot, m, dtot, false, &tot) && threadIdx.x == 0) {
+            rc.red[m].val[slot] = tot;
+            if (sa.flags & SF_INIT_DOT) {
+                rc.red[m].val[RS_RZ0] = tot;
+                if (!(tot > 0.0)) ctl[m].inner_done = 1;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Coarse levels (lc .. nlev-1): one block per member runs the rest of the V-cycle in shared memory.
 struct CoarseArgs {
     Level lev[MAX_LEVELS];
@@ -502,10 +684,36 @@ static void launch_smooth_b(int M, int nsweep, cudaStream_t st, const SmoothArgs
 }
 
 template <class T>
+static void launch_smooth0(int M, int nsweep, cudaStream_t st, const SmoothArgs &sa, const T *f, const T *ein, T *e,
+                           const T *ec, T *fc, const RedCtx &rc, MemberCtl *ctl, int inner_guard)
+{
+    const Level &L = sa.L;
+    const int nt = S0_WARPS * 32;
+    switch (nsweep) {
+    case 1: {
+        dim3 grd(cdiv(L.nx, s0_tw<T>(1)), cdiv(L.ny, s0_th<T>(1)), M);
+        k_smooth0<T, 1><<<grd, nt, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+        break;
+    }
+    case 2: {
+        dim3 grd(cdiv(L.nx, s0_tw<T>(2)), cdiv(L.ny, s0_th<T>(2)), M);
+        k_smooth0<T, 2><<<grd, nt, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+        break;
+    }
+    default: {
+        dim3 grd(cdiv(L.nx, s0_tw<T>(3)), cdiv(L.ny, s0_th<T>(3)), M);
+        k_smooth0<T, 3><<<grd, nt, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+        break;
+    }
+    }
+    count_launches(1);
+}
+
+template <class T>
 static void launch_smooth(int M, int nsweep, cudaStream_t st, const SmoothArgs &sa, const T *f, const T *ein, T *e,
                           const T *ec, T *fc, const RedCtx &rc, MemberCtl *ctl, int inner_guard)
 {
-    if (sa.L.open) launch_smooth_b<T, true>(M, nsweep, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+    if (sa.L.open) launch_smooth0<T>(M, nsweep, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
     else launch_smooth_b<T, false>(M, nsweep, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
 }
 
