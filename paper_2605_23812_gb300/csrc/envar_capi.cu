@@ -276,7 +276,41 @@ static int build_geometry(envar_handle h)
         CK(cudaMemcpy(csf, f2.data(), sizeof(float) * L.S, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(cwd, L.cw.data(), sizeof(double) * L.S, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(csd, L.cs.data(), sizeof(double) * L.S, cudaMemcpyHostToDevice));
-        h->lev[l] = Level{L.nx, L.ny, L.P, L.S, dfl, cwf, csf, cwd, csd, nullptr, 0.0, 0.0};
+        h->lev[l] = Level{L.nx, L.ny, L.P, L.S, dfl, cwf, csf, cwd, csd, nullptr, 0.0, 0.0, nullptr, nullptr, nullptr};
+        if (l == 0 || L.nx % 2) continue;   // the coded smoother works on cell pairs
+        // conductance codes: the distinct conductances of each direction in first-seen order
+        std::vector<double> tx, ty;
+        auto index_of = [](std::vector<double> &t, double v) -> int {
+            for (size_t k = 0; k < t.size(); ++k)
+                if (t[k] == v) return (int)k;
+            t.push_back(v);
+            return (int)t.size() - 1;
+        };
+        std::vector<uint16_t> code((size_t)L.S, 0);
+        bool fits = true;
+        for (int j = 0; j < L.ny && fits; ++j)
+            for (int i = 0; i < L.nx && fits; ++i) {
+                const size_t c = (size_t)j * L.P + i;
+                const int kw = index_of(tx, L.cw[c]), ke = index_of(tx, L.cw[c + 1]);
+                const int ks = index_of(ty, L.cs[c]), kn = index_of(ty, L.cs[c + L.P]);
+                if (tx.size() > 16 || ty.size() > 16) { fits = false; break; }
+                code[c] = (uint16_t)(kw | (ke << 4) | (ks << 8) | (kn << 12));
+            }
+        if (!fits) continue;   // this level keeps the explicit-conductance smoother
+        std::vector<double> td(32, 0.0);
+        std::vector<float> tf(32, 0.f);
+        for (size_t k = 0; k < tx.size(); ++k) { td[k] = tx[k]; tf[k] = (float)tx[k]; }
+        for (size_t k = 0; k < ty.size(); ++k) { td[16 + k] = ty[k]; tf[16 + k] = (float)ty[k]; }
+        uint16_t *dcode;
+        float *dtf;
+        double *dtd;
+        DA(dcode, L.S); DA(dtf, 32); DA(dtd, 32);
+        CK(cudaMemcpy(dcode, code.data(), sizeof(uint16_t) * L.S, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dtf, tf.data(), sizeof(float) * 32, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dtd, td.data(), sizeof(double) * 32, cudaMemcpyHostToDevice));
+        h->lev[l].code = dcode;
+        h->lev[l].ktabf = dtf;
+        h->lev[l].ktabd = dtd;
     }
     {   // level-0 open-face bits (W 1, E 2, S 4, N 8) of fluid cells
         std::vector<uint8_t> op((size_t)S, 0);

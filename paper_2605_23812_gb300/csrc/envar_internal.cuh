@@ -34,6 +34,11 @@ struct Level {
     const double *csd;
     const uint8_t *open;    // level 0 only: open-face bits (1 W, 2 E, 4 S, 8 N) of fluid cells
     double cx, cy;          // level 0 only: conductance of an open x / y face
+    // levels >= 1 with at most 16 distinct conductances per direction: per cell the table indices
+    // of its W, E, S, N faces (4 bits each, W lowest) and the tables [x faces 0..15 | y faces 0..15]
+    const uint16_t *code;
+    const float *ktabf;
+    const double *ktabd;
 };
 
 struct Grid {

@@ -356,45 +356,52 @@ __global__ void __launch_bounds__(SC_THREADS, sizeof(T) == 4 ? 2 : 1) k_smooth(S
 #undef KN
 
 // ------------------------------------------------------------------------------------------------
-// Fine-level (level 0) smoother.  On level 0 every open face has the same conductance (cx for x
-// faces, cy for y faces) and a closed face always separates a fluid cell from a solid or outside
-// cell, whose value is zero in every vector the solver smooths (right-hand sides and guesses are
-// zero there and the update leaves a cell with no open face at zero).  The Gauss-Seidel update of
-// a fluid cell is therefore e_c = (f_c + cx (e_W + e_E) + cy (e_S + e_N)) / d_c, with
-// d_c = cx (#open x faces) + cy (#open y faces); a cell with no open face gets 1/d_c = 0.
+// Warp-row smoother (level 0, and coarser levels whose conductances fit a 16-entry table).
+// On level 0 every open face has the same conductance (cx for x faces, cy for y faces) and a
+// closed face always separates a fluid cell from a solid or outside cell, whose value is zero in
+// every vector the solver smooths (right-hand sides and guesses are zero there and the update
+// leaves a cell with no open face at zero).  The Gauss-Seidel update of a fluid cell is therefore
+// e_c = (f_c + cx (e_W + e_E) + cy (e_S + e_N)) / d_c, with d_c = cx (#open x faces) +
+// cy (#open y faces); a cell with no open face gets 1/d_c = 0.
 //
-// Layout: a block's region is 64 columns x (S0_WARPS * R) rows; warp w owns R consecutive rows and
+// Layout: a block's region is 64 columns x (WARPS * R) rows; warp w owns R consecutive rows and
 // lane l the cell pair (2l, 2l+1) of each: one red and one black cell per row, so a half-sweep
 // updates exactly one cell per lane and row, chosen by the row's parity (the region starts on an
 // even column and row).  East / west neighbours come from the neighbouring lane by shuffle,
 // north / south ones from the lane's own registers, except across warps, where the boundary rows
 // go through shared memory (double-buffered, one barrier per half-sweep).  The halo is
-// H = 2 nsweep + 2 cells (even, for the alignment): the outermost ring is never updated (its
-// inverse diagonal is zeroed), so after the 2 nsweep half-sweeps the tile and its first ring hold
-// exactly the values of the global red-black sweep sequence (a wrong value moves one cell inward
-// per half-sweep), which the restriction and the dot product use.
-constexpr int S0_COLS = 64, S0_WARPS = 12;
+// H = 2 nsweep + 2 cells (even, for the alignment).  The region's outermost ring lacks neighbours,
+// so its inverse diagonal is zeroed and it goes wrong at its first update; a wrong value moves one
+// cell inward per half-sweep, so after the 2 nsweep half-sweeps the tile and its first ring still
+// hold exactly the values of the global red-black sweep sequence, which the restriction and the
+// dot product use.
+constexpr int S0_COLS = 64;
 template <class T> struct S0 {
     static constexpr int R = sizeof(T) == 4 ? 8 : 4;   // rows per warp
 };
 __host__ __device__ constexpr int s0_halo(int ns) { return 2 * ns + 2; }
-template <class T> __host__ __device__ constexpr int s0_tw(int ns) { return S0_COLS - 2 * s0_halo(ns); }
-template <class T> __host__ __device__ constexpr int s0_th(int ns) { return S0_WARPS * S0<T>::R - 2 * s0_halo(ns); }
 
 template <class T> struct Pair2;
 template <> struct Pair2<float> { using type = float2; };
 template <> struct Pair2<double> { using type = double2; };
 
-template <class T, int NS>
-__global__ void __launch_bounds__(S0_WARPS * 32, 2) k_smooth0(SmoothArgs sa, const T *__restrict__ f,
-                                                             const T *__restrict__ ein, T *__restrict__ e,
-                                                             const T *__restrict__ ec, T *__restrict__ fc, RedCtx rc,
-                                                             MemberCtl *ctl, int inner_guard)
+template <class T> __device__ __forceinline__ const T *ktab_of(const Level &L);
+template <> __device__ __forceinline__ const float *ktab_of<float>(const Level &L) { return L.ktabf; }
+template <> __device__ __forceinline__ const double *ktab_of<double>(const Level &L) { return L.ktabd; }
+
+// CODED = false: level 0 (uniform conductances, open-face bits).  CODED = true: a coarser level
+// whose face conductances are table entries: per cell a 16-bit code holds the table indices of its
+// W, E, S, N faces, and the update uses them explicitly, e_c = (f_c + sum_f k_f e_f) / sum_f k_f.
+template <class T, int NS, int WARPS, bool CODED>
+__global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const T *__restrict__ f,
+                                                          const T *__restrict__ ein, T *__restrict__ e,
+                                                          const T *__restrict__ ec, T *__restrict__ fc, RedCtx rc,
+                                                          MemberCtl *ctl, int inner_guard)
 {
     using T2 = typename Pair2<T>::type;
-    constexpr int R = S0<T>::R, H = s0_halo(NS), NH = S0_WARPS * R, TW = S0_COLS - 2 * H, TH = NH - 2 * H;
+    constexpr int R = S0<T>::R, H = s0_halo(NS), NH = WARPS * R, TW = S0_COLS - 2 * H, TH = NH - 2 * H;
     static_assert(R % 2 == 0, "rows per warp come in pairs (restriction)");
-    __shared__ T2 xb[2][S0_WARPS][2][32];   // [buffer][warp][0: bottom row, 1: top row][lane]
+    __shared__ T2 xb[2][WARPS][2][32];   // [buffer][warp][0: bottom row, 1: top row][lane]
     const int m = blockIdx.z;
     if (ctl[m].outer_done) return;
     if (inner_guard && ctl[m].inner_done) return;
@@ -413,20 +420,30 @@ __global__ void __launch_bounds__(S0_WARPS * 32, 2) k_smooth0(SmoothArgs sa, con
     const bool zero = (sa.flags & SF_ZERO_INIT) != 0;
     const bool prolong = (sa.flags & SF_PROLONG) != 0;
 
-    // diagonal and its inverse per open-face pattern (W 1, E 2, S 4, N 8): 16 entries
-    __shared__ T dtab[16], ivtab[16];
-    if (threadIdx.x < 16) {
+    // CODED: conductance tables [x 0..15 | y 0..15].  Level 0: diagonal and its inverse per
+    // open-face pattern (W 1, E 2, S 4, N 8).
+    __shared__ T tab[32];
+    if (CODED) {
+        if (threadIdx.x < 32) tab[threadIdx.x] = ktab_of<T>(L)[threadIdx.x];
+    } else if (threadIdx.x < 16) {
         const unsigned int q = threadIdx.x;
         const T d = ((q & 1u) ? cx : (T)0) + ((q & 2u) ? cx : (T)0) + ((q & 4u) ? cy : (T)0) + ((q & 8u) ? cy : (T)0);
-        dtab[q] = d;
-        ivtab[q] = (d != (T)0) ? (T)1 / d : (T)0;
+        tab[q] = d;
+        tab[16 + q] = (d != (T)0) ? (T)1 / d : (T)0;
     }
     __syncthreads();
+    // face conductances of a cell from its code (CODED)
+    auto kW = [&](unsigned int q) { return tab[q & 15u]; };
+    auto kE = [&](unsigned int q) { return tab[(q >> 4) & 15u]; };
+    auto kS = [&](unsigned int q) { return tab[16 + ((q >> 8) & 15u)]; };
+    auto kN = [&](unsigned int q) { return tab[16 + ((q >> 12) & 15u)]; };
 
     T e0[R], e1[R], f0[R], f1[R], v0[R], v1[R];
-    unsigned int bits[(R + 3) / 4];                             // 8 bits (two cells) per row, 4 rows per word
+    // level 0: 8 open bits (two cells) per row, 4 rows per word; CODED: both cells' codes per row
+    constexpr int NB = CODED ? R : (R + 3) / 4;
+    unsigned int bits[NB];
 #pragma unroll
-    for (int q = 0; q < (R + 3) / 4; ++q) bits[q] = 0u;
+    for (int q = 0; q < NB; ++q) bits[q] = 0u;
     const long long c0 = (long long)(gj0 + w * R) * L.P + iL;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -434,22 +451,40 @@ __global__ void __launch_bounds__(S0_WARPS * 32, 2) k_smooth0(SmoothArgs sa, con
         const bool ok = colok && j >= 0 && j < L.ny;
         const long long c = c0 + (long long)r * L.P;
         T2 fv = {(T)0, (T)0}, ev = {(T)0, (T)0};
-        unsigned int b2 = 0u;
+        unsigned int qq = 0u, actl = 0u, actr = 0u;
         if (ok) {
-            b2 = *reinterpret_cast<const unsigned short *>(L.open + c);   // left cell low byte
+            if (CODED) {
+                qq = *reinterpret_cast<const unsigned int *>(L.code + c);   // left cell low half
+                const unsigned int fl = *reinterpret_cast<const unsigned short *>(L.fluid + c);
+                actl = fl & 0x00ffu; actr = fl & 0xff00u;
+            } else {
+                qq = *reinterpret_cast<const unsigned short *>(L.open + c);  // left cell low byte
+                actl = qq & 0x00ffu; actr = qq & 0xff00u;
+            }
             fv = *reinterpret_cast<const T2 *>(fm + c);
             if (!zero) ev = *reinterpret_cast<const T2 *>(eim + c);
             if (prolong) {
                 const T cv = ecm[(long long)(j >> 1) * sa.Pc + (iL >> 1)];
-                if (b2 & 0x00ffu) ev.x += cv;
-                if (b2 & 0xff00u) ev.y += cv;
+                if (actl) ev.x += cv;
+                if (actr) ev.y += cv;
             }
         }
-        const unsigned int bl = b2 & 15u, br = (b2 >> 8) & 15u;
-        bits[r >> 2] |= (bl | (br << 4)) << ((r & 3) * 8);
-        const bool ring_row = (w == 0 && r == 0) || (w == S0_WARPS - 1 && r == R - 1);
-        v0[r] = (ring_row || lane == 0) ? (T)0 : ivtab[bl];
-        v1[r] = (ring_row || lane == 31) ? (T)0 : ivtab[br];
+        T il, ir;
+        if (CODED) {
+            bits[r] = qq;
+            const unsigned int ql = qq & 0xffffu, qr = qq >> 16;
+            const T dl = kW(ql) + kE(ql) + kS(ql) + kN(ql), dr = kW(qr) + kE(qr) + kS(qr) + kN(qr);
+            il = (dl != (T)0) ? (T)1 / dl : (T)0;
+            ir = (dr != (T)0) ? (T)1 / dr : (T)0;
+        } else {
+            const unsigned int bl = qq & 15u, br = (qq >> 8) & 15u;
+            bits[r >> 2] |= (bl | (br << 4)) << ((r & 3) * 8);
+            il = tab[16 + bl];
+            ir = tab[16 + br];
+        }
+        const bool ring_row = (w == 0 && r == 0) || (w == WARPS - 1 && r == R - 1);
+        v0[r] = (ring_row || lane == 0) ? (T)0 : il;
+        v1[r] = (ring_row || lane == 31) ? (T)0 : ir;
         f0[r] = fv.x; f1[r] = fv.y;
         e0[r] = ev.x; e1[r] = ev.y;
     }
@@ -457,7 +492,7 @@ __global__ void __launch_bounds__(S0_WARPS * 32, 2) k_smooth0(SmoothArgs sa, con
     xb[1][w][1][lane] = T2{e0[R - 1], e1[R - 1]};
     __syncthreads();
 
-    const int wb = (w > 0) ? w - 1 : 0, wa = (w < S0_WARPS - 1) ? w + 1 : S0_WARPS - 1;
+    const int wb = (w > 0) ? w - 1 : 0, wa = (w < WARPS - 1) ? w + 1 : WARPS - 1;
 #pragma unroll
     for (int s = 0; s < 2 * NS; ++s) {
         const int col = (s & 1) ^ sa.order;                     // colour updated: (i + j) & 1 == col
@@ -471,12 +506,22 @@ __global__ void __launch_bounds__(S0_WARPS * 32, 2) k_smooth0(SmoothArgs sa, con
                 const T sS = (r > 0) ? e0[r > 0 ? r - 1 : 0] : below.x;
                 const T sN = (r < R - 1) ? e0[r < R - 1 ? r + 1 : 0] : above.x;
                 const T eW = __shfl_up_sync(0xffffffffu, e1[r], 1);
-                e0[r] = v0[r] * (f0[r] + cx * (eW + e1[r]) + cy * (sS + sN));
+                if (CODED) {
+                    const unsigned int q = bits[CODED ? r : 0] & 0xffffu;
+                    e0[r] = v0[r] * (f0[r] + kW(q) * eW + kE(q) * e1[r] + kS(q) * sS + kN(q) * sN);
+                } else {
+                    e0[r] = v0[r] * (f0[r] + cx * (eW + e1[r]) + cy * (sS + sN));
+                }
             } else {
                 const T sS = (r > 0) ? e1[r > 0 ? r - 1 : 0] : below.y;
                 const T sN = (r < R - 1) ? e1[r < R - 1 ? r + 1 : 0] : above.y;
                 const T eE = __shfl_down_sync(0xffffffffu, e0[r], 1);
-                e1[r] = v1[r] * (f1[r] + cx * (e0[r] + eE) + cy * (sS + sN));
+                if (CODED) {
+                    const unsigned int q = bits[CODED ? r : 0] >> 16;
+                    e1[r] = v1[r] * (f1[r] + kW(q) * e0[r] + kE(q) * eE + kS(q) * sS + kN(q) * sN);
+                } else {
+                    e1[r] = v1[r] * (f1[r] + cx * (e0[r] + eE) + cy * (sS + sN));
+                }
             }
         }
         xb[wbuf][w][0][lane] = T2{e0[0], e1[0]};
@@ -505,13 +550,23 @@ __global__ void __launch_bounds__(S0_WARPS * 32, 2) k_smooth0(SmoothArgs sa, con
             const T sS0 = (r > 0) ? e0[r > 0 ? r - 1 : 0] : below.x, sN0 = (r < R - 1) ? e0[r < R - 1 ? r + 1 : 0] : above.x;
             const T sS1 = (r > 0) ? e1[r > 0 ? r - 1 : 0] : below.y, sN1 = (r < R - 1) ? e1[r < R - 1 ? r + 1 : 0] : above.y;
             const T eW = __shfl_up_sync(0xffffffffu, e1[r], 1), eE = __shfl_down_sync(0xffffffffu, e0[r], 1);
-            const unsigned int bb = bits[r >> 2] >> ((r & 3) * 8);
-            // residual f - A e.  A fluid cell's closed faces have zero-valued neighbours, as in the
-            // sweep; a cell with no open face has the residual f (zero in a solid cell), whatever
-            // its neighbours hold.
-            const unsigned int ql = bb & 15u, qr = (bb >> 4) & 15u;
-            const T res0 = ql ? f0[r] - (dtab[ql] * e0[r] - cx * (eW + e1[r]) - cy * (sS0 + sN0)) : f0[r];
-            const T res1 = qr ? f1[r] - (dtab[qr] * e1[r] - cx * (e0[r] + eE) - cy * (sS1 + sN1)) : f1[r];
+            T res0, res1;
+            if (CODED) {
+                // residual f - A e with the explicit conductances (zero across closed faces)
+                const unsigned int ql = bits[CODED ? r : 0] & 0xffffu, qr = bits[CODED ? r : 0] >> 16;
+                res0 = f0[r] - ((kW(ql) + kE(ql) + kS(ql) + kN(ql)) * e0[r] - kW(ql) * eW - kE(ql) * e1[r] -
+                                kS(ql) * sS0 - kN(ql) * sN0);
+                res1 = f1[r] - ((kW(qr) + kE(qr) + kS(qr) + kN(qr)) * e1[r] - kW(qr) * e0[r] - kE(qr) * eE -
+                                kS(qr) * sS1 - kN(qr) * sN1);
+            } else {
+                // residual f - A e.  A fluid cell's closed faces have zero-valued neighbours, as in
+                // the sweep; a cell with no open face has the residual f (zero in a solid cell),
+                // whatever its neighbours hold.
+                const unsigned int bb = bits[r >> 2] >> ((r & 3) * 8);
+                const unsigned int ql = bb & 15u, qr = (bb >> 4) & 15u;
+                res0 = ql ? f0[r] - (tab[ql] * e0[r] - cx * (eW + e1[r]) - cy * (sS0 + sN0)) : f0[r];
+                res1 = qr ? f1[r] - (tab[qr] * e1[r] - cx * (e0[r] + eE) - cy * (sS1 + sN1)) : f1[r];
+            }
             const T res = res0 + res1;
             if (r & 1) {
                 if (tile) {
@@ -683,28 +738,24 @@ static void launch_smooth_b(int M, int nsweep, cudaStream_t st, const SmoothArgs
     count_launches(1);
 }
 
-template <class T>
-static void launch_smooth0(int M, int nsweep, cudaStream_t st, const SmoothArgs &sa, const T *f, const T *ein, T *e,
+template <class T, int NS, int WARPS, bool CODED>
+static void launch_smoothw_ns(int M, cudaStream_t st, const SmoothArgs &sa, const T *f, const T *ein, T *e,
+                              const T *ec, T *fc, const RedCtx &rc, MemberCtl *ctl, int inner_guard)
+{
+    constexpr int H = s0_halo(NS), TW = S0_COLS - 2 * H, TH = WARPS * S0<T>::R - 2 * H;
+    dim3 grd(cdiv(sa.L.nx, TW), cdiv(sa.L.ny, TH), M);
+    k_smoothw<T, NS, WARPS, CODED><<<grd, WARPS * 32, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+}
+
+// Level 0: 12 warps per block (96 x 64 regions for FP32); coded coarser levels: 8 warps.
+template <class T, int WARPS, bool CODED>
+static void launch_smoothw(int M, int nsweep, cudaStream_t st, const SmoothArgs &sa, const T *f, const T *ein, T *e,
                            const T *ec, T *fc, const RedCtx &rc, MemberCtl *ctl, int inner_guard)
 {
-    const Level &L = sa.L;
-    const int nt = S0_WARPS * 32;
     switch (nsweep) {
-    case 1: {
-        dim3 grd(cdiv(L.nx, s0_tw<T>(1)), cdiv(L.ny, s0_th<T>(1)), M);
-        k_smooth0<T, 1><<<grd, nt, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
-        break;
-    }
-    case 2: {
-        dim3 grd(cdiv(L.nx, s0_tw<T>(2)), cdiv(L.ny, s0_th<T>(2)), M);
-        k_smooth0<T, 2><<<grd, nt, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
-        break;
-    }
-    default: {
-        dim3 grd(cdiv(L.nx, s0_tw<T>(3)), cdiv(L.ny, s0_th<T>(3)), M);
-        k_smooth0<T, 3><<<grd, nt, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
-        break;
-    }
+    case 1: launch_smoothw_ns<T, 1, WARPS, CODED>(M, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard); break;
+    case 2: launch_smoothw_ns<T, 2, WARPS, CODED>(M, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard); break;
+    default: launch_smoothw_ns<T, 3, WARPS, CODED>(M, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard); break;
     }
     count_launches(1);
 }
@@ -713,7 +764,8 @@ template <class T>
 static void launch_smooth(int M, int nsweep, cudaStream_t st, const SmoothArgs &sa, const T *f, const T *ein, T *e,
                           const T *ec, T *fc, const RedCtx &rc, MemberCtl *ctl, int inner_guard)
 {
-    if (sa.L.open) launch_smooth0<T>(M, nsweep, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+    if (sa.L.open) launch_smoothw<T, 12, false>(M, nsweep, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+    else if (sa.L.code) launch_smoothw<T, 8, true>(M, nsweep, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
     else launch_smooth_b<T, false>(M, nsweep, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
 }
 
