@@ -261,9 +261,20 @@ static int build_geometry(envar_handle h)
         set_err(h, "grid %dx%d too small for the multigrid hierarchy", nx, ny);
         return ENVAR_EINVAL;
     }
+    // the coarse block starts at the first level from which all levels fit its shared memory
+    const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
+    auto coarse_bytes = [&](int lc) {
+        size_t ne = 0, nb = 0;
+        for (int l = lc; l < h->nlev; ++l) {
+            const size_t nx_ = hl[l].nx, ny_ = hl[l].ny;
+            ne += 2 * nx_ * ny_ + (nx_ + 1) * ny_ + nx_ * (ny_ + 1);
+            nb += nx_ * ny_;
+        }
+        return ((tsz * ne + 15) & ~(size_t)15) + nb;
+    };
     h->ncoarse = h->nlev - 1;
     for (int l = 1; l < h->nlev; ++l)
-        if (hl[l].nx <= COARSE_MAX_NX && hl[l].ny <= COARSE_MAX_NY) { h->ncoarse = l; break; }
+        if (coarse_bytes(l) <= (size_t)COARSE_SMEM_MAX) { h->ncoarse = l; break; }
     for (int l = 0; l < h->nlev; ++l) {
         const HostLevel &L = hl[l];
         uint8_t *dfl;
@@ -332,11 +343,9 @@ static int build_geometry(envar_handle h)
         h->lev[0].cy = g.cy;
     }
     // coarse block must fit in shared memory
-    size_t coarse_elems = 0;
-    for (int l = h->ncoarse; l < h->nlev; ++l) coarse_elems += 2 * (size_t)hl[l].nx * hl[l].ny;
-    if (coarse_elems * sizeof(double) > 150 * 1024) {
-        set_err(h, "coarse multigrid levels (%zu values) exceed shared memory; use nx, ny with more factors of 2",
-                coarse_elems);
+    if (coarse_bytes(h->ncoarse) > (size_t)COARSE_SMEM_MAX) {
+        set_err(h, "coarse multigrid levels (%zu bytes) exceed shared memory; use nx, ny with more factors of 2",
+                coarse_bytes(h->ncoarse));
         return ENVAR_EINVAL;
     }
 

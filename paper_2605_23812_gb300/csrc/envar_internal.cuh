@@ -20,9 +20,9 @@ constexpr int MAX_LEVELS = 12;
 constexpr int TILE_W = 64;
 constexpr int TILE_H = 16;
 constexpr int TILE_THREADS = 256;
-// The coarsest levels (nx <= 64 and ny <= 32) are solved by one block per member.
-constexpr int COARSE_MAX_NX = 64;
-constexpr int COARSE_MAX_NY = 32;
+// The coarsest levels are solved by one block per member in shared memory: from the first level
+// whose levels fit COARSE_SMEM_MAX bytes (values, guesses, conductances and fluid flags).
+constexpr int COARSE_SMEM_MAX = 200 * 1024;
 
 struct Level {
     int nx, ny, P;          // cells, pitch

@@ -594,111 +594,214 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
 
 // ------------------------------------------------------------------------------------------------
 // Coarse levels (lc .. nlev-1): one block per member runs the rest of the V-cycle in shared memory.
+// Each level's face conductances and fluid flags are staged in shared memory once per launch, so
+// the sweeps touch no global memory; the levels of at most COARSE_WARP_CELLS cells run in warp 0
+// alone, synchronised by __syncwarp instead of block barriers.
+constexpr int COARSE_WARP_CELLS = 256;
+
 struct CoarseArgs {
     Level lev[MAX_LEVELS];
-    int off[MAX_LEVELS];   // smem offsets (elements) of level l's e; f follows at + nx*ny
-    int lc, nlev;
+    int off[MAX_LEVELS];    // element offset of level l: e [n], f [n], cw [(nx+1) ny], cs [nx (ny+1)]
+    int offb[MAX_LEVELS];   // byte offset of level l's fluid flags [n]
+    int lc, lw, nlev;       // first coarse level; first level run by warp 0 alone (nlev: none)
     int nu_pre, nu_post, coarse_sweeps;
     int inner_guard;
 };
 
+// shared-memory layout of the coarse levels; returns the bytes needed
 template <class T>
-__device__ void coarse_sweep(const Level &L, T *se, const T *sf, int colour)
+size_t coarse_layout(const Level *lev, int lc, int nlev, int *off, int *offb)
 {
-    const T *cw = cw_of<T>(L), *cs = cs_of<T>(L);
-    const int n = L.nx * L.ny;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        int i = q % L.nx, j = q / L.nx;
-        if (((i + j) & 1) != colour) continue;
-        long long c = (long long)j * L.P + i;
-        T cW = cw[c], cE = cw[c + 1], cS = cs[c], cN = cs[c + L.P];
-        T d = cW + cE + cS + cN;
-        if (d == (T)0) continue;
-        T acc = sf[q];
-        if (i > 0) acc += cW * se[q - 1];
-        if (i + 1 < L.nx) acc += cE * se[q + 1];
-        if (j > 0) acc += cS * se[q - L.nx];
-        if (j + 1 < L.ny) acc += cN * se[q + L.nx];
-        se[q] = acc / d;
+    size_t ne = 0;
+    for (int l = lc; l < nlev; ++l) {
+        const size_t nx = lev[l].nx, ny = lev[l].ny;
+        off[l] = (int)ne;
+        ne += 2 * nx * ny + (nx + 1) * ny + nx * (ny + 1);
     }
-    __syncthreads();
+    size_t nb = (sizeof(T) * ne + 15) & ~(size_t)15;
+    for (int l = lc; l < nlev; ++l) {
+        offb[l] = (int)nb;
+        nb += (size_t)lev[l].nx * lev[l].ny;
+    }
+    return nb;
+}
+template size_t coarse_layout<float>(const Level *, int, int, int *, int *);
+template size_t coarse_layout<double>(const Level *, int, int, int *, int *);
+
+template <class T> struct CLev {
+    int nx, ny;
+    T *e, *f, *cw, *cs;
+    uint8_t *fl;
+};
+template <class T> __device__ __forceinline__ CLev<T> clev(const CoarseArgs &ca, unsigned char *smem, int l)
+{
+    const Level &L = ca.lev[l];
+    T *b = reinterpret_cast<T *>(smem) + ca.off[l];
+    const int n = L.nx * L.ny;
+    return CLev<T>{L.nx, L.ny, b, b + n, b + 2 * n, b + 2 * n + (L.nx + 1) * L.ny, smem + ca.offb[l]};
+}
+
+template <bool WARP> __device__ __forceinline__ void csync()
+{
+    if (WARP) __syncwarp(); else __syncthreads();
+}
+
+// one Gauss-Seidel half-sweep over the cells of one colour ((i + j) & 1 == colour)
+template <class T>
+__device__ __forceinline__ void cl_sweep(const CLev<T> &L, int colour, int tid, int nt)
+{
+    const int hx = (L.nx + 1) >> 1, n2 = hx * L.ny;
+    for (int q2 = tid; q2 < n2; q2 += nt) {
+        const int j = q2 / hx;
+        const int i = 2 * (q2 - j * hx) + ((j + colour) & 1);
+        if (i >= L.nx) continue;
+        const int q = j * L.nx + i, w = j * (L.nx + 1) + i;
+        const T cW = L.cw[w], cE = L.cw[w + 1], cS = L.cs[q], cN = L.cs[q + L.nx];
+        const T d = cW + cE + cS + cN;
+        if (d == (T)0) continue;
+        T acc = L.f[q];
+        if (i > 0) acc += cW * L.e[q - 1];
+        if (i + 1 < L.nx) acc += cE * L.e[q + 1];
+        if (j > 0) acc += cS * L.e[q - L.nx];
+        if (j + 1 < L.ny) acc += cN * L.e[q + L.nx];
+        L.e[q] = acc / d;
+    }
+}
+
+// zero guess, pre-smoothing, residual restricted (cell sums) to the next level's right-hand side
+template <class T, bool WARP>
+__device__ void cl_descend(const CoarseArgs &ca, unsigned char *smem, int l, int tid, int nt)
+{
+    const CLev<T> V = clev<T>(ca, smem, l), C = clev<T>(ca, smem, l + 1);
+    for (int q = tid; q < V.nx * V.ny; q += nt) V.e[q] = (T)0;
+    csync<WARP>();
+    for (int s = 0; s < ca.nu_pre; ++s) {
+        cl_sweep<T>(V, 0, tid, nt); csync<WARP>();
+        cl_sweep<T>(V, 1, tid, nt); csync<WARP>();
+    }
+    for (int q = tid; q < C.nx * C.ny; q += nt) {
+        const int I = q % C.nx, J = q / C.nx;
+        T sum = (T)0;
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int i = 2 * I + di, j = 2 * J + dj;
+                const int qq = j * V.nx + i, w = j * (V.nx + 1) + i;
+                const T cW = V.cw[w], cE = V.cw[w + 1], cS = V.cs[qq], cN = V.cs[qq + V.nx];
+                T ax = (cW + cE + cS + cN) * V.e[qq];
+                if (i > 0) ax -= cW * V.e[qq - 1];
+                if (i + 1 < V.nx) ax -= cE * V.e[qq + 1];
+                if (j > 0) ax -= cS * V.e[qq - V.nx];
+                if (j + 1 < V.ny) ax -= cN * V.e[qq + V.nx];
+                sum += V.f[qq] - ax;
+            }
+        C.f[q] = sum;
+    }
+    csync<WARP>();
+}
+
+// coarsest level: coarse_sweeps red-black pairs, then as many black-red pairs (symmetric)
+template <class T, bool WARP>
+__device__ void cl_coarsest(const CoarseArgs &ca, unsigned char *smem, int l, int tid, int nt)
+{
+    const CLev<T> V = clev<T>(ca, smem, l);
+    for (int q = tid; q < V.nx * V.ny; q += nt) V.e[q] = (T)0;
+    csync<WARP>();
+    for (int s = 0; s < ca.coarse_sweeps; ++s) {
+        cl_sweep<T>(V, 0, tid, nt); csync<WARP>();
+        cl_sweep<T>(V, 1, tid, nt); csync<WARP>();
+    }
+    for (int s = 0; s < ca.coarse_sweeps; ++s) {
+        cl_sweep<T>(V, 1, tid, nt); csync<WARP>();
+        cl_sweep<T>(V, 0, tid, nt); csync<WARP>();
+    }
+}
+
+// piecewise-constant prolongation of level l+1's correction onto the fluid cells of level l,
+// then post-smoothing (black-red)
+template <class T, bool WARP>
+__device__ void cl_ascend(const CoarseArgs &ca, unsigned char *smem, int l, int tid, int nt)
+{
+    const CLev<T> V = clev<T>(ca, smem, l), C = clev<T>(ca, smem, l + 1);
+    for (int q = tid; q < V.nx * V.ny; q += nt) {
+        const int i = q % V.nx, j = q / V.nx;
+        if (V.fl[q]) V.e[q] += C.e[(j >> 1) * C.nx + (i >> 1)];
+    }
+    csync<WARP>();
+    for (int s = 0; s < ca.nu_post; ++s) {
+        cl_sweep<T>(V, 1, tid, nt); csync<WARP>();
+        cl_sweep<T>(V, 0, tid, nt); csync<WARP>();
+    }
 }
 
 template <class T>
 __global__ void __launch_bounds__(1024) k_coarse(CoarseArgs ca, const T *__restrict__ fin, T *__restrict__ eout,
                                                  MemberCtl *ctl)
 {
-    extern __shared__ unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
+    extern __shared__ __align__(16) unsigned char smem[];
     const int m = blockIdx.x;
     if (ctl[m].outer_done) return;
     if (ca.inner_guard && ctl[m].inner_done) return;
-    const int lc = ca.lc, nl = ca.nlev;
-    {   // load f of level lc
-        const Level &L = ca.lev[lc];
-        T *sf = sm + ca.off[lc] + L.nx * L.ny;
-        for (int q = threadIdx.x; q < L.nx * L.ny; q += blockDim.x) {
-            int i = q % L.nx, j = q / L.nx;
-            sf[q] = fin[(long long)m * L.S + (long long)j * L.P + i];
-        }
-        __syncthreads();
-    }
+    const int lc = ca.lc, nl = ca.nlev, tid = threadIdx.x, nt = blockDim.x;
+    // stage conductances and fluid flags of every coarse level, and the right-hand side of level lc
     for (int l = lc; l < nl; ++l) {
         const Level &L = ca.lev[l];
-        T *se = sm + ca.off[l];
-        T *sf = se + L.nx * L.ny;
-        for (int q = threadIdx.x; q < L.nx * L.ny; q += blockDim.x) se[q] = (T)0;
-        __syncthreads();
-        if (l == nl - 1) {
-            for (int s = 0; s < ca.coarse_sweeps; ++s) { coarse_sweep<T>(L, se, sf, 0); coarse_sweep<T>(L, se, sf, 1); }
-            for (int s = 0; s < ca.coarse_sweeps; ++s) { coarse_sweep<T>(L, se, sf, 1); coarse_sweep<T>(L, se, sf, 0); }
-            break;
+        const CLev<T> V = clev<T>(ca, smem, l);
+        const T *cwg = cw_of<T>(L), *csg = cs_of<T>(L);
+        for (int q = tid; q < (L.nx + 1) * L.ny; q += nt) {
+            const int j = q / (L.nx + 1), i = q - j * (L.nx + 1);
+            V.cw[q] = cwg[(long long)j * L.P + i];
         }
-        for (int s = 0; s < ca.nu_pre; ++s) { coarse_sweep<T>(L, se, sf, 0); coarse_sweep<T>(L, se, sf, 1); }
-        // residual -> restriction
-        const Level &Lc = ca.lev[l + 1];
-        T *sfc = sm + ca.off[l + 1] + Lc.nx * Lc.ny;
-        const T *cw = cw_of<T>(L), *cs = cs_of<T>(L);
-        for (int q = threadIdx.x; q < Lc.nx * Lc.ny; q += blockDim.x) {
-            int I = q % Lc.nx, J = q / Lc.nx;
-            T sum = (T)0;
-            for (int dj = 0; dj < 2; ++dj)
-                for (int di = 0; di < 2; ++di) {
-                    int i = 2 * I + di, j = 2 * J + dj;
-                    int qq = j * L.nx + i;
-                    long long c = (long long)j * L.P + i;
-                    T cW = cw[c], cE = cw[c + 1], cS = cs[c], cN = cs[c + L.P];
-                    T ax = (cW + cE + cS + cN) * se[qq];
-                    if (i > 0) ax -= cW * se[qq - 1];
-                    if (i + 1 < L.nx) ax -= cE * se[qq + 1];
-                    if (j > 0) ax -= cS * se[qq - L.nx];
-                    if (j + 1 < L.ny) ax -= cN * se[qq + L.nx];
-                    sum += sf[qq] - ax;
-                }
-            sfc[q] = sum;
+        for (int q = tid; q < L.nx * (L.ny + 1); q += nt) {
+            const int j = q / L.nx, i = q - j * L.nx;
+            V.cs[q] = csg[(long long)j * L.P + i];
         }
-        __syncthreads();
+        for (int q = tid; q < L.nx * L.ny; q += nt) {
+            const int j = q / L.nx, i = q - j * L.nx;
+            V.fl[q] = L.fluid[(long long)j * L.P + i];
+            if (l == lc) V.f[q] = fin[(long long)m * L.S + (long long)j * L.P + i];
+        }
     }
-    for (int l = nl - 2; l >= lc; --l) {
-        const Level &L = ca.lev[l], &Lc = ca.lev[l + 1];
-        T *se = sm + ca.off[l];
-        T *sf = se + L.nx * L.ny;
-        const T *sec = sm + ca.off[l + 1];
-        for (int q = threadIdx.x; q < L.nx * L.ny; q += blockDim.x) {
-            int i = q % L.nx, j = q / L.nx;
-            if (L.fluid[(long long)j * L.P + i]) se[q] += sec[(j >> 1) * Lc.nx + (i >> 1)];
+    __syncthreads();
+    // block-wide levels lc .. lt-1, then the tail lt .. nl-1 (in warp 0 when its levels are small)
+    const int lt = (ca.lw < nl) ? ca.lw : nl - 1;
+    for (int l = lc; l < lt; ++l) cl_descend<T, false>(ca, smem, l, tid, nt);
+    if (ca.lw < nl) {
+        if (tid < 32) {
+            for (int l = lt; l < nl - 1; ++l) cl_descend<T, true>(ca, smem, l, tid, 32);
+            cl_coarsest<T, true>(ca, smem, nl - 1, tid, 32);
+            for (int l = nl - 2; l >= lt; --l) cl_ascend<T, true>(ca, smem, l, tid, 32);
         }
         __syncthreads();
-        for (int s = 0; s < ca.nu_post; ++s) { coarse_sweep<T>(L, se, sf, 1); coarse_sweep<T>(L, se, sf, 0); }
+    } else {
+        cl_coarsest<T, false>(ca, smem, nl - 1, tid, nt);
     }
+    for (int l = lt - 1; l >= lc; --l) cl_ascend<T, false>(ca, smem, l, tid, nt);
     {
         const Level &L = ca.lev[lc];
-        const T *se = sm + ca.off[lc];
-        for (int q = threadIdx.x; q < L.nx * L.ny; q += blockDim.x) {
-            int i = q % L.nx, j = q / L.nx;
-            eout[(long long)m * L.S + (long long)j * L.P + i] = se[q];
+        const CLev<T> V = clev<T>(ca, smem, lc);
+        for (int q = tid; q < L.nx * L.ny; q += nt) {
+            const int i = q % L.nx, j = q / L.nx;
+            eout[(long long)m * L.S + (long long)j * L.P + i] = V.e[q];
         }
     }
+}
+
+// kernel arguments and dynamic shared memory of the coarse block
+template <class T>
+static size_t coarse_args(const Level *lev, const PoissonCfg &pc, int inner_guard, CoarseArgs *ca)
+{
+    for (int l = 0; l < pc.nlev; ++l) { ca->lev[l] = lev[l]; ca->off[l] = 0; ca->offb[l] = 0; }
+    const size_t bytes = coarse_layout<T>(lev, pc.ncoarse, pc.nlev, ca->off, ca->offb);
+    ca->lc = pc.ncoarse;
+    ca->nlev = pc.nlev;
+    ca->lw = pc.nlev;
+    for (int l = pc.ncoarse; l < pc.nlev; ++l)
+        if (lev[l].nx * lev[l].ny <= COARSE_WARP_CELLS) { ca->lw = l; break; }
+    ca->nu_pre = pc.nu_pre;
+    ca->nu_post = pc.nu_post;
+    ca->coarse_sweeps = pc.coarse_sweeps;
+    ca->inner_guard = inner_guard;
+    return bytes;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -790,25 +893,10 @@ static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B,
     // coarse block
     {
         CoarseArgs ca;
-        int off = 0;
-        for (int l = 0; l < pc.nlev; ++l) {
-            ca.lev[l] = lev[l];
-            if (l >= lc) {
-                ca.off[l] = off;
-                off += 2 * lev[l].nx * lev[l].ny;
-            } else {
-                ca.off[l] = 0;
-            }
-        }
-        ca.lc = lc;
-        ca.nlev = pc.nlev;
-        ca.nu_pre = pc.nu_pre;
-        ca.nu_post = pc.nu_post;
-        ca.coarse_sweeps = pc.coarse_sweeps;
-        ca.inner_guard = inner_guard;
+        const size_t smem = coarse_args<T>(lev, pc, inner_guard, &ca);
         const T *fin = (lc == 0) ? f0 : (const T *)B.lev_f[lc];
         T *eout = (lc == 0) ? z : (T *)B.lev_e[lc];
-        k_coarse<T><<<M, 1024, sizeof(T) * off, st>>>(ca, fin, eout, ctl);
+        k_coarse<T><<<M, 1024, smem, st>>>(ca, fin, eout, ctl);
         count_launches(1);
     }
     // ascend
@@ -841,7 +929,7 @@ template void launch_vcycle<double>(const Grid &, const Level *, int, const Pois
 template <class TM>
 void prepare_poisson_kernels()
 {
-    cudaFuncSetAttribute(k_coarse<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_coarse<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, COARSE_SMEM_MAX);
 }
 template void prepare_poisson_kernels<float>();
 template void prepare_poisson_kernels<double>();
@@ -916,18 +1004,9 @@ int launch_poisson_single(int which, const Grid &g, const Level *lev, int M, con
         k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, r, e, rc, ctl, -1.0, 0);
         break;
     case 7: {
-        PoissonCfg p2 = pc;
         CoarseArgs ca;
-        int off = 0;
-        for (int l = 0; l < pc.nlev; ++l) {
-            ca.lev[l] = lev[l];
-            ca.off[l] = (l >= pc.ncoarse) ? off : 0;
-            if (l >= pc.ncoarse) off += 2 * lev[l].nx * lev[l].ny;
-        }
-        ca.lc = p2.ncoarse; ca.nlev = p2.nlev; ca.nu_pre = p2.nu_pre; ca.nu_post = p2.nu_post;
-        ca.coarse_sweeps = p2.coarse_sweeps; ca.inner_guard = 0;
-        k_coarse<TM><<<M, 1024, sizeof(TM) * off, st>>>(ca, (const TM *)B.lev_f[p2.ncoarse], (TM *)B.lev_e[p2.ncoarse],
-                                                        ctl);
+        const size_t smem = coarse_args<TM>(lev, pc, 0, &ca);
+        k_coarse<TM><<<M, 1024, smem, st>>>(ca, (const TM *)B.lev_f[pc.ncoarse], (TM *)B.lev_e[pc.ncoarse], ctl);
         break;
     }
     default: return -1;
