@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -80,6 +81,13 @@ class Dist:
     def close(self):
         if self.pg:
             self.pg.destroy_process_group()
+
+
+def whole_job(dist: "Dist", units_per_rank: float, t_local: float):
+    """Whole-job throughput over all ranks: every rank processed units_per_rank units, and the job
+    took as long as its slowest rank.  Returns (units per second, max time)."""
+    t = dist.max(t_local)
+    return dist.world * units_per_rank / t, t
 
 
 # ------------------------------------------------------------------------------------------------
@@ -188,16 +196,18 @@ def reference_arm(args, dist):
 
 
 # ------------------------------------------------------------------------------------------------
-def kernel_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def kernel_traffic(summary: str):
+    """DRAM bytes per launch from a committed ncu summary under profiles/, if the kernel's source
+    file is unchanged since the capture (its 'source' line holds the file and its sha256 prefix)."""
+    path = os.path.join(ROOT, "profiles", summary)
     try:
-        rec = json.load(open(path))[kernel]
-    except (OSError, KeyError, ValueError):
+        text = open(path).read()
+        traffic = float(re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", text, re.M).group(1))
+        src, sha = re.search(r"^source:\s*(\S+)\s+sha256\[:16\]\s*=\s*([0-9a-f]{16})", text, re.M).groups()
+        cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+    except (OSError, AttributeError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2605_23812_gb300", "csrc", rec["source"])
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return rec["dram_bytes_per_launch"] if sha == rec["source_sha256_16"] else None
+    return traffic if cur == sha else None
 
 
 def gb300_arm(args, dist):
@@ -245,8 +255,7 @@ def gb300_arm(args, dist):
         J_hist.append(float(J0_dev.item()))
         diag = ens.diagnostics()
         status = ens.member_status()
-    t = dist.max(t_dev)
-    value = dist.world * cells_per_iter * args.steps / t
+    value, t = whole_job(dist, cells_per_iter * args.steps, t_dev)
 
     # end to end through the public call with host buffers: w in pinned host memory copied in,
     # w and J0 read back, every step
@@ -257,18 +266,18 @@ def gb300_arm(args, dist):
     dist.barrier()
     t0 = time.perf_counter()
     rc = capi.lib().envar_step(ens._h, ALPHA, ctypes.c_void_p(w_host.data_ptr()), ctypes.c_void_p(J0_host.data_ptr()))
-    t_e2e = dist.max(time.perf_counter() - t0)
+    e2e_value, t_e2e = whole_job(dist, cells_per_iter, time.perf_counter() - t0)
     if rc != 0:
         raise RuntimeError(capi.lib().envar_last_error(ens._h).decode())
     J_hist.append(float(J0_host[0]))
-    e2e = {"value": dist.world * cells_per_iter / t_e2e, "unit": "cell-updates/s",
+    e2e = {"value": e2e_value, "unit": "cell-updates/s",
            "h2d_bytes_per_step": 8 * NENS, "d2h_bytes_per_step": 8 * NENS + 8,
            "envar_iter_s": t_e2e}
 
     out = None
     if dist.rank == 0:
         # roofline of the dominant kernel (level-0 multigrid prolongation + post-smoothing + dot), timed
-        # live on the handle's stream; algorithmic bytes: f, input guess, output (4 B each) and the
+        # live on the handle's stream with a cold L2; algorithmic bytes: f, input guess, output (4 B each) and the
         # coarse correction (1 B per fine cell) per cell and member, plus the open-face bits (1 B per
         # cell, shared by the members)
         with torch.cuda.stream(stream):
@@ -281,10 +290,11 @@ def gb300_arm(args, dist):
         except (OSError, ValueError):
             pass
         peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"kernel": "k_smooth<float,2,true> (level-0 prolongation + post-smoothing + r.z)", "bound": "hbm",
+        roof = {"kernel": "k_smoothw<float,2,12,0> (level-0 prolongation + post-smoothing + r.z)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "traffic": kernel_traffic("k_smooth_l0_post"), "launch_ms": ms}
+                "traffic": kernel_traffic("k_smoothw_l0_post_512x256x33.md"), "launch_ms": ms,
+                "timing": "cold L2 (256 MB write before each launch), mean of 20 launches"}
         # the plain one-member-at-a-time FP64 GPU path, bounded sample (1 member x 600 steps)
         cfg64 = pkg.default_config(NX, NY, Re=RE, n_steps=600, n_window=300, n_members=0,
                                    precision=pkg.FP64_PLAIN, div_tol=1e-10)

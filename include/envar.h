@@ -189,8 +189,9 @@ int envar_advance(envar_handle h, int n_steps);
 int envar_kernel_launches(envar_handle h, long long *count);
 
 /* Time one hot-path kernel over all member slots: two untimed launches, then `reps`
- * back-to-back launches on the handle's stream between CUDA events; *ms_per_launch
- * receives the mean.  which: 0 momentum predictor, 1 level-0 pre-smoothing + restriction,
+ * launches on the handle's stream, each preceded by a 256 MB write that evicts the L2 and
+ * timed alone between CUDA events; *ms_per_launch receives the mean.  The first call
+ * allocates the 256 MB eviction buffer (kept by the handle).  which: 0 momentum predictor, 1 level-0 pre-smoothing + restriction,
  * 2 level-0 prolongation + post-smoothing + dot product, 3 inner SpMV, 4 inner AXPY,
  * 5 outer FP64 residual, 6 projection correction with the Welford update, 7 coarse-level
  * block kernel, 8 Poisson right-hand side.  Overwrites the members' state: call
