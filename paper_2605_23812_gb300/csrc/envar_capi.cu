@@ -76,6 +76,8 @@ struct envar_handle_s {
     cudaGraphExec_t adj_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [first step][in window]
     long long adj_fwd_steps = 0, adj_rev_steps = 0, adj_stores = 0, adj_restores = 0;
     unsigned char *d_flush = nullptr;   // L2 eviction buffer of envar_time_kernel
+    unsigned char *d_cimg = nullptr;    // coarse-block constants image
+    int cimg_bytes = 0;
     char err[512] = {0};
 };
 
@@ -264,15 +266,9 @@ static int build_geometry(envar_handle h)
     }
     // the coarse block starts at the first level from which all levels fit its shared memory
     const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
-    auto coarse_bytes = [&](int lc) {
-        size_t ne = 0, nb = 0;
-        for (int l = lc; l < h->nlev; ++l) {
-            const size_t nx_ = hl[l].nx, ny_ = hl[l].ny;
-            ne += 2 * nx_ * ny_ + (nx_ + 1) * ny_ + nx_ * (ny_ + 1);
-            nb += nx_ * ny_;
-        }
-        return ((tsz * ne + 15) & ~(size_t)15) + nb;
-    };
+    Level dims[MAX_LEVELS]{};
+    for (int l = 0; l < h->nlev; ++l) { dims[l].nx = hl[l].nx; dims[l].ny = hl[l].ny; }
+    auto coarse_bytes = [&](int lc) { return (size_t)coarse_layout(dims, lc, h->nlev, tsz).total_bytes; };
     h->ncoarse = h->nlev - 1;
     for (int l = 1; l < h->nlev; ++l)
         if (coarse_bytes(l) <= (size_t)COARSE_SMEM_MAX) { h->ncoarse = l; break; }
@@ -323,6 +319,26 @@ static int build_geometry(envar_handle h)
         h->lev[l].code = dcode;
         h->lev[l].ktabf = dtf;
         h->lev[l].ktabd = dtd;
+    }
+    {   // constant part of the coarse block's shared memory (conductances and fluid flags)
+        const CoarseLayout lay = coarse_layout(dims, h->ncoarse, h->nlev, tsz);
+        std::vector<unsigned char> im((size_t)lay.image_bytes, 0);
+        auto put = [&](int byte_off, size_t idx, double v) {
+            if (h->mixed) { const float f = (float)v; std::memcpy(&im[byte_off + 4 * idx], &f, 4); }
+            else std::memcpy(&im[byte_off + 8 * idx], &v, 8);
+        };
+        for (int l = h->ncoarse; l < h->nlev; ++l) {
+            const HostLevel &L = hl[l];
+            for (int j = 0; j < L.ny; ++j)
+                for (int i = 0; i <= L.nx; ++i) put(lay.cw[l], (size_t)j * (L.nx + 1) + i, L.cw[(size_t)j * L.P + i]);
+            for (int j = 0; j <= L.ny; ++j)
+                for (int i = 0; i < L.nx; ++i) put(lay.cs[l], (size_t)j * L.nx + i, L.cs[(size_t)j * L.P + i]);
+            for (int j = 0; j < L.ny; ++j)
+                for (int i = 0; i < L.nx; ++i) im[lay.fl[l] + (size_t)j * L.nx + i] = L.F[(size_t)j * L.P + i];
+        }
+        DA(h->d_cimg, im.size());
+        CK(cudaMemcpy(h->d_cimg, im.data(), im.size(), cudaMemcpyHostToDevice));
+        h->cimg_bytes = lay.image_bytes;
     }
     {   // level-0 open-face bits (W 1, E 2, S 4, N 8) of fluid cells
         std::vector<uint8_t> op((size_t)S, 0);
@@ -683,6 +699,8 @@ extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda
         pc.max_outer = c.max_outer; pc.max_inner = c.max_inner;
         pc.inner_rtol2 = c.inner_rtol * c.inner_rtol;
         pc.rtol_abs = c.div_tol * h->g.hxy / h->g.dt;
+        pc.cimg = h->d_cimg;
+        pc.cimg_bytes = h->cimg_bytes;
         {
             const Grid &g = h->g;
             auto split = [](double d, float *hi, float *lo) { *hi = (float)d; *lo = (float)(d - (double)*hi); };

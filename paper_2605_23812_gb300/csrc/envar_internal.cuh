@@ -242,7 +242,18 @@ struct PoissonCfg {
     double rtol_abs;                // outer stop: max |r| <= rtol_abs (r = b - A x, FV form)
     int df_outer;                   // 1: outer residual / update in df64 (mixed mode)
     MixConst mc;
+    const unsigned char *cimg;      // coarse-block shared-memory image of the coarse levels' constants
+    int cimg_bytes;                 // its size (a multiple of 16)
 };
+// Shared-memory layout of the coarse block (levels lc .. nlev-1).  The constant part (per level:
+// west-face conductances [ny][nx+1], south-face conductances [ny+1][nx] in TM, fluid flags
+// [ny][nx] bytes) comes first and is copied verbatim from an image built once; the per-level
+// guess e [ny][nx] and right-hand side f [ny][nx] follow.  Offsets in bytes, each 16-aligned.
+struct CoarseLayout {
+    int cw[MAX_LEVELS], cs[MAX_LEVELS], fl[MAX_LEVELS], e[MAX_LEVELS];
+    int image_bytes, total_bytes;
+};
+CoarseLayout coarse_layout(const Level *lev, int lc, int nlev, size_t tsz);
 template <class TM> void prepare_poisson_kernels();
 template <class TM>
 void launch_vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc,

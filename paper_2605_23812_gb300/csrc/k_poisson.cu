@@ -176,6 +176,146 @@ __global__ void __launch_bounds__(256) k_axpy(Grid g, TM *__restrict__ e, TM *__
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctl[m].inner_its += 1;
 }
 
+template <class T> struct Pair2Of;
+template <> struct Pair2Of<float> { using type = float2; };
+template <> struct Pair2Of<double> { using type = double2; };
+
+// ------------------------------------------------------------------------------------------------
+// Inner CG vector kernels on level 0 (used when the level has open-face bits).
+//
+// k_spmv0: p_new = z + beta p_old, q = A p_new and the partial p^T q.  A warp owns a 64-column
+// strip of SPMV_ROWS rows, lane l the cell pair (2l, 2l+1); it walks down the strip keeping p of
+// the rows below, at and above the current one in registers, takes east / west neighbours from
+// the neighbouring lanes by shuffle (from memory at the strip's edges), and uses the uniform
+// level-0 conductances: (A p)_c = d_c p_c - cx (p_W + p_E) - cy (p_S + p_N), closed faces having
+// zero-valued neighbours (p is zero outside the fluid, as z and p_old are).
+constexpr int SPMV_ROWS = 16, SPMV_WARPS = 4;
+
+template <class T>
+__global__ void __launch_bounds__(SPMV_WARPS * 32) k_spmv0(Grid g, Level L0, const T *__restrict__ z,
+                                                          const T *__restrict__ pold, T *__restrict__ pnew,
+                                                          T *__restrict__ q, RedCtx rc, MemberCtl *ctl, int k)
+{
+    using T2 = typename Pair2Of<T>::type;
+    const int m = blockIdx.z;
+    if (ctl[m].outer_done || ctl[m].inner_done) return;
+    const long long off = (long long)m * g.S;
+    double beta = 0.0;
+    if (k > 0) {
+        double rzk = rc.red[m].val[(k & 1) ? RS_RZB : RS_RZA];
+        double rzp = rc.red[m].val[(k & 1) ? RS_RZA : RS_RZB];
+        beta = rzk / rzp;
+    }
+    const T bt = (T)beta;
+    const T cx = (T)L0.cx, cy = (T)L0.cy;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int iL = blockIdx.x * 64 + 2 * lane;
+    const bool colok = iL + 1 < g.nx;                       // nx is even
+    const int j0 = (blockIdx.y * SPMV_WARPS + w) * SPMV_ROWS;
+    const T *zm = z + off, *pm = pold + off;
+    auto ld_p = [&](int j) -> T2 {
+        if (!colok || j < 0 || j >= g.ny) return T2{(T)0, (T)0};
+        const long long c = (long long)j * g.P + iL;
+        const T2 zz = *reinterpret_cast<const T2 *>(zm + c);
+        if (k == 0) return zz;
+        const T2 pp = *reinterpret_cast<const T2 *>(pm + c);
+        return T2{zz.x + bt * pp.x, zz.y + bt * pp.y};
+    };
+    auto ld_p1 = [&](int j, int i) -> T {
+        if (i < 0 || i >= g.nx || j < 0 || j >= g.ny) return (T)0;
+        const long long c = (long long)j * g.P + i;
+        return (k == 0) ? zm[c] : zm[c] + bt * pm[c];
+    };
+    auto diag = [&](unsigned int b) {
+        return ((b & 1u) ? cx : (T)0) + ((b & 2u) ? cx : (T)0) + ((b & 4u) ? cy : (T)0) + ((b & 8u) ? cy : (T)0);
+    };
+    DotAcc<T> pq;
+    if (j0 < g.ny) {
+        T2 pS = ld_p(j0 - 1), pC = ld_p(j0);
+#pragma unroll 4
+        for (int r = 0; r < SPMV_ROWS; ++r) {
+            const int j = j0 + r;
+            if (j >= g.ny) break;
+            const T2 pN = ld_p(j + 1);
+            T pW = __shfl_up_sync(0xffffffffu, pC.y, 1), pE = __shfl_down_sync(0xffffffffu, pC.x, 1);
+            if (lane == 0) pW = ld_p1(j, iL - 1);
+            if (lane == 31) pE = ld_p1(j, iL + 2);
+            if (colok) {
+                const long long c = (long long)j * g.P + iL;
+                const unsigned int b2 = *reinterpret_cast<const unsigned short *>(L0.open + c);
+                const unsigned int bl = b2 & 15u, br = (b2 >> 8) & 15u;
+                const T ql = bl ? diag(bl) * pC.x - cx * (pW + pC.y) - cy * (pS.x + pN.x) : (T)0;
+                const T qr = br ? diag(br) * pC.y - cx * (pC.x + pE) - cy * (pS.y + pN.y) : (T)0;
+                *reinterpret_cast<T2 *>(pnew + off + c) = pC;
+                *reinterpret_cast<T2 *>(q + off + c) = T2{ql, qr};
+                pq.add(pC.x, ql);
+                pq.add(pC.y, qr);
+            }
+            pS = pC;
+            pC = pN;
+        }
+    }
+    double pqt = pq.total();
+    double tot;
+    if (publish_partial(rc, RS_PQ, m, pqt, false, &tot) && threadIdx.x == 0) {
+        rc.red[m].val[RS_PQ] = tot;
+        if (!(tot > 0.0)) ctl[m].inner_done = 1;   // breakdown: stop this member's inner loop
+    }
+}
+
+// k_axpy4: e += alpha p, r -= alpha q over the fluid-domain rows, four values per thread (two
+// aligned pairs).
+template <class T>
+__global__ void __launch_bounds__(128) k_axpy4(Grid g, T *__restrict__ e, T *__restrict__ r, const T *__restrict__ p,
+                                              const T *__restrict__ q, RedCtx rc, MemberCtl *ctl, int k)
+{
+    using T2 = typename Pair2Of<T>::type;
+    const int m = blockIdx.z;
+    if (ctl[m].outer_done || ctl[m].inner_done) return;
+    const double alpha = rc.red[m].val[(k & 1) ? RS_RZB : RS_RZA] / rc.red[m].val[RS_PQ];
+    const T a = (T)alpha;
+    const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y;
+    if (i < g.nx) {
+        const long long c = (long long)m * g.S + (long long)j * g.P + i;
+#pragma unroll
+        for (int h = 0; h < 4; h += 2) {
+            T2 ev = *reinterpret_cast<const T2 *>(e + c + h), rv = *reinterpret_cast<const T2 *>(r + c + h);
+            const T2 pv = *reinterpret_cast<const T2 *>(p + c + h), qv = *reinterpret_cast<const T2 *>(q + c + h);
+            ev.x += a * pv.x; ev.y += a * pv.y;
+            rv.x -= a * qv.x; rv.y -= a * qv.y;
+            *reinterpret_cast<T2 *>(e + c + h) = ev;
+            *reinterpret_cast<T2 *>(r + c + h) = rv;
+        }
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctl[m].inner_its += 1;
+}
+
+// launchers: the level-0 kernels above when the level has open-face bits and nx is a multiple of 4
+template <class TM>
+static void launch_spmv(const Grid &g, const Level &L0, int M, const TM *z, const TM *pold, TM *pnew, TM *q,
+                        const RedCtx &rc, MemberCtl *ctl, int k, cudaStream_t st)
+{
+    if (L0.open) {
+        dim3 grd(cdiv(g.nx, 64), cdiv(g.ny, SPMV_WARPS * SPMV_ROWS), M);
+        k_spmv0<TM><<<grd, SPMV_WARPS * 32, 0, st>>>(g, L0, z, pold, pnew, q, rc, ctl, k);
+    } else {
+        dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
+        k_spmv<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, z, pold, pnew, q, rc, ctl, k);
+    }
+}
+template <class TM>
+static void launch_axpy(const Grid &g, int M, TM *e, TM *r, const TM *p, const TM *q, const RedCtx &rc,
+                        MemberCtl *ctl, int k, cudaStream_t st)
+{
+    if (g.nx % 4 == 0) {
+        dim3 grd(cdiv(g.nx / 4, 128), g.ny, M);
+        k_axpy4<TM><<<grd, 128, 0, st>>>(g, e, r, p, q, rc, ctl, k);
+    } else {
+        dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
+        k_axpy<TM><<<grd, TILE_THREADS, 0, st>>>(g, e, r, p, q, rc, ctl, k);
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Red-black Gauss-Seidel smoothing of one multigrid level, nsweep red-black sweep pairs per launch.
 // A block owns a tile of TW x TH cells and loads it with a halo of H = 2*nsweep + 1 cells, i.e. a
@@ -601,32 +741,32 @@ constexpr int COARSE_WARP_CELLS = 256;
 
 struct CoarseArgs {
     Level lev[MAX_LEVELS];
-    int off[MAX_LEVELS];    // element offset of level l: e [n], f [n], cw [(nx+1) ny], cs [nx (ny+1)]
-    int offb[MAX_LEVELS];   // byte offset of level l's fluid flags [n]
+    CoarseLayout lay;
+    const uint4 *img;       // the constant part of the layout, lay.image_bytes
     int lc, lw, nlev;       // first coarse level; first level run by warp 0 alone (nlev: none)
     int nu_pre, nu_post, coarse_sweeps;
     int inner_guard;
 };
 
-// shared-memory layout of the coarse levels; returns the bytes needed
-template <class T>
-size_t coarse_layout(const Level *lev, int lc, int nlev, int *off, int *offb)
+CoarseLayout coarse_layout(const Level *lev, int lc, int nlev, size_t tsz)
 {
-    size_t ne = 0;
+    CoarseLayout L{};
+    auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    size_t b = 0;
     for (int l = lc; l < nlev; ++l) {
         const size_t nx = lev[l].nx, ny = lev[l].ny;
-        off[l] = (int)ne;
-        ne += 2 * nx * ny + (nx + 1) * ny + nx * (ny + 1);
+        L.cw[l] = (int)b; b = up16(b + tsz * (nx + 1) * ny);
+        L.cs[l] = (int)b; b = up16(b + tsz * nx * (ny + 1));
+        L.fl[l] = (int)b; b = up16(b + nx * ny);
     }
-    size_t nb = (sizeof(T) * ne + 15) & ~(size_t)15;
+    L.image_bytes = (int)b;
     for (int l = lc; l < nlev; ++l) {
-        offb[l] = (int)nb;
-        nb += (size_t)lev[l].nx * lev[l].ny;
+        L.e[l] = (int)b;
+        b = up16(b + tsz * 2 * (size_t)lev[l].nx * lev[l].ny);
     }
-    return nb;
+    L.total_bytes = (int)b;
+    return L;
 }
-template size_t coarse_layout<float>(const Level *, int, int, int *, int *);
-template size_t coarse_layout<double>(const Level *, int, int, int *, int *);
 
 template <class T> struct CLev {
     int nx, ny;
@@ -636,9 +776,9 @@ template <class T> struct CLev {
 template <class T> __device__ __forceinline__ CLev<T> clev(const CoarseArgs &ca, unsigned char *smem, int l)
 {
     const Level &L = ca.lev[l];
-    T *b = reinterpret_cast<T *>(smem) + ca.off[l];
-    const int n = L.nx * L.ny;
-    return CLev<T>{L.nx, L.ny, b, b + n, b + 2 * n, b + 2 * n + (L.nx + 1) * L.ny, smem + ca.offb[l]};
+    T *e = reinterpret_cast<T *>(smem + ca.lay.e[l]);
+    return CLev<T>{L.nx, L.ny, e, e + L.nx * L.ny, reinterpret_cast<T *>(smem + ca.lay.cw[l]),
+                   reinterpret_cast<T *>(smem + ca.lay.cs[l]), smem + ca.lay.fl[l]};
 }
 
 template <bool WARP> __device__ __forceinline__ void csync()
@@ -646,25 +786,32 @@ template <bool WARP> __device__ __forceinline__ void csync()
     if (WARP) __syncwarp(); else __syncthreads();
 }
 
+// Loops over a level: row j by warp (stride = warps in use), column by lane (stride 32), so no
+// thread divides by the level's width.
+#define CL_ROWS(j, tid, nt, ny) for (int j = (tid) >> 5; j < (ny); j += (nt) >> 5)
+#define CL_COLS(i, tid, n) for (int i = (tid) & 31; i < (n); i += 32)
+
 // one Gauss-Seidel half-sweep over the cells of one colour ((i + j) & 1 == colour)
 template <class T>
 __device__ __forceinline__ void cl_sweep(const CLev<T> &L, int colour, int tid, int nt)
 {
-    const int hx = (L.nx + 1) >> 1, n2 = hx * L.ny;
-    for (int q2 = tid; q2 < n2; q2 += nt) {
-        const int j = q2 / hx;
-        const int i = 2 * (q2 - j * hx) + ((j + colour) & 1);
-        if (i >= L.nx) continue;
-        const int q = j * L.nx + i, w = j * (L.nx + 1) + i;
-        const T cW = L.cw[w], cE = L.cw[w + 1], cS = L.cs[q], cN = L.cs[q + L.nx];
-        const T d = cW + cE + cS + cN;
-        if (d == (T)0) continue;
-        T acc = L.f[q];
-        if (i > 0) acc += cW * L.e[q - 1];
-        if (i + 1 < L.nx) acc += cE * L.e[q + 1];
-        if (j > 0) acc += cS * L.e[q - L.nx];
-        if (j + 1 < L.ny) acc += cN * L.e[q + L.nx];
-        L.e[q] = acc / d;
+    const int hx = (L.nx + 1) >> 1;
+    CL_ROWS(j, tid, nt, L.ny) {
+        const int par = (j + colour) & 1;
+        CL_COLS(i2, tid, hx) {
+            const int i = 2 * i2 + par;
+            if (i >= L.nx) continue;
+            const int q = j * L.nx + i, w = j * (L.nx + 1) + i;
+            const T cW = L.cw[w], cE = L.cw[w + 1], cS = L.cs[q], cN = L.cs[q + L.nx];
+            const T d = cW + cE + cS + cN;
+            if (d == (T)0) continue;
+            T acc = L.f[q];
+            if (i > 0) acc += cW * L.e[q - 1];
+            if (i + 1 < L.nx) acc += cE * L.e[q + 1];
+            if (j > 0) acc += cS * L.e[q - L.nx];
+            if (j + 1 < L.ny) acc += cN * L.e[q + L.nx];
+            L.e[q] = acc / d;
+        }
     }
 }
 
@@ -679,8 +826,7 @@ __device__ void cl_descend(const CoarseArgs &ca, unsigned char *smem, int l, int
         cl_sweep<T>(V, 0, tid, nt); csync<WARP>();
         cl_sweep<T>(V, 1, tid, nt); csync<WARP>();
     }
-    for (int q = tid; q < C.nx * C.ny; q += nt) {
-        const int I = q % C.nx, J = q / C.nx;
+    CL_ROWS(J, tid, nt, C.ny) CL_COLS(I, tid, C.nx) {
         T sum = (T)0;
         for (int dj = 0; dj < 2; ++dj)
             for (int di = 0; di < 2; ++di) {
@@ -694,7 +840,7 @@ __device__ void cl_descend(const CoarseArgs &ca, unsigned char *smem, int l, int
                 if (j + 1 < V.ny) ax -= cN * V.e[qq + V.nx];
                 sum += V.f[qq] - ax;
             }
-        C.f[q] = sum;
+        C.f[J * C.nx + I] = sum;
     }
     csync<WARP>();
 }
@@ -722,8 +868,8 @@ template <class T, bool WARP>
 __device__ void cl_ascend(const CoarseArgs &ca, unsigned char *smem, int l, int tid, int nt)
 {
     const CLev<T> V = clev<T>(ca, smem, l), C = clev<T>(ca, smem, l + 1);
-    for (int q = tid; q < V.nx * V.ny; q += nt) {
-        const int i = q % V.nx, j = q / V.nx;
+    CL_ROWS(j, tid, nt, V.ny) CL_COLS(i, tid, V.nx) {
+        const int q = j * V.nx + i;
         if (V.fl[q]) V.e[q] += C.e[(j >> 1) * C.nx + (i >> 1)];
     }
     csync<WARP>();
@@ -742,24 +888,16 @@ __global__ void __launch_bounds__(1024) k_coarse(CoarseArgs ca, const T *__restr
     if (ctl[m].outer_done) return;
     if (ca.inner_guard && ctl[m].inner_done) return;
     const int lc = ca.lc, nl = ca.nlev, tid = threadIdx.x, nt = blockDim.x;
-    // stage conductances and fluid flags of every coarse level, and the right-hand side of level lc
-    for (int l = lc; l < nl; ++l) {
-        const Level &L = ca.lev[l];
-        const CLev<T> V = clev<T>(ca, smem, l);
-        const T *cwg = cw_of<T>(L), *csg = cs_of<T>(L);
-        for (int q = tid; q < (L.nx + 1) * L.ny; q += nt) {
-            const int j = q / (L.nx + 1), i = q - j * (L.nx + 1);
-            V.cw[q] = cwg[(long long)j * L.P + i];
-        }
-        for (int q = tid; q < L.nx * (L.ny + 1); q += nt) {
-            const int j = q / L.nx, i = q - j * L.nx;
-            V.cs[q] = csg[(long long)j * L.P + i];
-        }
-        for (int q = tid; q < L.nx * L.ny; q += nt) {
-            const int j = q / L.nx, i = q - j * L.nx;
-            V.fl[q] = L.fluid[(long long)j * L.P + i];
-            if (l == lc) V.f[q] = fin[(long long)m * L.S + (long long)j * L.P + i];
-        }
+    // constants of every coarse level: one vectorised copy of the prebuilt image; right-hand side
+    // of level lc
+    {
+        uint4 *dst = reinterpret_cast<uint4 *>(smem);
+        const int nv = ca.lay.image_bytes >> 4;
+#pragma unroll 4
+        for (int q = tid; q < nv; q += nt) dst[q] = ca.img[q];
+        const Level &L = ca.lev[lc];
+        const CLev<T> V = clev<T>(ca, smem, lc);
+        CL_ROWS(j, tid, nt, L.ny) CL_COLS(i, tid, L.nx) V.f[j * L.nx + i] = fin[(long long)m * L.S + (long long)j * L.P + i];
     }
     __syncthreads();
     // block-wide levels lc .. lt-1, then the tail lt .. nl-1 (in warp 0 when its levels are small)
@@ -779,10 +917,7 @@ __global__ void __launch_bounds__(1024) k_coarse(CoarseArgs ca, const T *__restr
     {
         const Level &L = ca.lev[lc];
         const CLev<T> V = clev<T>(ca, smem, lc);
-        for (int q = tid; q < L.nx * L.ny; q += nt) {
-            const int i = q % L.nx, j = q / L.nx;
-            eout[(long long)m * L.S + (long long)j * L.P + i] = V.e[q];
-        }
+        CL_ROWS(j, tid, nt, L.ny) CL_COLS(i, tid, L.nx) eout[(long long)m * L.S + (long long)j * L.P + i] = V.e[j * L.nx + i];
     }
 }
 
@@ -790,8 +925,9 @@ __global__ void __launch_bounds__(1024) k_coarse(CoarseArgs ca, const T *__restr
 template <class T>
 static size_t coarse_args(const Level *lev, const PoissonCfg &pc, int inner_guard, CoarseArgs *ca)
 {
-    for (int l = 0; l < pc.nlev; ++l) { ca->lev[l] = lev[l]; ca->off[l] = 0; ca->offb[l] = 0; }
-    const size_t bytes = coarse_layout<T>(lev, pc.ncoarse, pc.nlev, ca->off, ca->offb);
+    for (int l = 0; l < pc.nlev; ++l) ca->lev[l] = lev[l];
+    ca->lay = coarse_layout(lev, pc.ncoarse, pc.nlev, sizeof(T));
+    ca->img = reinterpret_cast<const uint4 *>(pc.cimg);
     ca->lc = pc.ncoarse;
     ca->nlev = pc.nlev;
     ca->lw = pc.nlev;
@@ -801,7 +937,7 @@ static size_t coarse_args(const Level *lev, const PoissonCfg &pc, int inner_guar
     ca->nu_post = pc.nu_post;
     ca->coarse_sweeps = pc.coarse_sweeps;
     ca->inner_guard = inner_guard;
-    return bytes;
+    return (size_t)ca->lay.total_bytes;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -955,8 +1091,8 @@ void launch_pressure_solve(const Grid &g, const Level *lev, int M, const Poisson
         if (o == pc.max_outer) break;
         vcycle<TM>(g, lev, M, B, pc, rc, ctl, 0, 0, 1, st);
         for (int k = 0; k < pc.max_inner; ++k) {
-            k_spmv<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, z, pv[k & 1], pv[(k + 1) & 1], q, rc, ctl, k);
-            k_axpy<TM><<<grd, TILE_THREADS, 0, st>>>(g, e, r, pv[(k + 1) & 1], q, rc, ctl, k);
+            launch_spmv<TM>(g, L0, M, z, pv[k & 1], pv[(k + 1) & 1], q, rc, ctl, k, st);
+            launch_axpy<TM>(g, M, e, r, pv[(k + 1) & 1], q, rc, ctl, k, st);
             count_launches(2);
             if (k + 1 == pc.max_inner) break;   // the last update needs no new preconditioned residual
             vcycle<TM>(g, lev, M, B, pc, rc, ctl, 1, k, 0, st);
@@ -994,8 +1130,8 @@ int launch_poisson_single(int which, const Grid &g, const Level *lev, int M, con
                           rc, ctl, 0);
         return 0;
     }
-    case 3: k_spmv<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, z, pv[1], pv[0], q, rc, ctl, 1); break;
-    case 4: k_axpy<TM><<<grd, TILE_THREADS, 0, st>>>(g, e, r, pv[0], q, rc, ctl, 1); break;
+    case 3: launch_spmv<TM>(g, L0, M, z, pv[1], pv[0], q, rc, ctl, 1, st); break;
+    case 4: launch_axpy<TM>(g, M, e, r, pv[0], q, rc, ctl, 1, st); break;
     case 5:
         if (pc.df_outer) {
             launch_outer_residual_mx(g, L0, pc.mc, M, B.ms, (float *)r, (float *)e, rc, ctl, -1.0, 0, st);
