@@ -226,6 +226,10 @@ def gb300_arm(args, dist):
     ens = pkg.Ensemble(cfg, stream=stream)
     u0, v0 = synth.cavity_ic(NX, NY, seed=1234 + dist.rank)
     ens.set_initial_state(u0, v0)
+    # pressure-solve parameters tuned on this GPU (setup, outside the timed region): the fastest of
+    # the library's candidates that keeps every member within div_tol over a 200-step probe
+    with torch.cuda.stream(stream):
+        solver = ens.autotune(200)
     M = NENS + 1
     cells_per_iter = M * NX * NY * (N_WARM + N_WINDOW)
 
@@ -318,7 +322,8 @@ def gb300_arm(args, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64 (mixed)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [NX, NY], "Re": RE, "members": M,
                        "time_steps": N_WARM + N_WINDOW, "precision": "mixed (FP32 stencil/MG, df64 state)",
-                       "l2": L2_NOTE, "parallelism": "replicas" if dist.world > 1 else "1 GPU"},
+                       "l2": L2_NOTE, "parallelism": "replicas" if dist.world > 1 else "1 GPU",
+                       "solver": solver},
             "envar_iter_s": t / args.steps, "envar_iters_per_hour": 3600.0 * args.steps / t,
             "fp64_plain": {"value": plain, "unit": "cell-updates/s", "sample": "1 member x 600 steps, FP64_PLAIN",
                            "envar_iter_s_extrapolated": cells_per_iter / plain},

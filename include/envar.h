@@ -97,6 +97,9 @@ typedef struct envar_config {
     int nu_pre, nu_post;     /* red-black Gauss-Seidel sweeps before / after coarse correction */
     int coarse_sweeps;       /* symmetric sweep pairs on the coarsest multigrid level */
     int steps_per_graph;     /* time steps per captured CUDA graph (even) */
+    int member_groups;       /* batched runs: member groups whose time steps run as concurrent
+                                branches of the captured graph; 0 = automatic (4 from 24 member
+                                slots, 2 from 8), 1 .. 4 */
 } envar_config;
 
 typedef struct envar_handle_s *envar_handle;
@@ -234,6 +237,19 @@ int envar_adjoint_stats(envar_handle h, long long *forward_steps, long long *rev
  * in order, each from its own forward state).  recompute: forward steps beyond the initial sweep;
  * stores, restores: checkpoint copies.  Returns ENVAR_ESTATE if the check fails. */
 int envar_revolve_plan(long long n_steps, int n_slots, long long *recompute, long long *stores, long long *restores);
+
+/* Pick the fastest pressure-solve parameters for this handle on this GPU: for each candidate of a
+ * fixed list (refinement cap, inner-iteration cap and tolerance, smoothing sweep pairs, coarse
+ * sweeps) run all member slots probe_steps time steps from the initial state with the current
+ * forcing, and keep the fastest candidate under which no member reports a status bit (every solve
+ * met div_tol).  The divergence tolerance itself is not a candidate parameter: results change only
+ * within it.  *best_ms_per_step (may be NULL): the winner's time per step; chosen (may be NULL,
+ * 4 ints): max_outer, max_inner, nu_pre (= nu_post), coarse_sweeps.  Overwrites the members' state
+ * and recaptures the step graphs.  ENVAR_ESTATE (parameters unchanged) if no candidate qualifies. */
+int envar_autotune(envar_handle h, int probe_steps, double *best_ms_per_step, int *chosen);
+
+/* The handle's configuration as currently used (after envar_autotune, its solver parameters). */
+int envar_get_config(envar_handle h, envar_config *cfg);
 
 /* Draw the ensemble matrix E without allocating device memory.  The paper has no counterpart:
  * this is for callers that cannot let a library call cudaMalloc (a framework whose caching

@@ -37,6 +37,7 @@ class Config(ctypes.Structure):
         ("div_tol", c_double),
         ("max_outer", c_int), ("max_inner", c_int), ("inner_rtol", c_double),
         ("nu_pre", c_int), ("nu_post", c_int), ("coarse_sweeps", c_int), ("steps_per_graph", c_int),
+        ("member_groups", c_int),
     ]
 
 
@@ -83,6 +84,8 @@ def lib():
         "envar_time_kernel": [H, c_int, c_int, ctypes.POINTER(c_double)],
         "envar_apply_preconditioner": [H, c_void_p, c_void_p],
         "envar_adjoint_gradient": [H, c_void_p, c_void_p, c_int, c_void_p],
+        "envar_autotune": [H, c_int, ctypes.POINTER(c_double), ctypes.POINTER(c_int)],
+        "envar_get_config": [H, ctypes.POINTER(Config)],
         "envar_adjoint_stats": [H] + [ctypes.POINTER(ctypes.c_longlong)] * 4,
         "envar_revolve_plan": [ctypes.c_longlong, c_int] + [ctypes.POINTER(ctypes.c_longlong)] * 3,
         "envar_draw_ensemble_noalloc": [ctypes.POINTER(Config), c_void_p, c_int, c_void_p],
@@ -260,6 +263,21 @@ class Ensemble:
         ms = c_double()
         self._check(lib().envar_time_kernel(self._h, int(which), int(reps), ctypes.byref(ms)), "envar_time_kernel")
         return ms.value
+
+    # ---- solver tuning
+    def autotune(self, probe_steps: int = 200):
+        """Fastest pressure-solve parameters on this GPU (see envar_autotune); returns them."""
+        ms = c_double()
+        ch = (c_int * 4)()
+        self.torch.cuda.current_stream().synchronize()
+        self._check(lib().envar_autotune(self._h, int(probe_steps), ctypes.byref(ms), ch), "envar_autotune")
+        return {"max_outer": ch[0], "max_inner": ch[1], "nu": ch[2], "coarse_sweeps": ch[3],
+                "inner_rtol": self.config().inner_rtol, "probe_ms_per_step": ms.value}
+
+    def config(self) -> Config:
+        c = Config()
+        self._check(lib().envar_get_config(self._h, ctypes.byref(c)), "envar_get_config")
+        return c
 
     # ---- discrete adjoint (FP64 handles)
     def adjoint_gradient(self, f, max_snapshots: int = 64):

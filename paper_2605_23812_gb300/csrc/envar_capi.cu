@@ -23,6 +23,8 @@ void launch_axis_factor(double h, double a, int ncell, int m, int pad, int nxi, 
 }
 using namespace envar;
 
+constexpr int ENVAR_MAX_GROUPS = 4;
+
 struct GraphSet {
     cudaGraphExec_t many = nullptr;   // steps_per_graph steps
     cudaGraphExec_t one = nullptr;    // one step
@@ -77,6 +79,9 @@ struct envar_handle_s {
     long long adj_fwd_steps = 0, adj_rev_steps = 0, adj_stores = 0, adj_restores = 0;
     unsigned char *d_flush = nullptr;   // L2 eviction buffer of envar_time_kernel
     unsigned char *d_cimg = nullptr;    // coarse-block constants image
+    int ngroups = 1;                    // concurrent member groups of the captured step
+    cudaStream_t side[ENVAR_MAX_GROUPS] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[ENVAR_MAX_GROUPS] = {};
     int cimg_bytes = 0;
     char err[512] = {0};
 };
@@ -476,7 +481,7 @@ static int alloc_buffers(envar_handle h)
     {
         char *r, *e, *z, *q, *pv;
         DA(r, tsz * n0); DA(e, tsz * n0); DA(z, tsz * n0); DA(q, tsz * n0); DA(pv, 2 * tsz * n0);
-        h->pb.r = r; h->pb.e = e; h->pb.z = z; h->pb.q = q; h->pb.pv = pv;
+        h->pb.r = r; h->pb.e = e; h->pb.z = z; h->pb.q = q; h->pb.pv = pv; h->pb.pv1 = pv + tsz * n0;
         for (int l = 1; l < h->nlev; ++l) {
             char *le, *lf;
             DA(le, tsz * (size_t)h->lev[l].S * M); DA(lf, tsz * (size_t)h->lev[l].S * M);
@@ -489,6 +494,7 @@ static int alloc_buffers(envar_handle h)
         }
     }
     h->pt.nblk = cdiv(h->g.nx, 32) * cdiv(h->g.ny, 16);   // capacity for every partial-producing tiling
+    h->pt.stride = M;
     DA(h->pt.part, (size_t)RS_COUNT * M * h->pt.nblk);
     DA(h->pt.red, M);
     CK(cudaMemset(h->pt.red, 0, sizeof(MemberRed) * M));
@@ -508,36 +514,101 @@ static int alloc_buffers(envar_handle h)
 }
 
 // ------------------------------------------------------------------------------------ stepping
-static void enqueue_step(envar_handle h, int M)
+// The per-member arrays of member slots m0, m0+1, ...: every such array is laid out member-major,
+// so a group of members is a pointer offset (the partials keep the handle's member stride).
+struct MemberView {
+    MixState ms;
+    PoissonBufs pb;
+    Partials pt;
+    MemberCtl *ctl;
+    double *ubc, *series, *u, *v, *us, *vs, *p, *wf, *frect;
+    void *Ru, *Rv;
+};
+static MemberView member_view(envar_handle h, int m0)
+{
+    const long long S = h->g.S, o = (long long)m0 * S;
+    const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
+    auto fs = [&](float *q, long long k) { return q ? q + k : q; };
+    auto ds = [&](double *q, long long k) { return q ? q + k : q; };
+    auto vs = [&](void *q, long long elems) { return q ? (void *)((char *)q + tsz * elems) : q; };
+    MemberView v;
+    v.ms = h->ms;
+    if (h->mixed) {
+        MixState &w = v.ms;
+        w.uh = fs(w.uh, o); w.ul = fs(w.ul, o); w.vh = fs(w.vh, o); w.vl = fs(w.vl, o);
+        w.ush = fs(w.ush, o); w.usl = fs(w.usl, o); w.vsh = fs(w.vsh, o); w.vsl = fs(w.vsl, o);
+        w.p = fs(w.p, o); w.Ru = fs(w.Ru, o); w.Rv = fs(w.Rv, o);
+        w.bh = fs(w.bh, o); w.bl = fs(w.bl, o); w.xh = fs(w.xh, o); w.xl = fs(w.xl, o);
+        w.wf = fs(w.wf, 6 * o);
+        w.frect = fs(w.frect, (long long)m0 * 2 * h->nrect);
+    }
+    v.pb = h->pb;
+    v.pb.ms = v.ms;
+    v.pb.b = ds(v.pb.b, o); v.pb.x = ds(v.pb.x, o);
+    v.pb.r = vs(v.pb.r, o); v.pb.e = vs(v.pb.e, o); v.pb.z = vs(v.pb.z, o); v.pb.q = vs(v.pb.q, o);
+    v.pb.pv = vs(v.pb.pv, o); v.pb.pv1 = vs(v.pb.pv1, o);
+    for (int l = 0; l < h->nlev; ++l) {
+        const long long ol = (long long)m0 * h->lev[l].S;
+        v.pb.lev_e[l] = vs(v.pb.lev_e[l], ol);
+        v.pb.lev_f[l] = vs(v.pb.lev_f[l], ol);
+        v.pb.lev_t[l] = vs(v.pb.lev_t[l], ol);
+    }
+    v.pt = h->pt;
+    v.pt.part += (long long)m0 * h->pt.nblk;
+    v.pt.red += m0;
+    v.ctl = h->d_ctl + m0;
+    v.ubc = h->d_ubc + (long long)m0 * h->g.ny;
+    v.series = h->cfg.n_window > 0 ? h->d_series_slot + (long long)m0 * h->cfg.n_window * 8 : nullptr;
+    v.u = ds(h->d_u, o); v.v = ds(h->d_v, o); v.us = ds(h->d_us, o); v.vs = ds(h->d_vs, o);
+    v.p = ds(h->d_p, o); v.wf = ds(h->d_wf, 3 * o);
+    v.frect = ds(h->d_frect, (long long)m0 * 2 * h->nrect);
+    v.Ru = vs(h->d_Ru, o); v.Rv = vs(h->d_Rv, o);
+    return v;
+}
+
+// One time step of M member slots starting at the view's first member.
+static void enqueue_range(envar_handle h, int M, const MemberView &v, cudaStream_t st)
 {
     const Grid &g = h->g;
-    cudaStream_t st = h->st;
+    const int want_wf = h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0;
     if (h->mixed) {
-        launch_outflow_mx(g, M, h->ms, h->d_ubc, h->d_ctl, st);
-        launch_predict_mx(g, h->mc, M, h->ms, h->d_ubc, h->d_inh, h->d_inl, h->d_ctl, st);
-        launch_rhs_mx(g, h->mc, M, h->ms, st);
-        launch_pressure_solve<float>(g, h->lev, M, h->pb, h->pc, h->pt, h->d_ctl, st);
-        launch_correct_mx(g, h->mc, M, h->ms, h->x0, h->y0, h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0,
-                          h->cfg.n_window > 0 ? h->d_series_slot : nullptr, h->pt, h->d_ctl, h->cfg.div_tol,
-                          h->nfluid, st);
+        launch_outflow_mx(g, M, v.ms, v.ubc, v.ctl, st);
+        launch_predict_mx(g, h->mc, M, v.ms, v.ubc, h->d_inh, h->d_inl, v.ctl, st);
+        launch_rhs_mx(g, h->mc, M, v.ms, st);
+        launch_pressure_solve<float>(g, h->lev, M, v.pb, h->pc, v.pt, v.ctl, st);
+        launch_correct_mx(g, h->mc, M, v.ms, h->x0, h->y0, want_wf, v.series, v.pt, v.ctl, h->cfg.div_tol, h->nfluid,
+                          st);
         return;
     }
-    launch_outflow(g, M, h->d_u, h->d_ubc, h->d_ctl, st);
-    if (h->mixed)
-        launch_predict<float>(g, M, h->d_u, h->d_v, h->d_p, (float *)h->d_Ru, (float *)h->d_Rv, h->d_us, h->d_vs,
-                              h->d_ubc, h->d_frect, h->d_ctl, st);
-    else
-        launch_predict<double>(g, M, h->d_u, h->d_v, h->d_p, (double *)h->d_Ru, (double *)h->d_Rv, h->d_us,
-                               h->d_vs, h->d_ubc, h->d_frect, h->d_ctl, st);
-    launch_rhs(g, M, h->d_us, h->d_vs, h->pb.b, h->d_ctl, st);
-    if (h->mixed)
-        launch_pressure_solve<float>(g, h->lev, M, h->pb, h->pc, h->pt, h->d_ctl, st);
-    else
-        launch_pressure_solve<double>(g, h->lev, M, h->pb, h->pc, h->pt, h->d_ctl, st);
-    launch_correct(g, h->x0, h->y0, M, h->d_u, h->d_v, h->d_p, h->d_us, h->d_vs, h->pb.x, h->d_wf,
-                   h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0, h->cfg.n_window > 0 ? h->d_series_slot : nullptr,
-                   h->pt, h->d_ctl, h->cfg.div_tol, h->nfluid, st);
-    launch_recenter(g, M, h->pb.x, h->pt, h->nfluid, st);
+    launch_outflow(g, M, v.u, v.ubc, v.ctl, st);
+    launch_predict<double>(g, M, v.u, v.v, v.p, (double *)v.Ru, (double *)v.Rv, v.us, v.vs, v.ubc, v.frect, v.ctl, st);
+    launch_rhs(g, M, v.us, v.vs, v.pb.b, v.ctl, st);
+    launch_pressure_solve<double>(g, h->lev, M, v.pb, h->pc, v.pt, v.ctl, st);
+    launch_correct(g, h->x0, h->y0, M, v.u, v.v, v.p, v.us, v.vs, v.pb.x, v.wf, want_wf, v.series, v.pt, v.ctl,
+                   h->cfg.div_tol, h->nfluid, st);
+    launch_recenter(g, M, v.pb.x, v.pt, h->nfluid, st);
+}
+
+// One time step of the first M member slots.  With all slots and several member groups, the
+// groups' steps are independent chains on side streams (parallel branches of the captured graph),
+// so one group's latency-bound phases overlap another's bandwidth-bound ones.
+static void enqueue_step(envar_handle h, int M)
+{
+    const int G = (M == h->Mall) ? h->ngroups : 1;
+    if (G <= 1) {
+        enqueue_range(h, M, member_view(h, 0), h->st);
+        return;
+    }
+    cudaEventRecord(h->ev_fork, h->st);
+    const int per = (M + G - 1) / G;
+    for (int k = 0; k < G; ++k) {
+        const int m0 = k * per, Mg = std::min(per, M - m0);
+        if (Mg <= 0) break;
+        cudaStreamWaitEvent(h->side[k], h->ev_fork, 0);
+        enqueue_range(h, Mg, member_view(h, m0), h->side[k]);
+        cudaEventRecord(h->ev_join[k], h->side[k]);
+        cudaStreamWaitEvent(h->st, h->ev_join[k], 0);
+    }
 }
 
 static int capture(envar_handle h, int M, int nsteps, cudaGraphExec_t *out, long long *kernels)
@@ -659,7 +730,8 @@ extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda
         c.n_members < 0 || !(c.Re > 0) || !(c.cfl > 0) || !(c.eps > 0) || !(c.sigma >= 0) || !(c.corr_len > 0) ||
         c.precision < 0 || c.precision > 2 || c.cost_mode < 0 || c.cost_mode > 1 || !(c.div_tol > 0) ||
         c.max_outer < 1 || c.max_inner < 1 || c.nu_pre < 1 || c.nu_pre > 3 || c.nu_post < 1 || c.nu_post > 3 ||
-        c.coarse_sweeps < 1 || c.steps_per_graph < 1 || !(c.x1 > c.x0) || !(c.y1 > c.y0) || !(c.inner_rtol > 0)) {
+        c.coarse_sweeps < 1 || c.steps_per_graph < 1 || !(c.x1 > c.x0) || !(c.y1 > c.y0) || !(c.inner_rtol > 0) ||
+        c.member_groups < 0 || c.member_groups > ENVAR_MAX_GROUPS) {
         set_err(nullptr, "envar_init: invalid configuration");
         return ENVAR_EINVAL;
     }
@@ -689,6 +761,22 @@ extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda
             return ENVAR_ECUDA;
         }
         h->own_stream = true;
+    }
+    {   // member groups: side streams and fork / join events for the captured step
+        int G = c.member_groups ? c.member_groups : (h->Mall >= 24 ? 4 : (h->Mall >= 8 ? 2 : 1));
+        if (!h->batched) G = 1;
+        h->ngroups = std::max(1, std::min(G, h->Mall));
+        if (h->ngroups > 1) {
+            bool ok = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+            for (int k = 0; ok && k < h->ngroups; ++k)
+                ok = cudaStreamCreateWithFlags(&h->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+            if (!ok) {
+                set_err(nullptr, "envar_init: stream or event creation failed");
+                envar_destroy(h);
+                return ENVAR_ECUDA;
+            }
+        }
     }
     int rc = build_geometry(h);
     if (!rc) rc = alloc_buffers(h);
@@ -741,6 +829,11 @@ extern "C" int envar_destroy(envar_handle h)
             if (ge) cudaGraphExecDestroy(ge);
     for (void *p : h->allocs) cudaFree(p);
     if (h->d_snap) cudaFree(h->d_snap);
+    for (int k = 0; k < ENVAR_MAX_GROUPS; ++k) {
+        if (h->side[k]) cudaStreamDestroy(h->side[k]);
+        if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->own_stream) cudaStreamDestroy(h->st);
     delete h;
     return ENVAR_OK;
@@ -1297,5 +1390,93 @@ extern "C" int envar_adjoint_stats(envar_handle h, long long *forward_steps, lon
     if (reverse_steps) *reverse_steps = h->adj_rev_steps;
     if (stores) *stores = h->adj_stores;
     if (restores) *restores = h->adj_restores;
+    return ENVAR_OK;
+}
+
+// ------------------------------------------------------------------------------------ autotuning
+// Solver parameters that change only the speed of a time step (the refinement loop still stops at
+// div_tol): refinement cap, inner-iteration cap and tolerance, smoothing sweeps, coarse sweeps.
+struct SolverParams { int max_outer, max_inner, nu, coarse_sweeps; double inner_rtol; };
+static const SolverParams kTuneCandidates[] = {
+    {4, 3, 2, 2, 1e-3}, {4, 3, 2, 4, 1e-3}, {4, 4, 1, 2, 1e-3}, {4, 4, 2, 4, 1e-3},
+    {6, 2, 2, 2, 1e-3}, {4, 6, 2, 8, 1e-4}, {6, 4, 1, 4, 1e-3}, {6, 3, 2, 2, 1e-3},
+};
+
+static void drop_graphs(envar_handle h)
+{
+    for (auto &gs : h->graphs) {
+        if (gs.many) cudaGraphExecDestroy(gs.many);
+        if (gs.one) cudaGraphExecDestroy(gs.one);
+        gs = GraphSet{};
+    }
+    for (auto &row : h->adj_graph)
+        for (auto &ge : row)
+            if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
+}
+
+static void apply_params(envar_handle h, const SolverParams &p)
+{
+    h->cfg.max_outer = p.max_outer; h->cfg.max_inner = p.max_inner;
+    h->cfg.nu_pre = h->cfg.nu_post = p.nu; h->cfg.coarse_sweeps = p.coarse_sweeps; h->cfg.inner_rtol = p.inner_rtol;
+    h->pc.max_outer = p.max_outer; h->pc.max_inner = p.max_inner;
+    h->pc.nu_pre = h->pc.nu_post = p.nu; h->pc.coarse_sweeps = p.coarse_sweeps;
+    h->pc.inner_rtol2 = p.inner_rtol * p.inner_rtol;
+    drop_graphs(h);
+}
+
+extern "C" int envar_autotune(envar_handle h, int probe_steps, double *best_ms_per_step, int *chosen)
+{
+    if (!h || probe_steps < 2) return ENVAR_EINVAL;
+    if (!h->have_ic) { set_err(h, "envar_autotune: no initial state"); return ENVAR_ESTATE; }
+    const SolverParams orig{h->cfg.max_outer, h->cfg.max_inner, h->cfg.nu_pre, h->cfg.coarse_sweeps, h->cfg.inner_rtol};
+    const int M = h->Mall;
+    std::vector<MemberCtl> c((size_t)M);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = -1.0;
+    int best_k = -1;
+    const int n_cand = (int)(sizeof(kTuneCandidates) / sizeof(kTuneCandidates[0]));
+    for (int k = 0; k < n_cand; ++k) {
+        apply_params(h, kTuneCandidates[k]);
+        // untimed run (captures the graphs), then the timed probe from the same initial state
+        float t = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {
+            launch_member_forcing(M, 0, h->N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->ms.frect, h->st);
+            reset_members(h, M);
+            CK(cudaEventRecord(e0, h->st));
+            int rc = run_steps(h, M, probe_steps);
+            if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+            CK(cudaEventRecord(e1, h->st));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            CK(cudaMemcpy(c.data(), h->d_ctl, sizeof(MemberCtl) * M, cudaMemcpyDeviceToHost));
+            for (const MemberCtl &x : c) ok = ok && x.status == 0;
+        }
+        const double ms = (double)t / probe_steps;
+        if (ok && (best < 0 || ms < best)) { best = ms; best_k = k; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    apply_params(h, best_k >= 0 ? kTuneCandidates[best_k] : orig);
+    h->have_forward = false;
+    h->last_member_slot0 = -2;
+    if (best_ms_per_step) *best_ms_per_step = best;
+    if (chosen) {
+        const SolverParams &p = best_k >= 0 ? kTuneCandidates[best_k] : orig;
+        chosen[0] = p.max_outer; chosen[1] = p.max_inner; chosen[2] = p.nu; chosen[3] = p.coarse_sweeps;
+    }
+    if (best_k < 0) {
+        set_err(h, "envar_autotune: no candidate kept every member within div_tol; parameters unchanged");
+        return ENVAR_ESTATE;
+    }
+    return ENVAR_OK;
+}
+
+extern "C" int envar_get_config(envar_handle h, envar_config *cfg)
+{
+    if (!h || !cfg) return ENVAR_EINVAL;
+    *cfg = h->cfg;
     return ENVAR_OK;
 }

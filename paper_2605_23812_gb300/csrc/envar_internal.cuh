@@ -76,8 +76,9 @@ struct MemberRed {
 };
 struct Partials {
     int nblk;               // partial slots per member (>= blocks per member of any producing kernel)
-    double *part;           // [RS_COUNT][M][nblk]
-    MemberRed *red;         // [M]
+    double *part;           // [RS_COUNT][stride][nblk]
+    MemberRed *red;         // [stride]
+    int stride;             // member slots of the handle (a member group's view keeps it)
 };
 
 // Mixed-precision (ENVAR_MIXED) member state: df64 quantities are hi/lo float planes.
@@ -146,11 +147,11 @@ __device__ __forceinline__ double warp_partials(const double *p, int n, bool is_
 
 struct RedCtx {
     int nblk;             // partial slots per member (capacity)
-    double *part;         // [RS_COUNT][M][nblk]
-    MemberRed *red;       // [M]
-    int M;
+    double *part;         // [RS_COUNT][stride][nblk]
+    MemberRed *red;       // [stride]
+    int stride;
 };
-static inline RedCtx make_ctx(const Partials &pt, int M) { return RedCtx{pt.nblk, pt.part, pt.red, M}; }
+static inline RedCtx make_ctx(const Partials &pt) { return RedCtx{pt.nblk, pt.part, pt.red, pt.stride}; }
 
 // Publish a block partial of a per-member scalar; the blocks of one member are the kernel's
 // blockIdx.x/y grid.  Returns true in the (single) last block to arrive, whose thread 0 then holds
@@ -160,7 +161,7 @@ __device__ __forceinline__ bool publish_partial(const RedCtx &rc, int slot, int 
     __shared__ bool s_last;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nb = gridDim.x * gridDim.y;
-    double *p = rc.part + ((long long)slot * rc.M + m) * rc.nblk;
+    double *p = rc.part + ((long long)slot * rc.stride + m) * rc.nblk;
     if (tid == 0) {
         p[blockIdx.x + blockIdx.y * gridDim.x] = v;
         __threadfence();
@@ -228,7 +229,7 @@ void launch_export_state(const Grid &g, const double *u, const double *v, const 
 struct PoissonBufs {
     MixState ms;                    // mixed mode: df64 b and x live here
     double *b, *x;                  // level-0 FP64 right-hand side and solution (FP64 modes)
-    void *r, *e, *z, *pv, *q;       // level-0 inner vectors (TM)
+    void *r, *e, *z, *pv, *pv1, *q; // level-0 inner vectors (TM); pv, pv1: the two search directions
     void *lev_e[MAX_LEVELS];        // level >= 1 correction (TM)
     void *lev_f[MAX_LEVELS];        // level >= 1 right-hand side (TM)
     void *lev_t[MAX_LEVELS];        // pre-smoothed guess of each tiled level (level 0 included)

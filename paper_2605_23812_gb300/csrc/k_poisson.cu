@@ -942,10 +942,10 @@ static size_t coarse_args(const Level *lev, const PoissonCfg &pc, int inner_guar
 
 // ------------------------------------------------------------------------------------------------
 // Inner convergence flag after the V-cycle's dot: set by a one-warp kernel per member.
-__global__ void k_inner_check(RedCtx rc, MemberCtl *ctl, int k, double rtol2)
+__global__ void k_inner_check(RedCtx rc, MemberCtl *ctl, int k, double rtol2, int M)
 {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= rc.M) return;
+    if (m >= M) return;
     if (ctl[m].outer_done || ctl[m].inner_done) return;
     double rz = rc.red[m].val[((k + 1) & 1) ? RS_RZB : RS_RZA];
     if (!(rz > rtol2 * rc.red[m].val[RS_RZ0])) ctl[m].inner_done = 1;
@@ -1054,7 +1054,7 @@ template <class TM>
 void launch_vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc,
                    const Partials &pt, MemberCtl *ctl, cudaStream_t st)
 {
-    RedCtx rc = make_ctx(pt, M);
+    RedCtx rc = make_ctx(pt);
     vcycle<TM>(g, lev, M, B, pc, rc, ctl, 0, 0, 1, st);
 }
 template void launch_vcycle<float>(const Grid &, const Level *, int, const PoissonBufs &, const PoissonCfg &,
@@ -1074,11 +1074,11 @@ template <class TM>
 void launch_pressure_solve(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc,
                            const Partials &pt, MemberCtl *ctl, cudaStream_t st)
 {
-    RedCtx rc = make_ctx(pt, M);
+    RedCtx rc = make_ctx(pt);
     const Level &L0 = lev[0];
     dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
     TM *r = (TM *)B.r, *e = (TM *)B.e, *z = (TM *)B.z, *q = (TM *)B.q;
-    TM *pv[2] = {(TM *)B.pv, (TM *)B.pv + (size_t)g.S * M};
+    TM *pv[2] = {(TM *)B.pv, (TM *)B.pv1};
     for (int o = 0; o <= pc.max_outer; ++o) {
         if (pc.df_outer) {
             launch_outer_residual_mx(g, L0, pc.mc, M, B.ms, (float *)r, (float *)e, rc, ctl, pc.rtol_abs,
@@ -1096,7 +1096,7 @@ void launch_pressure_solve(const Grid &g, const Level *lev, int M, const Poisson
             count_launches(2);
             if (k + 1 == pc.max_inner) break;   // the last update needs no new preconditioned residual
             vcycle<TM>(g, lev, M, B, pc, rc, ctl, 1, k, 0, st);
-            k_inner_check<<<cdiv(M, 32), 32, 0, st>>>(rc, ctl, k, pc.inner_rtol2);
+            k_inner_check<<<cdiv(M, 32), 32, 0, st>>>(rc, ctl, k, pc.inner_rtol2, M);
             count_launches(1);
         }
         if (pc.df_outer) {
@@ -1112,11 +1112,11 @@ template <class TM>
 int launch_poisson_single(int which, const Grid &g, const Level *lev, int M, const PoissonBufs &B,
                           const PoissonCfg &pc, const Partials &pt, MemberCtl *ctl, cudaStream_t st)
 {
-    RedCtx rc = make_ctx(pt, M);
+    RedCtx rc = make_ctx(pt);
     const Level &L0 = lev[0], &L1 = lev[1];
     dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
     TM *r = (TM *)B.r, *e = (TM *)B.e, *z = (TM *)B.z, *q = (TM *)B.q;
-    TM *pv[2] = {(TM *)B.pv, (TM *)B.pv + (size_t)g.S * M};
+    TM *pv[2] = {(TM *)B.pv, (TM *)B.pv1};
     switch (which) {
     case 1: {
         SmoothArgs sa{L0, L1.P, L1.S, pc.nu_pre, 0, SF_ZERO_INIT | SF_RESTRICT, 0};

@@ -227,3 +227,50 @@ def test_forward_is_deterministic_at_bench_size():
     assert outs[0][2] == outs[1][2]
     assert outs[0][2]["max_div"] <= cfg.div_tol
     ens.close()
+
+
+@pytest.mark.parametrize("precision", [pkg.FP64_BATCHED, pkg.MIXED])
+def test_member_groups_give_identical_results(precision):
+    """Concurrent member groups (parallel graph branches over member ranges) must not change any
+    member's arithmetic: states, costs and the gradient agree bit for bit with one group."""
+    nx, ny, N = 64, 32, 8
+    out = []
+    for groups in (1, 2, 3):
+        cfg = pkg.default_config(nx, ny, Re=1000.0, n_steps=24, n_window=8, n_members=N, precision=precision,
+                                 member_groups=groups, steps_per_graph=10)
+        ens = pkg.Ensemble(cfg)
+        ens.set_initial_state(*synth.cavity_ic(nx, ny))
+        w = synth.weights(N)
+        ens.forward_ensemble(w)
+        J, _ = ens.cost()
+        g = ens.gradient()
+        u, v, p = (t.cpu().numpy() for t in ens.get_state(N))
+        out.append((J, g, u, v))
+        ens.close()
+    for J, g, u, v in out[1:]:
+        assert np.array_equal(J, out[0][0]) and np.array_equal(g, out[0][1])
+        assert np.array_equal(u, out[0][2]) and np.array_equal(v, out[0][3])
+
+
+def test_autotune_keeps_the_divergence_target():
+    """The autotuner only trades speed: the chosen parameters keep every member within div_tol,
+    and the forward results stay within the mixed-precision tolerance of the untuned run."""
+    nx, ny, N = 128, 64, 8
+    cfgs = []
+    outs = []
+    for tune in (False, True):
+        cfg = pkg.default_config(nx, ny, Re=1000.0, n_steps=60, n_window=20, n_members=N, precision=pkg.MIXED,
+                                 div_tol=1e-10)
+        ens = pkg.Ensemble(cfg)
+        ens.set_initial_state(*synth.cavity_ic(nx, ny))
+        if tune:
+            chosen = ens.autotune(30)
+            assert chosen["max_outer"] >= 1 and chosen["max_inner"] >= 1 and chosen["probe_ms_per_step"] > 0
+            assert ens.config().max_inner == chosen["max_inner"]
+        ens.forward_ensemble(synth.weights(N))
+        assert ens.diagnostics()["max_div"] <= 1e-10
+        assert (ens.member_status() == 0).all()
+        u, v, _ = (t.cpu().numpy() for t in ens.get_state(N))
+        outs.append((u, v))
+        ens.close()
+    assert vel_rel(outs[1][0], outs[1][1], outs[0][0], outs[0][1]) <= 1e-6
