@@ -28,11 +28,14 @@ template <class T> struct DotAcc;
 template <> struct DotAcc<float> {
     f2 v{0.f, 0.f};
     __device__ __forceinline__ void add(float a, float b) { v = df_add(v, two_prod(a, b)); }
+    // a0 b0 + a1 b1 rounded once in FP32 (the pair of a lane's cells), then added exactly
+    __device__ __forceinline__ void add_pair(float a0, float b0, float a1, float b1) { v = df_add_f(v, fmaf(a0, b0, a1 * b1)); }
     __device__ __forceinline__ double total() { return block_sum_df(v); }
 };
 template <> struct DotAcc<double> {
     double v = 0.0;
     __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ void add_pair(double a0, double b0, double a1, double b1) { v = fma(a0, b0, fma(a1, b1, v)); }
     __device__ __forceinline__ double total() { return block_reduce(v, false); }
 };
 
@@ -532,7 +535,7 @@ template <> __device__ __forceinline__ const double *ktab_of<double>(const Level
 // CODED = false: level 0 (uniform conductances, open-face bits).  CODED = true: a coarser level
 // whose face conductances are table entries: per cell a 16-bit code holds the table indices of its
 // W, E, S, N faces, and the update uses them explicitly, e_c = (f_c + sum_f k_f e_f) / sum_f k_f.
-template <class T, int NS, int WARPS, bool CODED>
+template <class T, int NS, int WARPS, bool CODED, int ORDER>
 __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const T *__restrict__ f,
                                                           const T *__restrict__ ein, T *__restrict__ e,
                                                           const T *__restrict__ ec, T *__restrict__ fc, RedCtx rc,
@@ -557,8 +560,9 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
     T *__restrict__ em = e + off;
     const T *__restrict__ ecm = ec + (long long)m * sa.Sc;
     const T cx = (T)L.cx, cy = (T)L.cy;
-    const bool zero = (sa.flags & SF_ZERO_INIT) != 0;
-    const bool prolong = (sa.flags & SF_PROLONG) != 0;
+    // ORDER 0: pre-smoothing (zero guess, red first, residual restricted); ORDER 1:
+    // post-smoothing (coarse correction prolonged, black first)
+    constexpr bool zero = ORDER == 0, prolong = ORDER == 1;
 
     // CODED: conductance tables [x 0..15 | y 0..15].  Level 0: diagonal and its inverse per
     // open-face pattern (W 1, E 2, S 4, N 8).
@@ -635,7 +639,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
     const int wb = (w > 0) ? w - 1 : 0, wa = (w < WARPS - 1) ? w + 1 : WARPS - 1;
 #pragma unroll
     for (int s = 0; s < 2 * NS; ++s) {
-        const int col = (s & 1) ^ sa.order;                     // colour updated: (i + j) & 1 == col
+        const int col = (s & 1) ^ ORDER;   // colour updated ((i + j) & 1 == col), known after unrolling
         const int rbuf = (s & 1) ^ 1, wbuf = s & 1;
         const T2 below = xb[rbuf][wb][1][lane];                  // top row of the warp below
         const T2 above = xb[rbuf][wa][0][lane];                  // bottom row of the warp above
@@ -673,7 +677,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
     constexpr int fb = (2 * NS - 1) & 1;                        // buffer of the last half-sweep
     const T2 below = xb[fb][wb][1][lane], above = xb[fb][wa][0][lane];
     const bool tile_col = colok && iL >= i0 && iL < i0 + TW;
-    const bool restrict_ = (sa.flags & SF_RESTRICT) != 0;
+    constexpr bool restrict_ = ORDER == 0;
     const bool want_dot = (sa.flags & (SF_DOT | SF_INIT_DOT)) != 0;
     DotAcc<T> dot;
     T racc = (T)0;
@@ -684,7 +688,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
         const long long c = (long long)j * L.P + iL;
         if (tile) {
             *reinterpret_cast<T2 *>(em + c) = T2{e0[r], e1[r]};
-            if (want_dot) { dot.add(f0[r], e0[r]); dot.add(f1[r], e1[r]); }
+            if (want_dot) dot.add_pair(f0[r], e0[r], f1[r], e1[r]);
         }
         if (restrict_) {
             const T sS0 = (r > 0) ? e0[r > 0 ? r - 1 : 0] : below.x, sN0 = (r < R - 1) ? e0[r < R - 1 ? r + 1 : 0] : above.x;
@@ -983,7 +987,12 @@ static void launch_smoothw_ns(int M, cudaStream_t st, const SmoothArgs &sa, cons
 {
     constexpr int H = s0_halo(NS), TW = S0_COLS - 2 * H, TH = WARPS * S0<T>::R - 2 * H;
     dim3 grd(cdiv(sa.L.nx, TW), cdiv(sa.L.ny, TH), M);
-    k_smoothw<T, NS, WARPS, CODED><<<grd, WARPS * 32, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+    // the warp-row kernel ties the work to the order: pre-smoothing = zero guess + restriction,
+    // post-smoothing = prolongation (+ optional dot), which is how the V-cycle calls it
+    if (sa.order)
+        k_smoothw<T, NS, WARPS, CODED, 1><<<grd, WARPS * 32, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
+    else
+        k_smoothw<T, NS, WARPS, CODED, 0><<<grd, WARPS * 32, 0, st>>>(sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
 }
 
 // Level 0: 12 warps per block (96 x 64 regions for FP32); coded coarser levels: 8 warps.
