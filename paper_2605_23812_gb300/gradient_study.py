@@ -57,8 +57,11 @@ def main():
     spin.close()
 
     # reference gradient: FP64 discrete adjoint
+    # FP64 inner CG: enough refinements and inner iterations to reach div_tol at every step of the
+    # horizon (rare steps of the unsteady flow need more than the library defaults allow)
     adj = pkg.Ensemble(pkg.default_config(nx, ny, Re=args.Re, n_steps=T, n_window=T, n_members=1,
-                                          precision=pkg.FP64_BATCHED, div_tol=1e-10), stream=stream)
+                                          precision=pkg.FP64_BATCHED, div_tol=1e-10, max_outer=20, max_inner=30,
+                                          inner_rtol=1e-6), stream=stream)
     adj.set_initial_state(u0, v0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()

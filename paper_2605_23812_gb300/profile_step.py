@@ -2,9 +2,10 @@
 
     python -m paper_2605_23812_gb300.profile_step [--steps 20] [--kernels 1,2]
 
-Builds the library, runs one forward evaluation of the 512x256 / Re 7500 / 33-member ensemble
-over --steps time steps to warm up (graph capture), then a second one inside the NVTX range
-"timed" (for ncu --nvtx --nvtx-include "timed/").  --kernels additionally launches the listed
+Builds the library, autotunes the solver parameters as bench.py does (unless --no-autotune), runs
+one forward evaluation of the 512x256 / Re 7500 / 33-member ensemble over --steps time steps to
+warm up (graph capture), then a second one inside the NVTX range "timed" (for
+ncu --nvtx --nvtx-include "timed/").  --kernels additionally launches the listed
 hot kernels standalone (envar_time_kernel, one launch each) inside the range "kernels", for
 targeted captures of a single launch.
 """
@@ -22,6 +23,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--members", type=int, default=32)
     ap.add_argument("--kernels", default="")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default solver parameters")
     args = ap.parse_args()
     import torch
 
@@ -33,6 +35,9 @@ def main():
                              n_members=args.members, precision=pkg.MIXED)
     ens = pkg.Ensemble(cfg, stream=torch.cuda.Stream())
     ens.set_initial_state(*synth.cavity_ic(512, 256))
+    if not args.no_autotune:   # the solver parameters the bench uses
+        with torch.cuda.stream(ens.stream):
+            print("solver", ens.autotune(200))
     w = synth.weights(args.members)
     ens.forward_ensemble(w)
     torch.cuda.nvtx.range_push("timed")
