@@ -192,7 +192,7 @@ template <> struct Pair2Of<double> { using type = double2; };
 // the neighbouring lanes by shuffle (from memory at the strip's edges), and uses the uniform
 // level-0 conductances: (A p)_c = d_c p_c - cx (p_W + p_E) - cy (p_S + p_N), closed faces having
 // zero-valued neighbours (p is zero outside the fluid, as z and p_old are).
-constexpr int SPMV_ROWS = 16, SPMV_WARPS = 4;
+constexpr int SPMV_ROWS = 4, SPMV_WARPS = 4;
 
 template <class T>
 __global__ void __launch_bounds__(SPMV_WARPS * 32) k_spmv0(Grid g, Level L0, const T *__restrict__ z,
