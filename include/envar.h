@@ -239,7 +239,7 @@ int envar_adjoint_stats(envar_handle h, long long *forward_steps, long long *rev
 int envar_revolve_plan(long long n_steps, int n_slots, long long *recompute, long long *stores, long long *restores);
 
 /* Pick the fastest pressure-solve parameters for this handle on this GPU: for each candidate of a
- * fixed list (refinement cap, inner-iteration cap and tolerance, smoothing sweep pairs, coarse
+ * fixed list of twelve (refinement cap, inner-iteration cap and tolerance, smoothing sweep pairs, coarse
  * sweeps) run all member slots probe_steps time steps from the initial state with the current
  * forcing, and keep the fastest candidate under which no member reports a status bit (every solve
  * met div_tol).  The divergence tolerance itself is not a candidate parameter: results change only

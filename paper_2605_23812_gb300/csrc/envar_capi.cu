@@ -1400,6 +1400,7 @@ struct SolverParams { int max_outer, max_inner, nu, coarse_sweeps; double inner_
 static const SolverParams kTuneCandidates[] = {
     {4, 3, 2, 2, 1e-3}, {4, 3, 2, 4, 1e-3}, {4, 4, 1, 2, 1e-3}, {4, 4, 2, 4, 1e-3},
     {6, 2, 2, 2, 1e-3}, {4, 6, 2, 8, 1e-4}, {6, 4, 1, 4, 1e-3}, {6, 3, 2, 2, 1e-3},
+    {5, 2, 2, 2, 1e-3}, {5, 3, 2, 2, 1e-3}, {4, 3, 1, 2, 1e-3}, {5, 2, 3, 2, 1e-3},
 };
 
 static void drop_graphs(envar_handle h)
