@@ -196,12 +196,15 @@ def reference_arm(args, dist):
 
 
 # ------------------------------------------------------------------------------------------------
-def kernel_traffic(summary: str):
+def kernel_traffic(summary: str, sweeps: int):
     """DRAM bytes per launch from a committed ncu summary under profiles/, if the kernel's source
-    file is unchanged since the capture (its 'source' line holds the file and its sha256 prefix)."""
+    file is unchanged since the capture (its 'source' line holds the file and its sha256 prefix)
+    and the captured instantiation has the sweep count the run uses (its 'sweeps' line)."""
     path = os.path.join(ROOT, "profiles", summary)
     try:
         text = open(path).read()
+        if int(re.search(r"^sweeps:\s*(\d+)", text, re.M).group(1)) != sweeps:
+            return None
         traffic = float(re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", text, re.M).group(1))
         src, sha = re.search(r"^source:\s*(\S+)\s+sha256\[:16\]\s*=\s*([0-9a-f]{16})", text, re.M).groups()
         cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
@@ -298,7 +301,7 @@ def gb300_arm(args, dist):
                 "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "traffic": kernel_traffic("k_smoothw_l0_post_512x256x33.md"), "launch_ms": ms,
+                "traffic": kernel_traffic("k_smoothw_l0_post_512x256x33.md", solver["nu"]), "launch_ms": ms,
                 "timing": "cold L2 (256 MB write before each launch), mean of 20 launches"}
         # the plain one-member-at-a-time FP64 GPU path, bounded sample (1 member x 600 steps)
         cfg64 = pkg.default_config(NX, NY, Re=RE, n_steps=600, n_window=300, n_members=0,

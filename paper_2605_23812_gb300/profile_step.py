@@ -24,6 +24,8 @@ def main():
     ap.add_argument("--members", type=int, default=32)
     ap.add_argument("--kernels", default="")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default solver parameters")
+    ap.add_argument("--nu", type=int, default=0,
+                    help="fix the smoothing sweep pairs (no autotuning: under a profiler the tuner's timings change)")
     args = ap.parse_args()
     import torch
 
@@ -33,9 +35,11 @@ def main():
     from paper_2605_23812_gb300 import synth
     cfg = pkg.default_config(512, 256, Re=7500.0, n_steps=args.steps, n_window=max(1, args.steps // 2),
                              n_members=args.members, precision=pkg.MIXED)
+    if args.nu:
+        cfg.nu_pre = cfg.nu_post = args.nu
     ens = pkg.Ensemble(cfg, stream=torch.cuda.Stream())
     ens.set_initial_state(*synth.cavity_ic(512, 256))
-    if not args.no_autotune:   # the solver parameters the bench uses
+    if not args.nu and not args.no_autotune:   # the solver parameters the bench uses
         with torch.cuda.stream(ens.stream):
             print("solver", ens.autotune(200))
     w = synth.weights(args.members)
