@@ -70,12 +70,8 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
-def lib():
-    global _lib
-    if _lib is not None:
-        return _lib
-    build()
-    L = ctypes.CDLL(_LIB)
+def _configure(L):
+    """Declare the argument and result types of every exported oracle function on a loaded library."""
     P = ctypes.POINTER(Params)
     sig = {
         "orc_version": (c_int, []),
@@ -117,13 +113,55 @@ def lib():
         "orc_envar_gradient": (c_int, [P, _dp, _dp, _dp, c_int, c_int, _dp, _dp, c_double,
                                        c_int, c_int, c_int, c_int, _dp, _dp,
                                        ctypes.POINTER(c_double), c_void_p]),
+        "orc_envar_step": (None, [c_int, _dp, _dp, c_double, c_double, _dp, ctypes.POINTER(c_double)]),
+        "orc_domain_observation": (c_int, [P, _dp, _dp, _dp, _dp, c_int, c_int, _dp]),
+        "orc_envar_gradient_domain": (c_int, [P, _dp, _dp, _dp, c_int, c_int, _dp, _dp, c_double, c_int,
+                                              c_int, c_int, _dp, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
-    _lib = L
     return L
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    _lib = _configure(ctypes.CDLL(_LIB))
+    return _lib
+
+
+class planted_mistake:
+    """Context manager for pin tests that must FAIL on a wrong oracle: compiles a copy of the
+    oracle source with one text replacement (the planted mistake) into ``workdir`` and routes
+    every oracle call inside the ``with`` block through that copy.  The product never uses it."""
+
+    def __init__(self, old: str, new: str, workdir: str):
+        self.old, self.new, self.workdir = old, new, workdir
+
+    def __enter__(self):
+        global _lib
+        src = open(_SRC).read()
+        if src.count(self.old) != 1:
+            raise ValueError(f"planted_mistake: the text to replace occurs {src.count(self.old)} times")
+        tag = abs(hash((self.old, self.new))) % 10**8
+        csrc = os.path.join(self.workdir, f"mutant_{tag}.c")
+        so = os.path.join(self.workdir, f"libmutant_{tag}.so")
+        with open(csrc, "w") as f:
+            f.write(src.replace(self.old, self.new))
+        subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-o", so, csrc,
+                        "-lm", "-lpthread"], check=True)
+        self._saved = lib()
+        _lib = _configure(ctypes.CDLL(so))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
 
 
 # ----------------------------------------------------------------------------
@@ -432,3 +470,46 @@ def envar_gradient(P: Params, u0, v0, E, w, eps: float, n_steps: int, n_window: 
     if want_series:
         out["series"] = ser[:, :n_window]
     return out
+
+
+def envar_step(w, g, alpha: float, J0_obs: float):
+    """Weight update of Sec. 3.3.1, w - alpha g / (N-1), and the total cost J(w) of Eq. (J_w)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out, jt = np.zeros(len(w)), c_double()
+    lib().orc_envar_step(len(w), w, g, float(alpha), float(J0_obs), out, ctypes.byref(jt))
+    return out, jt.value
+
+
+def domain_observation(P: Params, u0, v0, n_steps: int, n_window: int, fu=None, fv=None):
+    """Observation vector h of the DOMAIN cost, [n_window][ny][nx][2], with J_domain = ||h||^2 / 2."""
+    su, sv, _ = shapes(P)
+    fu = np.zeros(su) if fu is None else np.ascontiguousarray(fu, dtype=np.float64).reshape(su)
+    fv = np.zeros(sv) if fv is None else np.ascontiguousarray(fv, dtype=np.float64).reshape(sv)
+    h = np.zeros((n_window, P.ny, P.nx, 2))
+    rc = lib().orc_domain_observation(ctypes.byref(P), np.ascontiguousarray(u0, dtype=np.float64).reshape(su),
+                                      np.ascontiguousarray(v0, dtype=np.float64).reshape(sv), fu, fv,
+                                      int(n_steps), int(n_window), h)
+    if rc != 0:
+        raise RuntimeError(f"oracle domain observation failed ({rc})")
+    return h
+
+
+def envar_gradient_domain(P: Params, u0, v0, E, w, eps: float, n_steps: int, n_window: int,
+                          nthreads: int | None = None, region=CAVITY_REGION):
+    """Eq. (gradient_EnVar) with Y from Eq. (fdapprox) on the DOMAIN observation vector:
+    g_i = Y_i^T h_0 + (N-1) w_i.  Returns (g, ||Y_i||^2)."""
+    su, sv, _ = shapes(P)
+    E = np.asarray(E, dtype=np.float64)
+    n_ctrl, N = E.shape
+    g, yy = np.zeros(N), np.zeros(N)
+    nthreads = nthreads or min(N, os.cpu_count() or 1)
+    rc = lib().orc_envar_gradient_domain(ctypes.byref(P), np.asarray(region, dtype=np.float64),
+                                         np.ascontiguousarray(u0, dtype=np.float64).reshape(su),
+                                         np.ascontiguousarray(v0, dtype=np.float64).reshape(sv), n_ctrl, N,
+                                         np.ascontiguousarray(E.T).reshape(-1),
+                                         np.ascontiguousarray(w, dtype=np.float64), float(eps), int(n_steps),
+                                         int(n_window), int(nthreads), g, yy)
+    if rc != 0:
+        raise RuntimeError(f"oracle domain gradient failed ({rc})")
+    return g, yy

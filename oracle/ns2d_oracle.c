@@ -21,14 +21,17 @@
  *     Eq. (covarianceB) with c_xy = infinity (Sec. 3.3.2 / Sec. 4.2);
  *   - the finite-difference ensemble sensitivities of Eq. (fdapprox) and the
  *     EnVar gradient of Eq. (gradient_EnVar) in w-space (prior term
- *     (N-1) w from Eq. (J_w)).
+ *     (N-1) w from Eq. (J_w)): the scalar-anomaly form from the member costs,
+ *     and the explicit contraction Y^T (Hq_0 - y) on the sensor series and on
+ *     the domain observation vector;
+ *   - the weight update of Sec. 3.3.1 with the prior-Hessian step.
  *
  * Parity status of each function is listed with the function.  Every function
  * below is pinned by a -m "not gpu" test except where the header says
  * "parity unpinned".
  *
- * Numerical choices (the paper is silent on all of them; they are the readings
- * listed in the design doc):
+ * Numerical choices (the paper is silent on all of them, so each is a reading
+ * made for this solver):
  *   * fluid cell  <=> its centre has y > 0, or 0 < x < 1 (open cavity, staircase);
  *   * u (v) face is an unknown iff both adjacent cells are fluid; a face with
  *     one fluid neighbour is a wall (normal velocity 0); a face with no fluid
@@ -1152,6 +1155,146 @@ void orc_sensor_gradient(int N, int n_window, const double *series, double eps, 
         g[m - 1] = acc + (double)(N - 1) * w[m - 1];
     }
     free(h0); free(hi);
+}
+
+/* Weight update of Sec. 3.3.1 with the step preconditioned by the prior Hessian (N-1) I of
+ * Eq. (J_w):  w <- w - alpha g / (N-1).  Also the total cost of Eq. (J_w) at the old w,
+ * J(w) = J_obs(member 0) + (N-1)/2 w^T w.  w_out may alias w. */
+void orc_envar_step(int N, const double *w, const double *g, double alpha, double J0_obs, double *w_out,
+                    double *J_total)
+{
+    double ww = 0.0;
+    for (int i = 0; i < N; ++i) ww += w[i] * w[i];
+    double denom = (N > 1) ? (double)(N - 1) : 1.0;
+    if (J_total) *J_total = J0_obs + 0.5 * (double)(N - 1) * ww;
+    for (int i = 0; i < N; ++i) w_out[i] = w[i] - alpha * g[i] / denom;
+}
+
+/* Observation vector of the DOMAIN cost (Eq. kinenergy normalised by the window length, R = I,
+ * y = 0): h[t][cell][comp] = sqrt(dx dy / n_w) (u_c(t) - mean_t u_c) for the cell-centred
+ * velocity of fluid cells at every window step (zero on solid cells), so that
+ * J_domain = 1/2 ||h||^2.  Two passes: the window samples are stored first, then the window
+ * means are subtracted.  h: n_window * nx * ny * 2 doubles. */
+int orc_domain_observation(const orc_params *P, const double *u0, const double *v0, const double *fu,
+                           const double *fv, int n_steps, int n_window, double *h)
+{
+    if (n_window < 1 || n_window > n_steps) return -1;
+    orc_sim *s = orc_create(P);
+    if (!s) return -2;
+    orc_set_state(s, u0, v0, NULL);
+    orc_set_face_forcing(s, fu, fv);
+    int nx = s->nx, ny = s->ny;
+    size_t nc = (size_t)nx * ny;
+    orc_step(s, n_steps - n_window);
+    for (int t = 0; t < n_window; ++t) {
+        step_once(s);
+        double *ht = h + (size_t)t * nc * 2;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t k = IC(s, i, j);
+                ht[2 * k] = s->F[k] ? 0.5 * (s->u[IU(s, i, j)] + s->u[IU(s, i + 1, j)]) : 0.0;
+                ht[2 * k + 1] = s->F[k] ? 0.5 * (s->v[IV(s, i, j)] + s->v[IV(s, i, j + 1)]) : 0.0;
+            }
+    }
+    double wgt = sqrt(s->dx * s->dy / (double)n_window);
+    for (size_t q = 0; q < 2 * nc; ++q) {
+        double m = 0.0;
+        for (int t = 0; t < n_window; ++t) m += h[(size_t)t * 2 * nc + q];
+        m /= n_window;
+        for (int t = 0; t < n_window; ++t) {
+            double *x = &h[(size_t)t * 2 * nc + q];
+            *x = (*x - m) * wgt;
+        }
+    }
+    orc_destroy(s);
+    return 0;
+}
+
+typedef struct {
+    const orc_params *P;
+    const double *region, *u0, *v0, *E, *w, *h0;
+    int N, n_steps, n_window, n_ctrl;
+    double eps;
+    double *g, *ynorm2;
+    int next;
+    pthread_mutex_t lock;
+} domain_job;
+
+static void member_forcing_faces(const orc_params *P, const double *region, const double *E, const double *w,
+                                 int N, int n_ctrl, double eps, int m, double *f, double *fu, double *fv)
+{
+    for (int r = 0; r < n_ctrl; ++r) {
+        double acc = 0.0;
+        for (int k = 0; k < N; ++k) acc += E[(size_t)k * n_ctrl + r] * w[k];
+        if (m > 0) acc += eps * E[(size_t)(m - 1) * n_ctrl + r];
+        f[r] = acc;
+    }
+    orc_control_to_faces(P, region, f, fu, fv);
+}
+
+static void *domain_worker(void *arg)
+{
+    domain_job *jb = (domain_job *)arg;
+    const orc_params *P = jb->P;
+    size_t nu_ = (size_t)(P->nx + 1) * P->ny, nv_ = (size_t)P->nx * (P->ny + 1);
+    size_t nobs = (size_t)jb->n_window * P->nx * P->ny * 2;
+    double *f = (double *)xcalloc((size_t)jb->n_ctrl, sizeof(double));
+    double *fu = (double *)xcalloc(nu_, sizeof(double)), *fv = (double *)xcalloc(nv_, sizeof(double));
+    double *hi = (double *)xcalloc(nobs, sizeof(double));
+    for (;;) {
+        pthread_mutex_lock(&jb->lock);
+        int m = ++jb->next;
+        pthread_mutex_unlock(&jb->lock);
+        if (m > jb->N) break;
+        member_forcing_faces(P, jb->region, jb->E, jb->w, jb->N, jb->n_ctrl, jb->eps, m, f, fu, fv);
+        orc_domain_observation(P, jb->u0, jb->v0, fu, fv, jb->n_steps, jb->n_window, hi);
+        /* column i of Y by Eq. (fdapprox), contracted with Hq_0 - y = h0 (Eq. gradient_EnVar) */
+        double acc = 0.0, yy = 0.0;
+        for (size_t k = 0; k < nobs; ++k) {
+            double yk = (hi[k] - jb->h0[k]) / jb->eps;
+            acc += yk * jb->h0[k];
+            yy += yk * yk;
+        }
+        jb->g[m - 1] = acc + (double)(jb->N - 1) * jb->w[m - 1];
+        if (jb->ynorm2) jb->ynorm2[m - 1] = yy;
+    }
+    free(f); free(fu); free(fv); free(hi);
+    return NULL;
+}
+
+/* Eq. (gradient_EnVar) for the DOMAIN observation operator, with every column of Y from
+ * Eq. (fdapprox):  g_i = Y_i^T (Hq_0 - y) + (N-1) w_i,  Y_i = (h_i - h_0)/eps,  h_m the
+ * observation vector of member m (orc_domain_observation).  ynorm2 (may be NULL): ||Y_i||^2.
+ * For J_obs = 1/2 ||h||^2 this differs from the scalar form (J_i - J_0)/eps by exactly
+ * (eps/2) ||Y_i||^2. */
+int orc_envar_gradient_domain(const orc_params *P, const double *region, const double *u0, const double *v0,
+                              int n_ctrl, int N, const double *E, const double *w, double eps, int n_steps,
+                              int n_window, int nthreads, double *g, double *ynorm2)
+{
+    int ncc = orc_control_cells(P, region, NULL, NULL);
+    if (n_ctrl != 2 * ncc || n_window < 1) return -1;
+    size_t nu_ = (size_t)(P->nx + 1) * P->ny, nv_ = (size_t)P->nx * (P->ny + 1);
+    size_t nobs = (size_t)n_window * P->nx * P->ny * 2;
+    double *h0 = (double *)xcalloc(nobs, sizeof(double));
+    double *f = (double *)xcalloc((size_t)n_ctrl, sizeof(double));
+    double *fu = (double *)xcalloc(nu_, sizeof(double)), *fv = (double *)xcalloc(nv_, sizeof(double));
+    member_forcing_faces(P, region, E, w, N, n_ctrl, eps, 0, f, fu, fv);
+    orc_domain_observation(P, u0, v0, fu, fv, n_steps, n_window, h0);
+    free(f); free(fu); free(fv);
+    domain_job jb;
+    jb.P = P; jb.region = region; jb.u0 = u0; jb.v0 = v0; jb.E = E; jb.w = w; jb.h0 = h0;
+    jb.N = N; jb.n_steps = n_steps; jb.n_window = n_window; jb.n_ctrl = n_ctrl; jb.eps = eps;
+    jb.g = g; jb.ynorm2 = ynorm2; jb.next = 0;
+    pthread_mutex_init(&jb.lock, NULL);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > N) nthreads = N > 0 ? N : 1;
+    pthread_t *th = (pthread_t *)xcalloc((size_t)nthreads, sizeof(pthread_t));
+    for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, domain_worker, &jb);
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&jb.lock);
+    free(h0);
+    return 0;
 }
 
 typedef struct {

@@ -124,6 +124,112 @@ def test_poiseuille_vertical_fixed_point():
 
 
 # --------------------------------------------------------------------------
+# Free-slip top (Sec. 4.4 boundary conditions, the workload's reading: symmetry at the top,
+# no slip at the bottom).  Half channel of height H, periodic in x, uniform fx: the continuous
+# steady profile is u = (fx Re / 2) y (2H - y), maximal at the top.  On the MAC grid the mirror
+# ghost of the bottom wall adds h^2/4 as for Poiseuille, and the even ghost of the top
+# (u_ny = u_ny-1) is exactly the symmetry of y (2H - y) about y = H, so
+# u_j = (fx Re / 2)(y_j (2H - y_j) + h^2/4) solves the discrete equations exactly.
+# --------------------------------------------------------------------------
+def _half_channel(P, fx):
+    _, yu, _, _ = face_coords(P)
+    H = P.y1 - P.y0
+    y = yu - P.y0
+    return 0.5 * fx * P.Re * (y * (2.0 * H - y) + 0.25 * P.dy * P.dy)
+
+
+def _half_channel_drift(P, fx):
+    prof = _half_channel(P, fx)
+    u = np.repeat(prof[:, None], P.nx + 1, axis=1)
+    v = np.zeros((P.ny + 1, P.nx))
+    s = oracle.Sim(P)
+    s.set_state(u, v)
+    s.set_forcing(np.full_like(u, fx), np.zeros_like(v))
+    s.step(25)
+    u1, v1, _ = s.state()
+    return np.abs(u1 - u).max() / np.abs(u).max(), np.abs(v1).max()
+
+
+def _half_channel_params(bc_y):
+    return oracle.make_params(nx=8, ny=24, x0=0.0, x1=0.5, y0=0.0, y1=0.75, Re=40.0, dt=2e-3,
+                              bc_x=1, bc_y=bc_y, geometry=1)
+
+
+def test_free_slip_top_half_channel_fixed_point():
+    du, vmax = _half_channel_drift(_half_channel_params(0), 0.25)
+    assert du <= 1e-12 and vmax <= 1e-13, (du, vmax)
+    # a no-slip top (bc_y = 2) does not hold the half-channel profile
+    du2, _ = _half_channel_drift(_half_channel_params(2), 0.25)
+    assert du2 > 1e-4, du2
+
+
+def test_free_slip_top_pin_fails_on_a_no_slip_top(tmp_path):
+    """Plant the plausible mistake (an odd ghost, i.e. no slip, at the top) in a copy of the
+    oracle: the fixed-point pin must catch it."""
+    with oracle.planted_mistake("UG(s, i, ny) = UG(s, i, ny - 1);      /* top: free slip */",
+                                "UG(s, i, ny) = -UG(s, i, ny - 1);", str(tmp_path)):
+        du, _ = _half_channel_drift(_half_channel_params(0), 0.25)
+    assert du > 1e-4, du
+
+
+# --------------------------------------------------------------------------
+# Convective outlet (the workload's outlet reading of Sec. 4.4: du/dt + Uc du/dx = 0 at the
+# outflow face with Uc = 1, then a uniform flux shift).  A channel periodic in y carries a
+# divergence-free disturbance u = 1 + e a(x) cos(ky), v = -e a'(x) sin(ky)/k on the uniform
+# stream U = 1; linearised about U the inviscid equations are pure transport at speed 1 (the
+# pressure disturbance vanishes), so the exact outflow profile is 1 + e a(x_out - t) cos(ky),
+# averaged over the face.  The outlet values must converge to it as the grid is refined; a
+# wrong sign, neighbour or speed in the upwind update does not converge.
+# --------------------------------------------------------------------------
+def _outlet_error(nx, T=0.8, eps=1e-3, sigma=0.15, xc=1.2):
+    ny = nx // 2
+    k = TWO_PI
+    # y in [1, 2]: the inlet profile erf(y / 0.1) equals 1 to rounding there
+    P = oracle.make_params(nx=nx, ny=ny, x0=0.0, x1=2.0, y0=1.0, y1=2.0, Re=1e6, dt=0.3 * 2.0 / nx,
+                           bc_x=0, bc_y=1, geometry=1, advection=1)
+    dx, dy = P.dx, P.dy
+    bump = lambda x: np.exp(-((x - xc) / sigma) ** 2)
+    X, Y = np.meshgrid(np.arange(nx + 1) * dx, P.y0 + np.arange(ny + 1) * dy)
+    psi = Y + eps * bump(X) * np.sin(k * Y) / k          # streamfunction at cell corners
+    u0 = (psi[1:, :] - psi[:-1, :]) / dy
+    v0 = -(psi[:, 1:] - psi[:, :-1]) / dx
+    s = oracle.Sim(P)
+    s.set_state(u0, v0)
+    yc = P.y0 + (np.arange(ny) + 0.5) * dy
+    face_avg_cos = (np.sin(k * (yc + dy / 2)) - np.sin(k * (yc - dy / 2))) / (k * dy)
+    err = 0.0
+    for n in range(1, int(round(T / P.dt)) + 1):
+        s.step(1)
+        u = s.state()[0]
+        exact = 1.0 + eps * bump(P.x1 - n * P.dt) * face_avg_cos
+        err = max(err, np.abs(u[:, nx] - exact).max())
+    return err / eps
+
+
+def test_convective_outlet_converges_to_transport_solution():
+    errs = [_outlet_error(n) for n in (32, 64)]
+    assert errs[1] < 0.15, errs
+    assert errs[0] / errs[1] > 2.0, errs
+
+
+@pytest.mark.parametrize("old,new", [
+    # sign of the upwind difference
+    ("s->ub_next[j] = ub - s->P.dt * s->P.conv_speed * (ub - ui) / s->dx;",
+     "s->ub_next[j] = ub + s->P.dt * s->P.conv_speed * (ub - ui) / s->dx;"),
+    # wrong upwind neighbour (two faces in)
+    ("double ub = s->u[IU(s, nx, j)], ui = s->u[IU(s, nx - 1, j)];",
+     "double ub = s->u[IU(s, nx, j)], ui = s->u[IU(s, nx - 2, j)];"),
+    # time step dropped from the update
+    ("s->ub_next[j] = ub - s->P.dt * s->P.conv_speed * (ub - ui) / s->dx;",
+     "s->ub_next[j] = ub - s->P.conv_speed * (ub - ui) * 0.5;"),
+])
+def test_convective_outlet_pin_fails_on_planted_mistakes(tmp_path, old, new):
+    with oracle.planted_mistake(old, new, str(tmp_path)):
+        errs = [_outlet_error(n) for n in (32, 64)]
+    assert not (errs[1] < 0.15 and errs[0] / errs[1] > 2.0), errs
+
+
+# --------------------------------------------------------------------------
 # Taylor-Green, Stokes: on a square periodic MAC grid the sampled TG field is
 # discretely divergence-free and an eigenvector of the discrete Laplacian with
 # eigenvalue lam = -(4/dx^2) sin^2(dx/2) - (4/dy^2) sin^2(dy/2).  The explicit
@@ -482,6 +588,94 @@ def test_envar_gradient_matches_central_differences():
             assert np.abs(gy - gc).max() <= 0.05 * np.abs(gc).max() + 1e-12, (gy, gc)
             # forward differences of 1/2||h||^2 exceed Y^T h_0 by exactly eps/2 ||Y_i||^2 >= 0
             assert np.all(gobs - gy >= -1e-12 * np.abs(gy).max())
+
+
+def test_domain_observation_vector_reproduces_the_domain_cost():
+    """J_domain = 1/2 ||h|| ^2 for the observation vector h (Eq. kinenergy / n_w, R = I, y = 0),
+    against the two-pass cost of orc_member_run; h is mean-free over the window in every cell."""
+    P = oracle.cavity_params(32, 16, 300.0)
+    u0, v0 = synth.cavity_ic(32, 16)
+    h = oracle.domain_observation(P, u0, v0, 80, 30)
+    J = oracle.member_run(P, u0, v0, 80, 30)["J_domain"]
+    assert 0.5 * (h**2).sum() == pytest.approx(J, rel=1e-12)
+    assert np.abs(h.sum(axis=0)).max() <= 1e-12 * np.abs(h).max()
+    F = oracle.fluid_mask(P).astype(bool)
+    assert np.all(h[:, ~F, :] == 0.0)
+
+
+def _domain_case(advection):
+    P = oracle.cavity_params(32, 16, 300.0, advection=advection)
+    N, sigma, a = 3, 0.1, 0.05
+    E = oracle.ensemble_seeded(P, sigma, a, N, 1000)
+    u0, v0 = synth.cavity_ic(32, 16)
+    w = np.array([0.3, -0.2, 0.1])
+    return P, E, u0, v0, w, 100, 40
+
+
+def test_domain_gradient_exact_for_linear_dynamics():
+    """Stokes flow (no advection term): the velocity, hence h, is affine in the forcing, so Y of
+    Eq. (fdapprox) is exact for any eps and Y^T h_0 equals the true gradient of J_obs = 1/2||h||^2.
+    Central differences of a quadratic J are exact too, so all three agree to rounding, while the
+    scalar form (J_i - J_0)/eps carries exactly the bias (eps/2)||Y_i||^2."""
+    P, E, u0, v0, w, n_steps, n_window = _domain_case(0)
+    N = E.shape[1]
+
+    def Jobs(f):
+        fu, fv = oracle.control_to_faces(P, f)
+        return oracle.member_run(P, u0, v0, n_steps, n_window, fu, fv)["J_domain"]
+
+    f0 = E @ w
+    h = 0.05
+    gc = np.array([(Jobs(f0 + h * E[:, i]) - Jobs(f0 - h * E[:, i])) / (2 * h) for i in range(N)])
+    for eps in (1e-2, 1e-1):
+        g, yy = oracle.envar_gradient_domain(P, u0, v0, E, w, eps, n_steps, n_window, nthreads=3)
+        np.testing.assert_allclose(g - (N - 1) * w, gc, rtol=1e-7, atol=1e-9 * np.abs(gc).max())
+        J = oracle.envar_gradient(P, u0, v0, E, w, eps, n_steps, n_window, nthreads=4)["J"]
+        scalar = (J[1:] - J[0]) / eps
+        np.testing.assert_allclose(scalar - (g - (N - 1) * w), 0.5 * eps * yy, rtol=1e-6)
+        assert np.all(yy > 0)
+
+
+def test_domain_gradient_identity_and_first_order_convergence():
+    """Navier-Stokes: the identity (J_i - J_0)/eps = Y_i^T h_0 + (eps/2)||Y_i||^2 holds for the
+    forward-difference Y (J from the independent two-pass cost), and Y^T h_0 converges to the
+    central-difference gradient at first order in eps."""
+    P, E, u0, v0, w, n_steps, n_window = _domain_case(1)
+    N = E.shape[1]
+
+    def Jobs(f):
+        fu, fv = oracle.control_to_faces(P, f)
+        return oracle.member_run(P, u0, v0, n_steps, n_window, fu, fv)["J_domain"]
+
+    f0 = E @ w
+    hc = 1e-3
+    gc = np.array([(Jobs(f0 + hc * E[:, i]) - Jobs(f0 - hc * E[:, i])) / (2 * hc) for i in range(N)])
+    errs = []
+    for eps in (4e-2, 2e-2):
+        g, yy = oracle.envar_gradient_domain(P, u0, v0, E, w, eps, n_steps, n_window, nthreads=3)
+        J = oracle.envar_gradient(P, u0, v0, E, w, eps, n_steps, n_window, nthreads=4)["J"]
+        gy = g - (N - 1) * w
+        np.testing.assert_allclose((J[1:] - J[0]) / eps - gy, 0.5 * eps * yy, rtol=1e-6)
+        errs.append(np.abs(gy - gc).max())
+    assert errs[1] < 0.7 * errs[0], errs
+
+
+def test_envar_step_update_and_total_cost():
+    """Sec. 3.3.1 update with the prior-Hessian step: on the prior term alone (J_obs constant,
+    g = (N-1) w) a unit step lands on its minimiser w = 0 and alpha = 1/2 halves w; the total cost
+    is Eq. (J_w)."""
+    rng = np.random.default_rng(11)
+    N = 7
+    w = rng.standard_normal(N)
+    w1, J = oracle.envar_step(w, (N - 1) * w, 1.0, 0.25)
+    np.testing.assert_array_equal(w1, np.zeros(N))
+    assert J == pytest.approx(0.25 + 0.5 * (N - 1) * (w @ w), rel=1e-15)
+    w2, _ = oracle.envar_step(w, (N - 1) * w, 0.5, 0.0)
+    np.testing.assert_allclose(w2, 0.5 * w, rtol=1e-15)
+    # a quadratic observation cost 1/2 c |w|^2 on top: the step moves along -g scaled by 1/(N-1)
+    g = (N - 1 + 3.0) * w
+    w3, _ = oracle.envar_step(w, g, 0.5, 0.0)
+    np.testing.assert_allclose(w3, w * (1.0 - 0.5 * (N + 2) / (N - 1)), rtol=1e-14)
 
 
 # --------------------------------------------------------------------------
