@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define ENVAR_ABI_VERSION 1
+#define ENVAR_ABI_VERSION 2
 
 enum {
     ENVAR_OK = 0,
@@ -54,8 +54,14 @@ enum {
     ENVAR_FP64_PLAIN = 0,   /* one member at a time, all arithmetic FP64 */
     ENVAR_FP64_BATCHED = 1, /* all N+1 members per launch, all arithmetic FP64 */
     ENVAR_MIXED = 2         /* all members per launch; FP32 tendencies, FP32 multigrid and inner
-                               CG; FP64 state, FP64 Poisson residual with iterative refinement,
-                               FP64 dot products and FP64 cost accumulation */
+                               CG vectors, whose dot products accumulate FP32 products (pairs
+                               rounded once) in df64; velocity state, predictor, Poisson
+                               right-hand side and solution, the outer Poisson residual of the
+                               iterative refinement and the Welford cost accumulators in double-float
+                               (df64: a pair of floats, about 48 significant bits, on the FP32 pipe);
+                               per-block partial sums, member costs and the gradient in FP64.  The
+                               outer refinement stops at the same divergence tolerance (div_tol) as
+                               the FP64 modes. */
 };
 
 /* Observation operator H of Sec. 4.1. */
@@ -144,20 +150,37 @@ int envar_forward_ensemble(envar_handle h, const double *w_dev);
  * J_prior = (N-1)/2 w^T w of Eq. (J_w) for the w of that run (either may be NULL). */
 int envar_cost(envar_handle h, double *J_host, double *J_prior_host);
 
-/* EnVar gradient of Eq. (gradient_EnVar) for the last forward run: g_host[N].
- * SENSORS: Y from Eq. (fdapprox) on the sensor time series, g = Y^T (Hq_0 - y) + (N-1) w.
- * DOMAIN: g_i = (J_i - J_0)/eps + (N-1) w_i  (= Y_i^T (Hq_0 - y) + O(eps)).
- * df_dev (nullable, n_ctrl doubles, device) receives E g / (N-1). */
+/* EnVar gradient of Eq. (gradient_EnVar) for the last forward run: g_host[N],
+ *   g = Y^T (Hq_0 - y) + (N-1) w,  Y_i = (H q_i - H q_0)/eps  (Eq. fdapprox),  R = I, y = 0.
+ * SENSORS: H q_m = the sensor series of member m minus its window mean; the contraction runs over
+ *   the 8 n_window observations.
+ * DOMAIN: H q_m = sqrt(dx dy / n_w) (cell-centred velocity minus its window mean) over every fluid
+ *   cell and window step; the forward run accumulates, per cell and member, the Welford sums of
+ *   d = u_m - u_0, so Y_i^T h_0 = (J_i - J_0 - 1/2 ||h_i - h_0||^2)/eps exactly (no (eps/2)||Y_i||^2
+ *   term of the scalar-anomaly form).
+ * A perturbed member whose status word is nonzero (envar_member_status) contributes no column of
+ * Y: its component is (N-1) w_i; envar_excluded_members counts them.  ENVAR_ESTATE if the
+ * unperturbed member 0 failed.  df_dev (nullable, n_ctrl doubles, device) receives E g / (N-1). */
 int envar_gradient(envar_handle h, double *g_host, double *df_dev);
 
-/* One EnVar iteration: forward ensemble at w, costs, gradient, and the update
+/* The scalar-anomaly form of the same gradient, g_i = (J_i - J_0)/eps + (N-1) w_i
+ * (= Y_i^T (Hq_0 - y) + (eps/2)||Y_i||^2 + (N-1) w_i), for comparison: g_host[N].  Excluded
+ * members as in envar_gradient. */
+int envar_gradient_scalar(envar_handle h, double *g_host);
+
+/* Number of perturbed members of the last forward run left out of the gradient (nonzero status). */
+int envar_excluded_members(envar_handle h, int *count);
+
+/* One EnVar iteration: forward ensemble at w, costs, gradient (envar_gradient), and the update
  * w <- w - alpha g / (N-1) (Sec. 3.3.1 weight update with the prior-Hessian
  * step).  w_inout_host: N doubles (host, in/out).  J0_out_host (nullable):
- * total cost J(w) = J_obs(member 0) + J_prior before the update. */
+ * total cost J(w) = J_obs(member 0) + J_prior before the update.  ENVAR_ESTATE (w unchanged)
+ * if the unperturbed member failed. */
 int envar_step(envar_handle h, double alpha, double *w_inout_host, double *J0_out_host);
 
 /* envar_step with device-resident w_inout_dev (N doubles) and J0_out_dev (nullable, 1 double):
- * no host copy of the step's inputs or results. */
+ * no host copy of the step's inputs or results, and no host synchronisation, so a failed
+ * unperturbed member is not detected here: check envar_member_status after the step. */
 int envar_step_device(envar_handle h, double alpha, double *w_inout_dev, double *J0_out_dev);
 
 /* Run ONE member with a given control vector f (n_ctrl doubles, device) over
@@ -258,8 +281,10 @@ int envar_get_config(envar_handle h, envar_config *cfg);
  * (n_ctrl x N column-major, E_dev caller-owned device memory) and uses as scratch a file-scope
  * device array of ENVAR_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until exit.
  * No cudaMalloc / cudaFree or allocating library routine is called.  The first call on a device
- * (with that device current) looks up the array's device address; make it before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race.  Configurations needing
+ * (with that device current) looks up the array's device address.  Every call copies from host
+ * memory and synchronises its stream, so no call may be made while its stream (or, in global
+ * capture mode, any stream) is being captured.  All calls share the array: calls that overlap on
+ * the GPU race.  Configurations needing
  * more scratch than the maximum are rejected (ENVAR_EINVAL); the message of a failure is returned
  * by envar_last_error(NULL).  Runs on cuda_stream (NULL = legacy default) and synchronises it. */
 #define ENVAR_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)

@@ -70,6 +70,8 @@ def lib():
         "envar_forward_ensemble": [H, c_void_p],
         "envar_cost": [H, c_void_p, c_void_p],
         "envar_gradient": [H, c_void_p, c_void_p],
+        "envar_gradient_scalar": [H, c_void_p],
+        "envar_excluded_members": [H, ctypes.POINTER(c_int)],
         "envar_step": [H, c_double, c_void_p, c_void_p],
         "envar_step_device": [H, c_double, c_void_p, c_void_p],
         "envar_forward_control": [H, c_void_p, c_void_p],
@@ -200,6 +202,17 @@ class Ensemble:
         df = self.torch.empty(self.n_ctrl, dtype=self.torch.float64, device="cuda") if want_df else None
         self._check(lib().envar_gradient(self._h, _np_ptr(g), _ptr(df)), "envar_gradient")
         return (g, df) if want_df else g
+
+    def gradient_scalar(self):
+        """Scalar-anomaly form (J_i - J_0)/eps + (N-1) w_i of the last forward run."""
+        g = np.zeros(self.N)
+        self._check(lib().envar_gradient_scalar(self._h, _np_ptr(g)), "envar_gradient_scalar")
+        return g
+
+    def excluded_members(self) -> int:
+        n = c_int()
+        self._check(lib().envar_excluded_members(self._h, ctypes.byref(n)), "envar_excluded_members")
+        return n.value
 
     def step(self, alpha, w):
         w = np.ascontiguousarray(w, dtype=np.float64).copy()

@@ -55,6 +55,9 @@ struct envar_handle_s {
     void *d_Ru = nullptr, *d_Rv = nullptr;
     size_t tend_bytes = 0;
     double *d_ubc = nullptr, *d_wf = nullptr, *d_series_slot = nullptr, *d_series = nullptr;
+    double *d_wd = nullptr;           // FP64 Welford of d = u - u_0 (3 planes per member slot)
+    double *d_traj = nullptr;         // FP64_PLAIN: member 0's window samples [n_window][2][S]
+    int *d_status = nullptr;          // status words of the N+1 members of the last forward run
     PoissonBufs pb{};
     PoissonCfg pc{};
     Partials pt{};
@@ -65,7 +68,8 @@ struct envar_handle_s {
     float *d_inh = nullptr, *d_inl = nullptr;
     // results
     double *d_Jd_slot = nullptr, *d_Js_slot = nullptr, *d_Jd = nullptr, *d_Js = nullptr, *d_costpart = nullptr;
-    double *d_w = nullptr, *d_g = nullptr, *d_jprior = nullptr;
+    double *d_Yd_slot = nullptr, *d_Yd = nullptr;   // 1/2 ||h_m - h_0||^2 per member (DOMAIN)
+    double *d_w = nullptr, *d_g = nullptr, *d_jprior = nullptr, *d_gscalar = nullptr;
     std::vector<MemberCtl> ctl_all;
     bool have_forward = false, have_ic = false;
     int last_member_slot0 = -1;       // member held in slot 0 after a plain-mode run
@@ -82,6 +86,7 @@ struct envar_handle_s {
     int ngroups = 1;                    // concurrent member groups of the captured step
     cudaStream_t side[ENVAR_MAX_GROUPS] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[ENVAR_MAX_GROUPS] = {};
+    cudaEvent_t ev_solved0 = nullptr;   // member 0's pressure increment is final (group 0)
     int cimg_bytes = 0;
     char err[512] = {0};
 };
@@ -457,6 +462,7 @@ static int alloc_buffers(envar_handle h)
         DA(ms.p, n0); DA(ms.Ru, n0); DA(ms.Rv, n0);
         DA(ms.bh, n0); DA(ms.bl, n0); DA(ms.xh, n0); DA(ms.xl, n0);
         if (h->cfg.cost_mode == ENVAR_COST_DOMAIN) DA(ms.wf, 6 * n0);
+        if (h->cfg.cost_mode == ENVAR_COST_DOMAIN && h->N > 0) DA(ms.wd, 4 * n0);
         DA(ms.frect, (size_t)M * 2 * h->nrect);
         DA(h->ic.uh, S); DA(h->ic.ul, S); DA(h->ic.vh, S); DA(h->ic.vl, S);
         CK(cudaMemset(h->ic.uh, 0, sizeof(float) * S)); CK(cudaMemset(h->ic.ul, 0, sizeof(float) * S));
@@ -471,6 +477,10 @@ static int alloc_buffers(envar_handle h)
         DA(a, h->tend_bytes); DA(b, h->tend_bytes);
         h->d_Ru = a; h->d_Rv = b;
         if (h->cfg.cost_mode == ENVAR_COST_DOMAIN) DA(h->d_wf, 3 * n0);
+        if (h->cfg.cost_mode == ENVAR_COST_DOMAIN && h->N > 0) {
+            DA(h->d_wd, 3 * n0);
+            if (!h->batched && h->cfg.n_window > 0) DA(h->d_traj, (size_t)h->cfg.n_window * 2 * S);
+        }
     }
     DA(h->d_ubc, (size_t)M * h->g.ny);
     const int nw = std::max(h->cfg.n_window, 1);
@@ -507,8 +517,12 @@ static int alloc_buffers(envar_handle h)
     DA(h->d_frect, (size_t)M * 2 * h->nrect);
     DA(h->d_Jd_slot, M); DA(h->d_Js_slot, M);
     DA(h->d_Jd, N + 1); DA(h->d_Js, N + 1);
-    DA(h->d_costpart, (size_t)64 * M);
-    DA(h->d_w, std::max(N, 1)); DA(h->d_g, std::max(N, 1)); DA(h->d_jprior, 1);
+    DA(h->d_costpart, (size_t)2 * 64 * M);
+    DA(h->d_Yd_slot, M); DA(h->d_Yd, N + 1);
+    CK(cudaMemset(h->d_Yd, 0, sizeof(double) * (N + 1)));
+    DA(h->d_status, N + 1);
+    CK(cudaMemset(h->d_status, 0, sizeof(int) * (N + 1)));
+    DA(h->d_w, std::max(N, 1)); DA(h->d_g, std::max(N, 1)); DA(h->d_jprior, 1); DA(h->d_gscalar, std::max(N, 1));
     CK(cudaMemset(h->d_w, 0, sizeof(double) * std::max(N, 1)));
     return ENVAR_OK;
 }
@@ -521,7 +535,7 @@ struct MemberView {
     PoissonBufs pb;
     Partials pt;
     MemberCtl *ctl;
-    double *ubc, *series, *u, *v, *us, *vs, *p, *wf, *frect;
+    double *ubc, *series, *u, *v, *us, *vs, *p, *wf, *wd, *frect;
     void *Ru, *Rv;
 };
 static MemberView member_view(envar_handle h, int m0)
@@ -540,6 +554,7 @@ static MemberView member_view(envar_handle h, int m0)
         w.p = fs(w.p, o); w.Ru = fs(w.Ru, o); w.Rv = fs(w.Rv, o);
         w.bh = fs(w.bh, o); w.bl = fs(w.bl, o); w.xh = fs(w.xh, o); w.xl = fs(w.xl, o);
         w.wf = fs(w.wf, 6 * o);
+        w.wd = fs(w.wd, 4 * o);
         w.frect = fs(w.frect, (long long)m0 * 2 * h->nrect);
     }
     v.pb = h->pb;
@@ -560,52 +575,82 @@ static MemberView member_view(envar_handle h, int m0)
     v.ubc = h->d_ubc + (long long)m0 * h->g.ny;
     v.series = h->cfg.n_window > 0 ? h->d_series_slot + (long long)m0 * h->cfg.n_window * 8 : nullptr;
     v.u = ds(h->d_u, o); v.v = ds(h->d_v, o); v.us = ds(h->d_us, o); v.vs = ds(h->d_vs, o);
-    v.p = ds(h->d_p, o); v.wf = ds(h->d_wf, 3 * o);
+    v.p = ds(h->d_p, o); v.wf = ds(h->d_wf, 3 * o); v.wd = ds(h->d_wd, 3 * o);
     v.frect = ds(h->d_frect, (long long)m0 * 2 * h->nrect);
     v.Ru = vs(h->d_Ru, o); v.Rv = vs(h->d_Rv, o);
     return v;
 }
 
-// One time step of M member slots starting at the view's first member.
-static void enqueue_range(envar_handle h, int M, const MemberView &v, cudaStream_t st)
+// Member 0's arrays for the Welford of d = u - u_0 in the other members' correction.
+static RefMember ref_member(envar_handle h)
+{
+    RefMember r{nullptr, nullptr, nullptr, nullptr};
+    if (h->mixed || !h->d_wd) return r;
+    if (h->batched) { r.us = h->d_us; r.vs = h->d_vs; r.x = h->pb.x; }
+    else r.traj = h->d_traj;
+    return r;
+}
+
+// One time step of M member slots starting at the view's first member, in two parts: the
+// predictor and the pressure solve (part 0), then the projection correction with the cost
+// accumulation (part 1).
+static void enqueue_range(envar_handle h, int M, const MemberView &v, cudaStream_t st, int part)
 {
     const Grid &g = h->g;
     const int want_wf = h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0;
     if (h->mixed) {
-        launch_outflow_mx(g, M, v.ms, v.ubc, v.ctl, st);
-        launch_predict_mx(g, h->mc, M, v.ms, v.ubc, h->d_inh, h->d_inl, v.ctl, st);
-        launch_rhs_mx(g, h->mc, M, v.ms, st);
-        launch_pressure_solve<float>(g, h->lev, M, v.pb, h->pc, v.pt, v.ctl, st);
-        launch_correct_mx(g, h->mc, M, v.ms, h->x0, h->y0, want_wf, v.series, v.pt, v.ctl, h->cfg.div_tol, h->nfluid,
-                          st);
+        if (part == 0) {
+            launch_outflow_mx(g, M, v.ms, v.ubc, v.ctl, st);
+            launch_predict_mx(g, h->mc, M, v.ms, v.ubc, h->d_inh, h->d_inl, v.ctl, st);
+            launch_rhs_mx(g, h->mc, M, v.ms, st);
+            launch_pressure_solve<float>(g, h->lev, M, v.pb, h->pc, v.pt, v.ctl, st);
+        } else {
+            launch_correct_mx(g, h->mc, M, v.ms, h->ms, h->x0, h->y0, want_wf, v.series, v.pt, v.ctl, h->cfg.div_tol,
+                              h->nfluid, st);
+        }
         return;
     }
-    launch_outflow(g, M, v.u, v.ubc, v.ctl, st);
-    launch_predict<double>(g, M, v.u, v.v, v.p, (double *)v.Ru, (double *)v.Rv, v.us, v.vs, v.ubc, v.frect, v.ctl, st);
-    launch_rhs(g, M, v.us, v.vs, v.pb.b, v.ctl, st);
-    launch_pressure_solve<double>(g, h->lev, M, v.pb, h->pc, v.pt, v.ctl, st);
-    launch_correct(g, h->x0, h->y0, M, v.u, v.v, v.p, v.us, v.vs, v.pb.x, v.wf, want_wf, v.series, v.pt, v.ctl,
-                   h->cfg.div_tol, h->nfluid, st);
-    launch_recenter(g, M, v.pb.x, v.pt, h->nfluid, st);
+    if (part == 0) {
+        launch_outflow(g, M, v.u, v.ubc, v.ctl, st);
+        launch_predict<double>(g, M, v.u, v.v, v.p, (double *)v.Ru, (double *)v.Rv, v.us, v.vs, v.ubc, v.frect, v.ctl,
+                               st);
+        launch_rhs(g, M, v.us, v.vs, v.pb.b, v.ctl, st);
+        launch_pressure_solve<double>(g, h->lev, M, v.pb, h->pc, v.pt, v.ctl, st);
+    } else {
+        launch_correct(g, h->x0, h->y0, M, v.u, v.v, v.p, v.us, v.vs, v.pb.x, v.wf, v.wd, ref_member(h), want_wf,
+                       v.series, v.pt, v.ctl, h->cfg.div_tol, h->nfluid, st);
+        launch_recenter(g, M, v.pb.x, v.pt, h->nfluid, st);
+    }
 }
 
 // One time step of the first M member slots.  With all slots and several member groups, the
 // groups' steps are independent chains on side streams (parallel branches of the captured graph),
-// so one group's latency-bound phases overlap another's bandwidth-bound ones.
+// so one group's latency-bound phases overlap another's bandwidth-bound ones.  The corrections of
+// groups 1.. read member 0's pressure increment (the exact DOMAIN contraction), so they wait for
+// group 0's pressure solve.
 static void enqueue_step(envar_handle h, int M)
 {
     const int G = (M == h->Mall) ? h->ngroups : 1;
     if (G <= 1) {
-        enqueue_range(h, M, member_view(h, 0), h->st);
+        const MemberView v = member_view(h, 0);
+        enqueue_range(h, M, v, h->st, 0);
+        enqueue_range(h, M, v, h->st, 1);
         return;
     }
+    const bool need_m0 = h->ms.wd != nullptr || h->d_wd != nullptr;
     cudaEventRecord(h->ev_fork, h->st);
     const int per = (M + G - 1) / G;
     for (int k = 0; k < G; ++k) {
         const int m0 = k * per, Mg = std::min(per, M - m0);
         if (Mg <= 0) break;
+        const MemberView v = member_view(h, m0);
         cudaStreamWaitEvent(h->side[k], h->ev_fork, 0);
-        enqueue_range(h, Mg, member_view(h, m0), h->side[k]);
+        enqueue_range(h, Mg, v, h->side[k], 0);
+        if (need_m0) {
+            if (k == 0) cudaEventRecord(h->ev_solved0, h->side[0]);
+            else cudaStreamWaitEvent(h->side[k], h->ev_solved0, 0);
+        }
+        enqueue_range(h, Mg, v, h->side[k], 1);
         cudaEventRecord(h->ev_join[k], h->side[k]);
         cudaStreamWaitEvent(h->st, h->ev_join[k], 0);
     }
@@ -660,26 +705,33 @@ static int run_steps(envar_handle h, int M, int nsteps)
     return ENVAR_OK;
 }
 
-static void reset_members(envar_handle h, int M)
+// Load the initial state into the first M slots; slot k then holds ensemble member base + k.
+static void reset_members(envar_handle h, int M, int base = 0)
 {
     if (h->mixed) {
         launch_reset_mx(h->g, M, h->ic, h->ms, h->d_ctl, h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0, h->st);
-        return;
+    } else {
+        launch_reset(h->g, M, h->d_u0, h->d_v0, h->d_u, h->d_v, h->d_p, h->pb.x, h->d_Ru, h->d_Rv,
+                     h->tend_bytes / h->Mall * M, h->d_wf, h->d_wd, h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0,
+                     h->d_ctl, h->st);
     }
-    launch_reset(h->g, M, h->d_u0, h->d_v0, h->d_u, h->d_v, h->d_p, h->pb.x, h->d_Ru, h->d_Rv,
-                 h->tend_bytes / h->Mall * M, h->d_wf, h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0, h->d_ctl,
-                 h->st);
+    launch_set_gidx(h->d_ctl, M, base, h->st);
 }
 
-static void enqueue_cost(envar_handle h, int M, double *Jd, double *Js)
+static void enqueue_cost(envar_handle h, int M, double *Jd, double *Js, double *Yd)
 {
     const double *ser = h->cfg.n_window > 0 ? h->d_series_slot : nullptr;
     if (h->mixed) {
         const int nparts = 64;
-        if (h->ms.wf) launch_domain_partial_mx(h->g, M, h->ms.wf, h->d_costpart, nparts, h->st);
-        launch_cost_final(h->g, M, h->ms.wf ? h->d_costpart : nullptr, nparts, ser, Jd, Js, h->st);
+        const long long S = h->g.S;
+        double *part_d = h->d_costpart + (long long)nparts * M;
+        if (h->ms.wf) launch_plane_partial_mx(h->g, M, h->ms.wf + 4 * S, h->ms.wf + 5 * S, 6 * S, h->d_costpart, nparts,
+                                              h->st);
+        if (h->ms.wd) launch_plane_partial_mx(h->g, M, h->ms.wd + 2 * S, h->ms.wd + 3 * S, 4 * S, part_d, nparts, h->st);
+        launch_cost_final(h->g, M, h->ms.wf ? h->d_costpart : nullptr, h->ms.wd ? part_d : nullptr, nparts, ser, Jd,
+                          Js, h->ms.wd ? Yd : nullptr, h->st);
     } else {
-        launch_cost(h->g, M, h->d_wf, ser, Jd, Js, h->d_costpart, h->st);
+        launch_cost(h->g, M, h->d_wf, h->d_wd, ser, Jd, Js, Yd, h->d_costpart, h->st);
     }
 }
 
@@ -695,16 +747,18 @@ static int forward_members(envar_handle h)
         reset_members(h, h->Mall);
         int rc = run_steps(h, h->Mall, h->cfg.n_steps);
         if (rc) return rc;
-        enqueue_cost(h, h->Mall, h->d_Jd, h->d_Js);
+        enqueue_cost(h, h->Mall, h->d_Jd, h->d_Js, h->d_Yd);
+        launch_copy_status(h->d_ctl, N + 1, h->d_status, h->st);
         CK(cudaMemcpyAsync(h->ctl_all.data(), h->d_ctl, sizeof(MemberCtl) * (N + 1), cudaMemcpyDeviceToHost, h->st));
     } else {
         for (int mm = 0; mm <= N; ++mm) {
             launch_member_forcing(1, mm, N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->ms.frect,
                                   h->st);
-            reset_members(h, 1);
+            reset_members(h, 1, mm);
             int rc = run_steps(h, 1, h->cfg.n_steps);
             if (rc) return rc;
-            enqueue_cost(h, 1, h->d_Jd + mm, h->d_Js + mm);
+            enqueue_cost(h, 1, h->d_Jd + mm, h->d_Js + mm, h->d_Yd + mm);
+            launch_copy_status(h->d_ctl, 1, h->d_status + mm, h->st);
             CK(cudaMemcpyAsync(h->d_series + (size_t)mm * nw * 8, h->d_series_slot, sizeof(double) * nw * 8,
                                cudaMemcpyDeviceToDevice, h->st));
             CK(cudaMemcpyAsync(&h->ctl_all[mm], h->d_ctl, sizeof(MemberCtl), cudaMemcpyDeviceToHost, h->st));
@@ -767,7 +821,8 @@ extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda
         if (!h->batched) G = 1;
         h->ngroups = std::max(1, std::min(G, h->Mall));
         if (h->ngroups > 1) {
-            bool ok = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+            bool ok = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&h->ev_solved0, cudaEventDisableTiming) == cudaSuccess;
             for (int k = 0; ok && k < h->ngroups; ++k)
                 ok = cudaStreamCreateWithFlags(&h->side[k], cudaStreamNonBlocking) == cudaSuccess &&
                      cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
@@ -834,6 +889,7 @@ extern "C" int envar_destroy(envar_handle h)
         if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
     }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_solved0) cudaEventDestroy(h->ev_solved0);
     if (h->own_stream) cudaStreamDestroy(h->st);
     delete h;
     return ENVAR_OK;
@@ -908,7 +964,7 @@ extern "C" int envar_cost(envar_handle h, double *J, double *Jprior)
     if (J) CK(cudaMemcpyAsync(J, src, sizeof(double) * (h->N + 1), cudaMemcpyDeviceToHost, h->st));
     if (Jprior) {
         if (h->N > 0) {
-            launch_scalar_gradient(h->N, src, h->d_w, h->cfg.eps, h->d_g, h->d_jprior, h->st);
+            launch_scalar_gradient(h->N, src, h->d_w, h->cfg.eps, h->d_status, h->d_gscalar, h->d_jprior, h->st);
             CK(cudaMemcpyAsync(Jprior, h->d_jprior, sizeof(double), cudaMemcpyDeviceToHost, h->st));
         } else {
             *Jprior = 0.0;
@@ -919,12 +975,29 @@ extern "C" int envar_cost(envar_handle h, double *J, double *Jprior)
     return ENVAR_OK;
 }
 
-static int compute_gradient(envar_handle h)
+// Eq. (gradient_EnVar) for the last forward run, on the device: the scalar-anomaly form and the
+// prior cost always (d_gscalar, d_jprior), and the explicit contraction Y^T (Hq_0 - y) + (N-1) w of
+// the configured observation operator in d_g.  Members whose status word is nonzero contribute
+// no column of Y.
+static void compute_gradient(envar_handle h)
 {
-    const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js : h->d_Jd;
-    launch_scalar_gradient(h->N, src, h->d_w, h->cfg.eps, h->d_g, h->d_jprior, h->st);
-    if (h->cfg.cost_mode == ENVAR_COST_SENSORS && h->cfg.n_window > 0)
-        launch_sensor_gradient(h->N, h->cfg.n_window, h->d_series, h->cfg.eps, h->d_w, h->d_g, h->st);
+    const bool sensors = h->cfg.cost_mode == ENVAR_COST_SENSORS;
+    const double *src = sensors ? h->d_Js : h->d_Jd;
+    launch_scalar_gradient(h->N, src, h->d_w, h->cfg.eps, h->d_status, h->d_gscalar, h->d_jprior, h->st);
+    if (sensors && h->cfg.n_window > 0)
+        launch_sensor_gradient(h->N, h->cfg.n_window, h->d_series, h->cfg.eps, h->d_w, h->d_status, h->d_g, h->st);
+    else if (!sensors && h->cfg.n_window > 0)
+        launch_domain_gradient(h->N, h->d_Jd, h->d_Yd, h->d_w, h->cfg.eps, h->d_status, h->d_g, h->st);
+    else
+        cudaMemcpyAsync(h->d_g, h->d_gscalar, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st);
+}
+
+static int check_member0(envar_handle h, const char *what)
+{
+    if (!h->ctl_all.empty() && h->ctl_all[0].status != 0) {
+        set_err(h, "%s: the unperturbed member failed (status 0x%x); no gradient", what, h->ctl_all[0].status);
+        return ENVAR_ESTATE;
+    }
     return ENVAR_OK;
 }
 
@@ -933,11 +1006,35 @@ extern "C" int envar_gradient(envar_handle h, double *g, double *df)
     if (!h) return ENVAR_EINVAL;
     if (!h->have_forward) { set_err(h, "envar_gradient: no forward run"); return ENVAR_ESTATE; }
     if (h->N < 1) { set_err(h, "envar_gradient: ensemble is empty"); return ENVAR_ESTATE; }
+    if (int rc = check_member0(h, "envar_gradient")) return rc;
     compute_gradient(h);
     if (df) launch_df(h->N, h->n_ctrl, h->d_E, h->d_g, 1.0 / std::max(h->N - 1, 1), df, h->st);
     if (g) CK(cudaMemcpyAsync(g, h->d_g, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+extern "C" int envar_gradient_scalar(envar_handle h, double *g)
+{
+    if (!h || !g) return ENVAR_EINVAL;
+    if (!h->have_forward) { set_err(h, "envar_gradient_scalar: no forward run"); return ENVAR_ESTATE; }
+    if (h->N < 1) { set_err(h, "envar_gradient_scalar: ensemble is empty"); return ENVAR_ESTATE; }
+    if (int rc = check_member0(h, "envar_gradient_scalar")) return rc;
+    compute_gradient(h);
+    CK(cudaMemcpyAsync(g, h->d_gscalar, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+extern "C" int envar_excluded_members(envar_handle h, int *count)
+{
+    if (!h || !count) return ENVAR_EINVAL;
+    if (!h->have_forward) { set_err(h, "envar_excluded_members: no forward run"); return ENVAR_ESTATE; }
+    int n = 0;
+    for (int m = 1; m <= h->N; ++m) n += h->ctl_all[m].status != 0;
+    *count = n;
     return ENVAR_OK;
 }
 
@@ -949,6 +1046,7 @@ extern "C" int envar_step(envar_handle h, double alpha, double *w_inout, double 
     CK(cudaMemcpyAsync(h->d_w, w_inout, sizeof(double) * h->N, cudaMemcpyHostToDevice, h->st));
     int rc = forward_members(h);
     if (rc) return rc;
+    if ((rc = check_member0(h, "envar_step"))) return rc;
     compute_gradient(h);
     double J0 = 0.0, jp = 0.0;
     const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js : h->d_Jd;
@@ -990,7 +1088,7 @@ extern "C" int envar_forward_control(envar_handle h, const double *f, double *J)
     reset_members(h, 1);
     int rc = run_steps(h, 1, h->cfg.n_steps);
     if (rc) return rc;
-    enqueue_cost(h, 1, h->d_Jd_slot, h->d_Js_slot);
+    enqueue_cost(h, 1, h->d_Jd_slot, h->d_Js_slot, h->d_Yd_slot);
     const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js_slot : h->d_Jd_slot;
     if (J) CK(cudaMemcpyAsync(J, src, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -1093,7 +1191,7 @@ extern "C" int envar_time_kernel(envar_handle h, int which, int reps, double *ms
     if (!h->have_ic) { set_err(h, "envar_time_kernel: no initial state"); return ENVAR_ESTATE; }
     const int M = h->Mall;
     std::vector<MemberCtl> c((size_t)M);
-    for (auto &x : c) { x = MemberCtl{}; x.step = h->cfg.n_steps; }
+    for (int m = 0; m < M; ++m) { c[m] = MemberCtl{}; c[m].step = h->cfg.n_steps; c[m].gidx = h->batched ? m : 0; }
     CK(cudaMemcpyAsync(h->d_ctl, c.data(), sizeof(MemberCtl) * M, cudaMemcpyHostToDevice, h->st));
     CK(cudaStreamSynchronize(h->st));
     const int wf = h->cfg.cost_mode == ENVAR_COST_DOMAIN ? 1 : 0;
@@ -1110,11 +1208,12 @@ extern "C" int envar_time_kernel(envar_handle h, int which, int reps, double *ms
             return 0;
         case 6:
             if (h->mixed) {
-                launch_correct_mx(g, h->mc, M, h->ms, h->x0, h->y0, wf, ser, h->pt, h->d_ctl, h->cfg.div_tol,
+                launch_correct_mx(g, h->mc, M, h->ms, h->ms, h->x0, h->y0, wf, ser, h->pt, h->d_ctl, h->cfg.div_tol,
                                   h->nfluid, h->st);
                 return 0;
             }
-            launch_correct(g, h->x0, h->y0, M, h->d_u, h->d_v, h->d_p, h->d_us, h->d_vs, h->pb.x, h->d_wf, wf, ser,
+            launch_correct(g, h->x0, h->y0, M, h->d_u, h->d_v, h->d_p, h->d_us, h->d_vs, h->pb.x, h->d_wf, h->d_wd,
+                           ref_member(h), wf, ser,
                            h->pt, h->d_ctl, h->cfg.div_tol, h->nfluid, h->st);
             return 0;
         case 8:
@@ -1361,7 +1460,7 @@ extern "C" int envar_adjoint_gradient(envar_handle h, const double *f, double *g
         at = pos[k];
     }
     if ((rc = ex.advance(at, n))) return rc;
-    enqueue_cost(h, 1, h->d_Jd_slot, h->d_Js_slot);
+    enqueue_cost(h, 1, h->d_Jd_slot, h->d_Js_slot, h->d_Yd_slot);
     // window means of the cell-centred velocity (member 0's Welford planes), then lambda^n
     CK(cudaMemcpyAsync(ex.mu, h->d_wf, sizeof(double) * 2 * S, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemsetAsync(a, 0, sizeof(double) * 8 * S, h->st));
@@ -1432,9 +1531,23 @@ extern "C" int envar_autotune(envar_handle h, int probe_steps, double *best_ms_p
     const SolverParams orig{h->cfg.max_outer, h->cfg.max_inner, h->cfg.nu_pre, h->cfg.coarse_sweeps, h->cfg.inner_rtol};
     const int M = h->Mall;
     std::vector<MemberCtl> c((size_t)M);
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // on any failure: the original parameters back in place, no event left behind
+    auto bail = [&](int rc) {
+        apply_params(h, orig);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        h->have_forward = false;
+        return rc;
+    };
+    auto ck = [&](cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return ENVAR_OK;
+        set_err(h, "envar_autotune: %s failed: %s", what, cudaGetErrorString(e));
+        return ENVAR_ECUDA;
+    };
+    int rc = ck(cudaEventCreate(&e0), "cudaEventCreate");
+    if (!rc) rc = ck(cudaEventCreate(&e1), "cudaEventCreate");
+    if (rc) return bail(rc);
     double best = -1.0;
     int best_k = -1;
     const int n_cand = (int)(sizeof(kTuneCandidates) / sizeof(kTuneCandidates[0]));
@@ -1446,13 +1559,13 @@ extern "C" int envar_autotune(envar_handle h, int probe_steps, double *best_ms_p
         for (int rep = 0; rep < 2 && ok; ++rep) {
             launch_member_forcing(M, 0, h->N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->ms.frect, h->st);
             reset_members(h, M);
-            CK(cudaEventRecord(e0, h->st));
-            int rc = run_steps(h, M, probe_steps);
-            if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
-            CK(cudaEventRecord(e1, h->st));
-            CK(cudaEventSynchronize(e1));
-            CK(cudaEventElapsedTime(&t, e0, e1));
-            CK(cudaMemcpy(c.data(), h->d_ctl, sizeof(MemberCtl) * M, cudaMemcpyDeviceToHost));
+            if ((rc = ck(cudaEventRecord(e0, h->st), "cudaEventRecord"))) return bail(rc);
+            if ((rc = run_steps(h, M, probe_steps))) return bail(rc);
+            if ((rc = ck(cudaEventRecord(e1, h->st), "cudaEventRecord"))) return bail(rc);
+            if ((rc = ck(cudaEventSynchronize(e1), "cudaEventSynchronize"))) return bail(rc);
+            if ((rc = ck(cudaEventElapsedTime(&t, e0, e1), "cudaEventElapsedTime"))) return bail(rc);
+            if ((rc = ck(cudaMemcpy(c.data(), h->d_ctl, sizeof(MemberCtl) * M, cudaMemcpyDeviceToHost), "cudaMemcpy")))
+                return bail(rc);
             for (const MemberCtl &x : c) ok = ok && x.status == 0;
         }
         const double ms = (double)t / probe_steps;

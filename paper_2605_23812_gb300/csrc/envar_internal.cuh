@@ -60,6 +60,8 @@ struct Grid {
 struct MemberCtl {
     int step;               // completed time steps of the current forward run
     int status;             // ENVAR_ST_* bits
+    int gidx;               // ensemble member held by this slot (0 = the unperturbed run)
+    int pad_;
     int outer_done;         // pressure solve converged for the current step
     int inner_done;         // inner CG converged for the current refinement
     double max_div;         // max |D u| seen over the run
@@ -89,6 +91,7 @@ struct MixState {
     float *Ru, *Rv;                 // previous tendency (FP32, AB2)
     float *bh, *bl, *xh, *xl;       // Poisson right-hand side and solution (df64)
     float *wf;                      // Welford per member: 6 planes (mean_u, mean_v, M2; hi/lo)
+    float *wd;                      // Welford of d = u - u_0 per member: 4 planes (mean_du, mean_dv, M2 hi/lo)
     float *frect;                   // member forcing on the control rectangle (FP32)
 };
 // Constants of the mixed step; df64 pairs (h, l) where FP64-level accuracy is needed.
@@ -209,19 +212,31 @@ void launch_predict(const Grid &g, int M, const double *u, const double *v, cons
                     TR *Ru, TR *Rv, double *us, double *vs, const double *ubc, const double *frect,
                     const MemberCtl *ctl, cudaStream_t st);
 void launch_reset(const Grid &g, int M, const double *u0, const double *v0, double *u, double *v, double *p,
-                  double *x, void *Ru, void *Rv, size_t tend_bytes, double *wf, int want_welford,
+                  double *x, void *Ru, void *Rv, size_t tend_bytes, double *wf, double *wd, int want_welford,
                   MemberCtl *ctl, cudaStream_t st);
 void launch_outflow(const Grid &g, int M, const double *u, double *ubc, MemberCtl *ctl, cudaStream_t st);
 void launch_rhs(const Grid &g, int M, const double *us, const double *vs, double *b, MemberCtl *ctl,
                 cudaStream_t st);
 void launch_recenter(const Grid &g, int M, double *x, const Partials &pt, long long nfluid, cudaStream_t st);
+// Member 0's cell-centred velocity in the cost window, which the other members' Welford of
+// d = u - u_0 needs (the exact contraction Y^T (Hq_0 - y) of the DOMAIN cost): batched runs read
+// member 0's predictor and pressure increment (slot 0, unchanged during the correction); a
+// one-member-at-a-time run stores member 0's samples in traj [n_window][2][S] and reads them back.
+struct RefMember {
+    const double *us, *vs, *x;      // FP64 batched: member 0's u*, v*, increment (nullptr otherwise)
+    double *traj;                   // FP64 plain: member 0's window samples (nullptr otherwise)
+};
 void launch_correct(const Grid &g, double x0, double y0, int M, double *u, double *v, double *p,
-                    const double *us, const double *vs, const double *x, double *wf, int want_welford,
-                    double *series, const Partials &pt, MemberCtl *ctl, double div_tol, long long nfluid,
-                    cudaStream_t st);
+                    const double *us, const double *vs, const double *x, double *wf, double *wd, RefMember ref,
+                    int want_welford, double *series, const Partials &pt, MemberCtl *ctl, double div_tol,
+                    long long nfluid, cudaStream_t st);
+void launch_set_gidx(MemberCtl *ctl, int M, int base, cudaStream_t st);
+void launch_copy_status(const MemberCtl *ctl, int M, int *status, cudaStream_t st);
 void launch_load_ic(const Grid &g, const double *u0, const double *v0, double *u, double *v, cudaStream_t st);
-void launch_cost(const Grid &g, int M, const double *wf, const double *series, double *J_domain,
-                 double *J_sensor, double *part, cudaStream_t st);
+// Window costs: J_domain = dx dy/(2 n_w) sum M2, J_sensor (two-pass over the series), and, when wd is
+// given, Yd = dx dy/(2 n_w) sum M2_d = 1/2 ||h_m - h_0||^2 (the squared norm of eps Y_m).
+void launch_cost(const Grid &g, int M, const double *wf, const double *wd, const double *series, double *J_domain,
+                 double *J_sensor, double *Yd, double *part, cudaStream_t st);
 void launch_export_state(const Grid &g, const double *u, const double *v, const double *p, double *uo,
                          double *vo, double *po, cudaStream_t st);
 
@@ -288,12 +303,15 @@ void launch_outer_residual_mx(const Grid &g, const Level &L0, const MixConst &K,
                               cudaStream_t st);
 void launch_outer_update_mx(const Grid &g, int M, const MixState &s, const float *e, const MemberCtl *ctl,
                             cudaStream_t st);
-void launch_correct_mx(const Grid &g, const MixConst &K, int M, const MixState &s, double x0, double y0,
-                       int want_welford, double *series, const Partials &pt, MemberCtl *ctl, double div_tol,
-                       long long nfluid, cudaStream_t st);
-void launch_domain_partial_mx(const Grid &g, int M, const float *wf, double *part, int nparts, cudaStream_t st);
-void launch_cost_final(const Grid &g, int M, const double *part, int nparts, const double *series, double *J_domain,
-                       double *J_sensor, cudaStream_t st);
+// ref: member 0's slot (its u*, v* and increment x are read for the Welford of d = u - u_0).
+void launch_correct_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const MixState &ref, double x0,
+                       double y0, int want_welford, double *series, const Partials &pt, MemberCtl *ctl,
+                       double div_tol, long long nfluid, cudaStream_t st);
+// Per-member partial sums over fluid cells of a df64 plane pair (hi, lo) with member stride mstride.
+void launch_plane_partial_mx(const Grid &g, int M, const float *hi, const float *lo, long long mstride, double *part,
+                             int nparts, cudaStream_t st);
+void launch_cost_final(const Grid &g, int M, const double *part, const double *part_d, int nparts,
+                       const double *series, double *J_domain, double *J_sensor, double *Yd, cudaStream_t st);
 
 // Ensemble kernels (k_ensemble.cu)
 void launch_normals(unsigned long long seed, unsigned long long stream, long long first, long long n, double *out,
@@ -307,10 +325,14 @@ void launch_rect_to_compact(int N, int nrect, int ncc, const int *cidx, const do
                             cudaStream_t st);
 void launch_compact_to_rect(int N, int nrect, int ncc, const int *cidx, const double *E, double *Erect,
                             cudaStream_t st);
-void launch_sensor_gradient(int N, int n_window, const double *series, double eps, const double *w, double *g,
-                            cudaStream_t st);
-void launch_scalar_gradient(int N, const double *J, const double *w, double eps, double *g, double *jprior,
-                            cudaStream_t st);
+// Gradients of Eq. (gradient_EnVar); a perturbed member whose status word is nonzero contributes no
+// column of Y (its component keeps only the prior term (N-1) w_i).  status: N+1 ints (device).
+void launch_sensor_gradient(int N, int n_window, const double *series, double eps, const double *w,
+                            const int *status, double *g, cudaStream_t st);
+void launch_scalar_gradient(int N, const double *J, const double *w, double eps, const int *status, double *g,
+                            double *jprior, cudaStream_t st);
+void launch_domain_gradient(int N, const double *J, const double *Yd, const double *w, double eps, const int *status,
+                            double *g, cudaStream_t st);
 void launch_df(int N, int n_ctrl, const double *E, const double *g, double scale, double *df, cudaStream_t st);
 void launch_update_w(int N, double *w, const double *g, double step, cudaStream_t st);
 void launch_d2f(long long n, const double *a, float *b, cudaStream_t st);

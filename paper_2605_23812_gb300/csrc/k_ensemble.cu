@@ -187,29 +187,53 @@ void launch_rect_to_compact(int N, int nrect, int ncc, const int *cidx, const do
 
 // ---------------------------------------------------------------- gradients (K9)
 // Scalar-anomaly form: g_i = (J_i - J_0)/eps + (N-1) w_i;  J_prior = (N-1)/2 w^T w.
+// Scalar-anomaly form: g_i = (J_i - J_0)/eps + (N-1) w_i, also J_prior = (N-1)/2 w^T w (Eq. J_w).
+// A member with a nonzero status word keeps only the prior term.
 __global__ void k_scalar_gradient(int N, const double *__restrict__ J, const double *__restrict__ w, double eps,
-                                  double *__restrict__ g, double *__restrict__ jprior)
+                                  const int *__restrict__ status, double *__restrict__ g, double *__restrict__ jprior)
 {
     double acc = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        g[i] = (J[i + 1] - J[0]) / eps + (double)(N - 1) * w[i];
+        const bool ok = !status || status[i + 1] == 0;
+        g[i] = (ok ? (J[i + 1] - J[0]) / eps : 0.0) + (double)(N - 1) * w[i];
         acc += w[i] * w[i];
     }
     acc = block_reduce(acc, false);
-    if (threadIdx.x == 0) *jprior = 0.5 * (double)(N - 1) * acc;
+    if (threadIdx.x == 0 && jprior) *jprior = 0.5 * (double)(N - 1) * acc;
 }
 
-void launch_scalar_gradient(int N, const double *J, const double *w, double eps, double *g, double *jprior,
-                            cudaStream_t st)
+void launch_scalar_gradient(int N, const double *J, const double *w, double eps, const int *status, double *g,
+                            double *jprior, cudaStream_t st)
 {
-    k_scalar_gradient<<<1, 256, 0, st>>>(N, J, w, eps, g, jprior);
+    k_scalar_gradient<<<1, 256, 0, st>>>(N, J, w, eps, status, g, jprior);
+    count_launches(1);
+}
+
+// DOMAIN form of Eq. (gradient_EnVar) with Y_i = (h_i - h_0)/eps from Eq. (fdapprox):
+//   Y_i^T h_0 = (1/2||h_i||^2 - 1/2||h_0||^2 - 1/2||h_i - h_0||^2) / eps = (J_i - J_0 - Yd_i)/eps,
+// with Yd_i = 1/2||h_i - h_0||^2 accumulated in the correction kernel (Welford of u_i - u_0).
+__global__ void k_domain_gradient(int N, const double *__restrict__ J, const double *__restrict__ Yd,
+                                  const double *__restrict__ w, double eps, const int *__restrict__ status,
+                                  double *__restrict__ g)
+{
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const bool ok = !status || status[i + 1] == 0;
+        g[i] = (ok ? (J[i + 1] - J[0] - Yd[i + 1]) / eps : 0.0) + (double)(N - 1) * w[i];
+    }
+}
+
+void launch_domain_gradient(int N, const double *J, const double *Yd, const double *w, double eps, const int *status,
+                            double *g, cudaStream_t st)
+{
+    k_domain_gradient<<<1, 256, 0, st>>>(N, J, Yd, w, eps, status, g);
     count_launches(1);
 }
 
 // Sensor form: h_m(t,s) = series_m(t,s) - mean_t series_m(., s);  Y_i = (h_i - h_0)/eps;
 // g_i = Y_i^T h_0 + (N-1) w_i.  One block per i.
 __global__ void k_sensor_gradient(int N, int nw, const double *__restrict__ series, double eps,
-                                  const double *__restrict__ w, double *__restrict__ g)
+                                  const double *__restrict__ w, const int *__restrict__ status,
+                                  double *__restrict__ g)
 {
     const int i = blockIdx.x;
     const double *s0 = series;
@@ -230,13 +254,14 @@ __global__ void k_sensor_gradient(int N, int nw, const double *__restrict__ seri
         }
         acc += block_reduce(a, false);
     }
-    if (threadIdx.x == 0) g[i] = acc + (double)(N - 1) * w[i];
+    const bool ok = !status || status[i + 1] == 0;
+    if (threadIdx.x == 0) g[i] = (ok ? acc : 0.0) + (double)(N - 1) * w[i];
 }
 
-void launch_sensor_gradient(int N, int n_window, const double *series, double eps, const double *w, double *g,
-                            cudaStream_t st)
+void launch_sensor_gradient(int N, int n_window, const double *series, double eps, const double *w,
+                            const int *status, double *g, cudaStream_t st)
 {
-    if (N > 0) k_sensor_gradient<<<N, 256, 0, st>>>(N, n_window, series, eps, w, g);
+    if (N > 0) k_sensor_gradient<<<N, 256, 0, st>>>(N, n_window, series, eps, w, status, g);
     count_launches(1);
 }
 

@@ -42,7 +42,7 @@ __global__ void k_broadcast(const double *__restrict__ src, double *__restrict__
 }
 
 void launch_reset(const Grid &g, int M, const double *u0, const double *v0, double *u, double *v, double *p,
-                  double *x, void *Ru, void *Rv, size_t tend_bytes, double *wf, int want_welford,
+                  double *x, void *Ru, void *Rv, size_t tend_bytes, double *wf, double *wd, int want_welford,
                   MemberCtl *ctl, cudaStream_t st)
 {
     size_t bytes = sizeof(double) * (size_t)g.S * M;
@@ -54,7 +54,30 @@ void launch_reset(const Grid &g, int M, const double *u0, const double *v0, doub
     cudaMemsetAsync(Ru, 0, tend_bytes, st);
     cudaMemsetAsync(Rv, 0, tend_bytes, st);
     if (want_welford) cudaMemsetAsync(wf, 0, 3 * bytes, st);
+    if (want_welford && wd) cudaMemsetAsync(wd, 0, 3 * bytes, st);
     cudaMemsetAsync(ctl, 0, sizeof(MemberCtl) * M, st);
+}
+
+__global__ void k_set_gidx(MemberCtl *ctl, int M, int base)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) ctl[m].gidx = base + m;
+}
+void launch_set_gidx(MemberCtl *ctl, int M, int base, cudaStream_t st)
+{
+    k_set_gidx<<<cdiv(M, 128), 128, 0, st>>>(ctl, M, base);
+    count_launches(1);
+}
+
+__global__ void k_copy_status(const MemberCtl *ctl, int M, int *status)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) status[m] = ctl[m].status;
+}
+void launch_copy_status(const MemberCtl *ctl, int M, int *status, cudaStream_t st)
+{
+    k_copy_status<<<cdiv(M, 128), 128, 0, st>>>(ctl, M, status);
+    count_launches(1);
 }
 
 // ---------------------------------------------------------------------------- outflow
@@ -258,12 +281,25 @@ __device__ void sample_sensors(const Grid &g, double x0, double y0, const double
     }
 }
 
+// Welford step of the window sample n (1-based) of a two-component quantity (a, b) into its
+// running means and summed squared deviation M2 (Welford 1962, with a shared count).
+__device__ __forceinline__ void welford2(double a, double b, int n, double *ma, double *mb, double *m2)
+{
+    const double inv_n = 1.0 / (double)n;
+    const double da = a - *ma, db = b - *mb;
+    const double na = *ma + da * inv_n, nb = *mb + db * inv_n;
+    *m2 += da * (a - na) + db * (b - nb);
+    *ma = na;
+    *mb = nb;
+}
+
 __global__ void __launch_bounds__(256) k_correct(Grid g, double x0, double y0, double *__restrict__ u,
                                                  double *__restrict__ v, double *__restrict__ p,
                                                  const double *__restrict__ us, const double *__restrict__ vs,
                                                  const double *__restrict__ x, double *__restrict__ wf,
-                                                 int want_welford, double *__restrict__ series, Partials pt,
-                                                 MemberCtl *ctl, double div_tol, long long nfluid)
+                                                 double *__restrict__ wd, RefMember ref, int want_welford,
+                                                 double *__restrict__ series, Partials pt, MemberCtl *ctl,
+                                                 double div_tol, long long nfluid)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -272,15 +308,17 @@ __global__ void __launch_bounds__(256) k_correct(Grid g, double x0, double y0, d
     const long long c = (long long)j * g.P + i;
     const double *usm = us + off, *vsm = vs + off, *xm = x + off;
     __shared__ double s_mean;
-    __shared__ int s_t;
+    __shared__ int s_t, s_gm;
     int tid = threadIdx.x + threadIdx.y * blockDim.x;
     if (tid == 0) {
         s_mean = pt.red[m].val[RS_XSUM] / (double)nfluid;
         s_t = ctl[m].step - (g.n_steps - g.n_window);
+        s_gm = ctl[m].gidx;
     }
     __syncthreads();
     const double xmean = s_mean;
     const int t = (s_t > 0 && s_t <= g.n_window) ? s_t : 0;  // window sample index (1-based), 0 outside
+    const int gm = s_gm;
     int bad = 0;
     if (i <= g.nx && j <= g.ny) {
         if (j < g.ny) {
@@ -301,14 +339,23 @@ __global__ void __launch_bounds__(256) k_correct(Grid g, double x0, double y0, d
                 double uc = 0.5 * (u_new(g, usm, xm, c) + u_new(g, usm, xm, c + 1));
                 double vc = 0.5 * (v_new(g, vsm, xm, c) + v_new(g, vsm, xm, c + g.P));
                 double *mu = wf + 3 * off, *mv = mu + g.S, *m2 = mv + g.S;
-                double inv_n = 1.0 / (double)t;
-                double du = uc - mu[c];
-                double mun = mu[c] + du * inv_n;
-                double dv = vc - mv[c];
-                double mvn = mv[c] + dv * inv_n;
-                m2[c] += du * (uc - mun) + dv * (vc - mvn);
-                mu[c] = mun;
-                mv[c] = mvn;
+                welford2(uc, vc, t, mu + c, mv + c, m2 + c);
+                // d = u - u_0 (Eq. fdapprox times eps, before the window mean is removed)
+                double u0c = 0.0, v0c = 0.0;
+                bool have0 = false;
+                if (ref.traj) {
+                    double *tr = ref.traj + (long long)(t - 1) * 2 * g.S;
+                    if (gm == 0) { tr[c] = uc; tr[g.S + c] = vc; }
+                    else { u0c = tr[c]; v0c = tr[g.S + c]; have0 = true; }
+                } else if (ref.us && gm != 0) {
+                    u0c = 0.5 * (u_new(g, ref.us, ref.x, c) + u_new(g, ref.us, ref.x, c + 1));
+                    v0c = 0.5 * (v_new(g, ref.vs, ref.x, c) + v_new(g, ref.vs, ref.x, c + g.P));
+                    have0 = true;
+                }
+                if (have0 && wd) {
+                    double *da = wd + 3 * off, *db = da + g.S, *d2 = db + g.S;
+                    welford2(uc - u0c, vc - v0c, t, da + c, db + c, d2 + c);
+                }
             }
         }
     }
@@ -328,13 +375,13 @@ __global__ void __launch_bounds__(256) k_correct(Grid g, double x0, double y0, d
 }
 
 void launch_correct(const Grid &g, double x0, double y0, int M, double *u, double *v, double *p,
-                     const double *us, const double *vs, const double *x, double *wf, int want_welford,
-                     double *series, const Partials &pt, MemberCtl *ctl, double div_tol, long long nfluid,
-                     cudaStream_t st)
+                    const double *us, const double *vs, const double *x, double *wf, double *wd, RefMember ref,
+                    int want_welford, double *series, const Partials &pt, MemberCtl *ctl, double div_tol,
+                    long long nfluid, cudaStream_t st)
 {
     dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), M);
-    k_correct<<<grd, blk, 0, st>>>(g, x0, y0, u, v, p, us, vs, x, wf, want_welford, series, pt, ctl, div_tol,
-                                   nfluid);
+    k_correct<<<grd, blk, 0, st>>>(g, x0, y0, u, v, p, us, vs, x, wf, wd, ref, want_welford, series, pt, ctl,
+                                   div_tol, nfluid);
     count_launches(1);
 }
 
@@ -358,29 +405,33 @@ void launch_recenter(const Grid &g, int M, double *x, const Partials &pt, long l
 }
 
 // ---------------------------------------------------------------------------- costs (K7)
-__global__ void k_domain_partial(Grid g, const double *__restrict__ wf, double *__restrict__ part)
+// Per-member partial sums over fluid cells of one plane (member stride mstride).
+__global__ void k_plane_partial(Grid g, const double *__restrict__ plane, long long mstride, double *__restrict__ part)
 {
     int m = blockIdx.y;
-    const double *m2 = wf + 3LL * m * g.S + 2LL * g.S;
+    const double *a = plane + (long long)m * mstride;
     long long ncell = (long long)g.ny * g.P;
     double acc = 0.0;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
         int i = (int)(c % g.P);
-        if (i < g.nx && g.fluid[c]) acc += m2[c];
+        if (i < g.nx && g.fluid[c]) acc += a[c];
     }
     acc = block_reduce(acc, false);
     if (threadIdx.x == 0) part[(long long)m * gridDim.x + blockIdx.x] = acc;
 }
 
-__global__ void k_cost_final(Grid g, const double *__restrict__ part, int nparts, const double *__restrict__ series,
-                             double *__restrict__ Jd, double *__restrict__ Js)
+__global__ void k_cost_final(Grid g, const double *__restrict__ part, const double *__restrict__ part_d, int nparts,
+                             const double *__restrict__ series, double *__restrict__ Jd, double *__restrict__ Js,
+                             double *__restrict__ Yd)
 {
     int m = blockIdx.x;
-    double acc = 0.0;
-    if (part) {
-        for (int k = threadIdx.x; k < nparts; k += blockDim.x) acc += part[(long long)m * nparts + k];
+    double acc = 0.0, accd = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+        if (part) acc += part[(long long)m * nparts + k];
+        if (part_d) accd += part_d[(long long)m * nparts + k];
     }
     acc = block_reduce(acc, false);
+    accd = block_reduce(accd, false);
     // sensors: two-pass over the window series
     double js = 0.0;
     int nw = g.n_window;
@@ -401,27 +452,34 @@ __global__ void k_cost_final(Grid g, const double *__restrict__ part, int nparts
     if (threadIdx.x == 0) {
         Jd[m] = (nw > 0) ? acc * g.hxy / (2.0 * nw) : 0.0;
         Js[m] = 0.5 * js;
+        if (Yd) Yd[m] = (nw > 0) ? accd * g.hxy / (2.0 * nw) : 0.0;
     }
 }
 
-void launch_cost_final(const Grid &g, int M, const double *part, int nparts, const double *series, double *J_domain,
-                       double *J_sensor, cudaStream_t st)
+void launch_cost_final(const Grid &g, int M, const double *part, const double *part_d, int nparts,
+                       const double *series, double *J_domain, double *J_sensor, double *Yd, cudaStream_t st)
 {
-    k_cost_final<<<M, 256, 0, st>>>(g, part, nparts, series, J_domain, J_sensor);
+    k_cost_final<<<M, 256, 0, st>>>(g, part, part_d, nparts, series, J_domain, J_sensor, Yd);
     count_launches(1);
 }
 
-void launch_cost(const Grid &g, int M, const double *wf, const double *series, double *J_domain, double *J_sensor,
-                 double *part, cudaStream_t st)
+void launch_cost(const Grid &g, int M, const double *wf, const double *wd, const double *series, double *J_domain,
+                 double *J_sensor, double *Yd, double *part, cudaStream_t st)
 {
     const int nparts = 64;
+    double *part_d = part + (long long)nparts * M;
     if (wf) {
         dim3 grd(nparts, M);
-        k_domain_partial<<<grd, 256, 0, st>>>(g, wf, part);
+        k_plane_partial<<<grd, 256, 0, st>>>(g, wf + 2 * g.S, 3 * g.S, part);
         count_launches(1);
     }
-    k_cost_final<<<M, 256, 0, st>>>(g, wf ? part : nullptr, nparts, series, J_domain, J_sensor);
-    count_launches(1);
+    if (wd) {
+        dim3 grd(nparts, M);
+        k_plane_partial<<<grd, 256, 0, st>>>(g, wd + 2 * g.S, 3 * g.S, part_d);
+        count_launches(1);
+    }
+    launch_cost_final(g, M, wf ? part : nullptr, wd ? part_d : nullptr, nparts, series, J_domain, J_sensor,
+                      wd ? Yd : nullptr, st);
 }
 
 // ---------------------------------------------------------------------------- state export

@@ -67,6 +67,7 @@ void launch_reset_mx(const Grid &g, int M, const MixState &ic, const MixState &s
     cudaMemsetAsync(s.Ru, 0, fb, st);
     cudaMemsetAsync(s.Rv, 0, fb, st);
     if (want_welford) cudaMemsetAsync(s.wf, 0, 6 * fb, st);
+    if (want_welford && s.wd) cudaMemsetAsync(s.wd, 0, 4 * fb, st);
     cudaMemsetAsync(ctl, 0, sizeof(MemberCtl) * M, st);
 }
 
@@ -410,7 +411,37 @@ __device__ __forceinline__ f2 corrected(bool unk, f2 us, f2 xa, f2 xb, f2 gam)
     return unk ? df_sub(us, df_mul(df_sub(xa, xb), gam)) : us;
 }
 
-__global__ void __launch_bounds__(256) k_correct_mx(Grid g, MixConst K, MixState s, double x0, double y0,
+// df64 Welford step of the window sample n (1-based) of (a, b) into running means and M2.
+__device__ __forceinline__ void welford2_df(f2 a, f2 b, int n, float *w, long long S, long long c)
+{
+    const f2 inv_n = df_recip_int(n);
+    const f2 mu{w[c], w[S + c]}, mv{w[2 * S + c], w[3 * S + c]};
+    f2 m2{w[4 * S + c], w[5 * S + c]};
+    const f2 du = df_sub(a, mu);
+    const f2 mun = df_add(mu, df_mul(du, inv_n));
+    const f2 dv = df_sub(b, mv);
+    const f2 mvn = df_add(mv, df_mul(dv, inv_n));
+    m2 = df_add(m2, df_add(df_mul(du, df_sub(a, mun)), df_mul(dv, df_sub(b, mvn))));
+    w[c] = mun.h; w[S + c] = mun.l;
+    w[2 * S + c] = mvn.h; w[3 * S + c] = mvn.l;
+    w[4 * S + c] = m2.h; w[5 * S + c] = m2.l;
+}
+
+// Welford step of the member-minus-member-0 difference d = (a, b), a quantity of the size of the
+// perturbation response: FP32 running means, df64 M2 (planes: mean_a, mean_b, M2 hi, M2 lo).
+__device__ __forceinline__ void welford2_diff(float a, float b, int n, float *w, long long S, long long c)
+{
+    const float inv_n = 1.0f / (float)n;
+    const float ma = w[c], mb = w[S + c];
+    const float da = a - ma, db = b - mb;
+    const float na = ma + da * inv_n, nb = mb + db * inv_n;
+    f2 m2{w[2 * S + c], w[3 * S + c]};
+    m2 = df_add(m2, df_add(two_prod(da, a - na), two_prod(db, b - nb)));
+    w[c] = na; w[S + c] = nb;
+    w[2 * S + c] = m2.h; w[3 * S + c] = m2.l;
+}
+
+__global__ void __launch_bounds__(256) k_correct_mx(Grid g, MixConst K, MixState s, MixState ref, double x0, double y0,
                                                     int want_welford, double *__restrict__ series, Partials pt,
                                                     MemberCtl *ctl, double div_tol, long long nfluid)
 {
@@ -426,15 +457,17 @@ __global__ void __launch_bounds__(256) k_correct_mx(Grid g, MixConst K, MixState
     const float *__restrict__ xh = s.xh + off;
     const float *__restrict__ xl = s.xl + off;
     __shared__ float s_mean;
-    __shared__ int s_t;
+    __shared__ int s_t, s_gm;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     if (tid == 0) {
         s_mean = (float)(pt.red[m].val[RS_XSUM] / (double)nfluid);
         s_t = ctl[m].step - (g.n_steps - g.n_window);
+        s_gm = ctl[m].gidx;
     }
     __syncthreads();
     const float xmean = s_mean;
     const int t = (s_t > 0 && s_t <= g.n_window) ? s_t : 0;
+    const int gm = s_gm;
     int bad = 0;
     if (i <= g.nx && j <= g.ny) {
         const bool has_u = j < g.ny, has_v = i < g.nx, cell = has_u && has_v;
@@ -469,19 +502,19 @@ __global__ void __launch_bounds__(256) k_correct_mx(Grid g, MixConst K, MixState
                 const f2 vN = corrected(vkN, vNs, xN, x0v, gy);
                 const f2 uc = df_scale_half(df_add(un, uE));
                 const f2 vc = df_scale_half(df_add(vn, vN));
-                float *__restrict__ w = s.wf + 6 * off;
-                const long long S = g.S;
-                const f2 inv_n = df_recip_int(t);
-                const f2 mu{w[c], w[S + c]}, mv{w[2 * S + c], w[3 * S + c]};
-                f2 m2{w[4 * S + c], w[5 * S + c]};
-                const f2 du = df_sub(uc, mu);
-                const f2 mun = df_add(mu, df_mul(du, inv_n));
-                const f2 dv = df_sub(vc, mv);
-                const f2 mvn = df_add(mv, df_mul(dv, inv_n));
-                m2 = df_add(m2, df_add(df_mul(du, df_sub(uc, mun)), df_mul(dv, df_sub(vc, mvn))));
-                w[c] = mun.h; w[S + c] = mun.l;
-                w[2 * S + c] = mvn.h; w[3 * S + c] = mvn.l;
-                w[4 * S + c] = m2.h; w[5 * S + c] = m2.l;
+                welford2_df(uc, vc, t, s.wf + 6 * off, g.S, c);
+                if (s.wd && gm != 0) {
+                    // member 0's corrected cell-centred velocity from its predictor and increment,
+                    // which this kernel does not modify (member 0's own block writes only u, v, p)
+                    const f2 r_x0{ref.xh[c], ref.xl[c]};
+                    const f2 ru = corrected(uk0, f2{ref.ush[c], ref.usl[c]}, r_x0, f2{ref.xh[cW], ref.xl[cW]}, gx);
+                    const f2 ruE = corrected(ukE, f2{ref.ush[cE], ref.usl[cE]}, f2{ref.xh[cE], ref.xl[cE]}, r_x0, gx);
+                    const f2 rv = corrected(vk0, f2{ref.vsh[c], ref.vsl[c]}, r_x0, f2{ref.xh[cS], ref.xl[cS]}, gy);
+                    const f2 rvN = corrected(vkN, f2{ref.vsh[cN], ref.vsl[cN]}, f2{ref.xh[cN], ref.xl[cN]}, r_x0, gy);
+                    const f2 du = df_sub(uc, df_scale_half(df_add(ru, ruE)));
+                    const f2 dv = df_sub(vc, df_scale_half(df_add(rv, rvN)));
+                    welford2_diff(du.h + du.l, dv.h + dv.l, t, s.wd + 4 * off, g.S, c);
+                }
             }
         }
     }
@@ -500,34 +533,36 @@ __global__ void __launch_bounds__(256) k_correct_mx(Grid g, MixConst K, MixState
     }
 }
 
-void launch_correct_mx(const Grid &g, const MixConst &K, int M, const MixState &s, double x0, double y0,
-                       int want_welford, double *series, const Partials &pt, MemberCtl *ctl, double div_tol,
-                       long long nfluid, cudaStream_t st)
+void launch_correct_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const MixState &ref, double x0,
+                       double y0, int want_welford, double *series, const Partials &pt, MemberCtl *ctl,
+                       double div_tol, long long nfluid, cudaStream_t st)
 {
     dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), M);
-    k_correct_mx<<<grd, blk, 0, st>>>(g, K, s, x0, y0, want_welford, series, pt, ctl, div_tol, nfluid);
+    k_correct_mx<<<grd, blk, 0, st>>>(g, K, s, ref, x0, y0, want_welford, series, pt, ctl, div_tol, nfluid);
     count_launches(1);
 }
 
 // ---------------------------------------------------------------------------- cost
-__global__ void k_domain_partial_mx(Grid g, const float *__restrict__ wf, double *__restrict__ part)
+__global__ void k_plane_partial_mx(Grid g, const float *__restrict__ hi, const float *__restrict__ lo, long long mstride,
+                                   double *__restrict__ part)
 {
     int m = blockIdx.y;
-    const float *m2h = wf + 6LL * m * g.S + 4LL * g.S, *m2l = m2h + g.S;
+    const float *ph = hi + (long long)m * mstride, *pl = lo + (long long)m * mstride;
     long long ncell = (long long)g.ny * g.P;
     double acc = 0.0;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
         int i = (int)(c % g.P);
-        if (i < g.nx && g.fluid[c]) acc += (double)m2h[c] + (double)m2l[c];
+        if (i < g.nx && g.fluid[c]) acc += (double)ph[c] + (double)pl[c];
     }
     acc = block_reduce(acc, false);
     if (threadIdx.x == 0) part[(long long)m * gridDim.x + blockIdx.x] = acc;
 }
 
-void launch_domain_partial_mx(const Grid &g, int M, const float *wf, double *part, int nparts, cudaStream_t st)
+void launch_plane_partial_mx(const Grid &g, int M, const float *hi, const float *lo, long long mstride, double *part,
+                             int nparts, cudaStream_t st)
 {
     dim3 grd(nparts, M);
-    k_domain_partial_mx<<<grd, 256, 0, st>>>(g, wf, part);
+    k_plane_partial_mx<<<grd, 256, 0, st>>>(g, hi, lo, mstride, part);
     count_launches(1);
 }
 

@@ -68,6 +68,8 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 extern "C" int envar_draw_ensemble_noalloc(const envar_config *cfg, double *E_dev, int n_ctrl, void *cuda_stream)
 {
     if (!cfg || !E_dev) return fail(ENVAR_EINVAL, "null argument");
+    // a launch error left behind by unrelated earlier work on this thread is not this call's
+    (void)cudaGetLastError();
     const envar_config &c = *cfg;
     if (c.nx < 8 || c.ny < 4 || c.n_members < 1 || !(c.corr_len > 0) || !(c.x1 > c.x0) || !(c.y1 > c.y0))
         return fail(ENVAR_EINVAL, "invalid configuration");
@@ -140,9 +142,10 @@ extern "C" int envar_draw_ensemble_noalloc(const envar_config *cfg, double *E_de
         launch_conv_sampler(1, nrx, nry, nxix, nxiy, Gx, Gy, Z, dr, c.sigma, Er, T, st);
         launch_rect_to_compact(1, nrect, ncc, dc, Er, E_dev + (size_t)k * n_ctrl, st);
     }
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return fail(ENVAR_ECUDA, "ensemble draw launch", e);
     // the host vectors above are read by the copies: wait for them before returning
     e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ENVAR_ECUDA, "ensemble draw", e);
     return ENVAR_OK;
 }

@@ -85,11 +85,24 @@ def test_trajectory_parity_100_steps(precision):
     ens.close()
 
 
+# Tolerances of the cost / gradient parity.  FP64: the two solvers converge to 1e-12 divergence
+# (GPU) and 1e-13 relative CG residual (oracle), so J agrees to ~1e-10 relative and the gradient,
+# a difference quotient with eps = 1e-2, to ~1e-8 of its largest component; the bounds keep 10-100x
+# of margin.  MIXED: the velocity tolerance of the mixed path is 1e-4 relative; J = 1/2||h||^2 is
+# quadratic in the fluctuation, whose rounding errors are correlated across the window, so J is
+# held to 1e-5 relative (measured errors are listed in the design notes), and the gradient (member
+# differences, where most of the mixed rounding cancels) to 1e-3 of its largest component.
+TOL = {pkg.FP64_BATCHED: dict(J=1e-9, g=1e-6, series=1e-10), pkg.MIXED: dict(J=1e-5, g=1e-3, series=1e-6)}
+
+
+@pytest.mark.parametrize("precision", [pkg.FP64_BATCHED, pkg.MIXED])
 @pytest.mark.parametrize("mode", [pkg.COST_DOMAIN, pkg.COST_SENSORS])
-def test_envar_costs_and_gradient_parity(mode):
+def test_envar_costs_and_gradient_parity(mode, precision):
     nx, ny, N = 32, 16, 3
     P = oracle.cavity_params(nx, ny, 300.0)
-    cfg = tight(nx, ny, Re=300.0, n_steps=120, n_window=60, n_members=N, cost_mode=mode)
+    cfg = tight(nx, ny, Re=300.0, n_steps=120, n_window=60, n_members=N, cost_mode=mode, precision=precision)
+    if precision == pkg.MIXED:
+        cfg.div_tol, cfg.inner_rtol, cfg.max_inner, cfg.max_outer = 1e-12, 1e-5, 12, 6
     E = oracle.ensemble_seeded(P, cfg.sigma, cfg.corr_len, N, cfg.seed)
     w = synth.weights(N)
     u0, v0 = synth.cavity_ic(nx, ny)
@@ -99,17 +112,25 @@ def test_envar_costs_and_gradient_parity(mode):
     ens.forward_ensemble(w)
     J, jp = ens.cost()
     g = ens.gradient()
+    gs = ens.gradient_scalar()
+    tol = TOL[precision]
     ref = oracle.envar_gradient(P, u0, v0, E, w, cfg.eps, cfg.n_steps, cfg.n_window, cost_mode=mode,
                                 nthreads=4, want_series=True)
-    np.testing.assert_allclose(J, ref["J"], rtol=1e-9)
+    np.testing.assert_allclose(J, ref["J"], rtol=tol["J"])
     assert jp == pytest.approx(ref["J_prior"], rel=1e-14)
-    gref = ref["g"] if mode == pkg.COST_DOMAIN else oracle.sensor_gradient(ref["series"], w, cfg.eps)
-    assert np.abs(g - gref).max() <= 1e-6 * np.abs(gref).max(), (g, gref)
+    # scalar-anomaly form against the oracle's, the explicit contraction Y^T h_0 against the oracle's
+    assert np.abs(gs - ref["g"]).max() <= tol["g"] * np.abs(ref["g"]).max(), (gs, ref["g"])
+    if mode == pkg.COST_DOMAIN:
+        gref, _ = oracle.envar_gradient_domain(P, u0, v0, E, w, cfg.eps, cfg.n_steps, cfg.n_window, nthreads=3)
+    else:
+        gref = oracle.sensor_gradient(ref["series"], w, cfg.eps)
+    assert np.abs(g - gref).max() <= tol["g"] * np.abs(gref).max(), (g, gref)
     for m in range(N + 1):
-        np.testing.assert_allclose(ens.get_series(m), ref["series"][m], rtol=0, atol=1e-10)
+        np.testing.assert_allclose(ens.get_series(m), ref["series"][m], rtol=0, atol=tol["series"])
     # df = E g / (N - 1)
     _, df = ens.gradient(want_df=True)
     np.testing.assert_allclose(df.cpu().numpy(), E @ g / (N - 1), rtol=1e-12, atol=1e-15)
+    assert ens.excluded_members() == 0
     ens.close()
 
 
@@ -124,7 +145,7 @@ def test_plain_and_batched_agree():
         outs.append((ens.cost()[0], ens.gradient()))
         ens.close()
     np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=1e-13)
-    np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=1e-9, atol=1e-12 * np.abs(outs[1][1]).max())
 
 
 @pytest.mark.parametrize("nx,ny,N", [(32, 16, 3), (128, 64, 8), (512, 256, 32)])
@@ -140,6 +161,8 @@ def test_ensemble_draw_matches_oracle(nx, ny, N):
 
 
 def test_step_applies_prior_preconditioned_update():
+    """envar_step = forward ensemble + envar_gradient + the oracle's update of Sec. 3.3.1 (and the
+    total cost of Eq. J_w), on the same w."""
     nx, ny, N = 32, 16, 4
     cfg = tight(nx, ny, Re=300.0, n_steps=40, n_window=20, n_members=N)
     ens = pkg.Ensemble(cfg)
@@ -149,35 +172,98 @@ def test_step_applies_prior_preconditioned_update():
     J, jp = ens.cost()
     g = ens.gradient()
     w1, J0 = ens.step(0.5, w)
-    assert J0 == pytest.approx(J[0] + jp, rel=1e-13)
-    np.testing.assert_allclose(w1, w - 0.5 * g / (N - 1), rtol=1e-13, atol=1e-16)
+    w_ref, J_ref = oracle.envar_step(w, g, 0.5, J[0])
+    assert J0 == pytest.approx(J_ref, rel=1e-13)
+    np.testing.assert_allclose(w1, w_ref, rtol=1e-13, atol=1e-16)
     ens.close()
 
 
-def test_bench_configuration_sampled_parity():
-    """The bench's launch configuration (512x256, Re 7500, N = 32, mixed precision, all 33
-    members in one launch) over 10 steps: sampled members against the oracle."""
-    nx, ny, N, steps = 512, 256, 32, 10
-    cfg = pkg.default_config(nx, ny, Re=7500.0, n_steps=steps, n_window=5, n_members=N, precision=pkg.MIXED,
+def test_failed_member_is_excluded_from_the_gradient():
+    """Host-side fault injection: one column of E scaled by 1e6 drives its member over the CFL
+    limit (the kernels flag it; every loop stays bounded by its iteration cap).  That member's
+    component of g keeps only the prior term, every other component is unchanged bit for bit, and
+    the count is reported."""
+    nx, ny, N, bad = 32, 16, 4, 2
+    out = []
+    for scale in (1.0, 1e6):
+        cfg = tight(nx, ny, Re=300.0, n_steps=30, n_window=10, n_members=N, max_outer=3, max_inner=20)
+        ens = pkg.Ensemble(cfg)
+        ens.set_initial_state(*synth.cavity_ic(nx, ny))
+        E = ens.get_ensemble().cpu().numpy()
+        E[:, bad] *= scale
+        ens.set_ensemble(E)
+        w = synth.weights(N)
+        w[bad] = 0.0   # the unperturbed forcing E w must not see the scaled column
+        ens.forward_ensemble(w)
+        st = ens.member_status()
+        out.append((st, ens.gradient(), ens.excluded_members(), w))
+        ens.close()
+    (st0, g0, n0, _), (st1, g1, n1, w) = out
+    assert (st0 == 0).all() and n0 == 0
+    assert st1[bad + 1] & (pkg.ST_CFL | pkg.ST_NONFINITE) and n1 == 1
+    assert all(st1[m] == 0 for m in range(N + 1) if m != bad + 1)
+    assert g1[bad] == (N - 1) * w[bad]
+    keep = [i for i in range(N) if i != bad]
+    np.testing.assert_array_equal(g1[keep], g0[keep])
+
+
+def test_unconverged_pressure_solve_is_reported():
+    """max_outer = 1 with a divergence tolerance no solve can reach: every member carries the
+    divergence bit, and with the unperturbed member failed there is no gradient."""
+    nx, ny, N = 32, 16, 2
+    cfg = tight(nx, ny, Re=300.0, n_steps=6, n_window=3, n_members=N, max_outer=1, max_inner=2, div_tol=1e-30)
+    ens = pkg.Ensemble(cfg)
+    ens.set_initial_state(*synth.cavity_ic(nx, ny))
+    ens.forward_ensemble(synth.weights(N))
+    st = ens.member_status()
+    assert all(s & pkg.ST_DIVERGENCE for s in st), st
+    with pytest.raises(pkg.EnvarError, match="ESTATE"):
+        ens.gradient()
+    with pytest.raises(pkg.EnvarError, match="ESTATE"):
+        ens.step(0.5, synth.weights(N))
+    ens.close()
+
+
+def divergence_max(P, u, v):
+    """max |D u| over the fluid cells, recomputed from an exported state."""
+    F = oracle.fluid_mask(P).astype(bool)
+    d = (u[:, 1:] - u[:, :-1]) / P.dx + (v[1:, :] - v[:-1, :]) / P.dy
+    return float(np.abs(d[F]).max())
+
+
+def test_bench_configuration_100_steps_parity():
+    """The bench's launch configuration (512x256, Re 7500, N = 32, mixed precision, all 33 members in
+    one launch, four member groups, solver parameters chosen by the autotuner exactly as the bench
+    does) over 100 steps: members 0, 1, 16 and 32 against the oracle at the mixed tolerance 1e-4, and
+    the divergence of every member's final state recomputed here from the exported fields."""
+    nx, ny, N, steps = 512, 256, 32, 100
+    cfg = pkg.default_config(nx, ny, Re=7500.0, n_steps=steps, n_window=50, n_members=N, precision=pkg.MIXED,
                              div_tol=1e-10)
     P = oracle.cavity_params(nx, ny, 7500.0)
     u0, v0 = synth.cavity_ic(nx, ny)
     w = synth.weights(N)
-    ens = pkg.Ensemble(cfg)
-    ens.set_initial_state(u0, v0)
-    E = ens.get_ensemble().cpu().numpy()
+    sample = [0, 1, 16, N]
     Eo = oracle.ensemble_seeded(P, cfg.sigma, cfg.corr_len, N, cfg.seed)
-    assert np.abs(E - Eo).max() <= 1e-12 * np.abs(Eo).max()
-    ens.forward_ensemble(w)
     fs = member_forcings(Eo, w, cfg.eps)
-    sample = [0, N]
-    ref = oracle_trajectories(P, u0, v0, [fs[m] for m in sample], steps, workers=2)
+    with cf.ThreadPoolExecutor(max_workers=1) as pool:
+        # the oracle runs on the host cores while the GPU works
+        fut = pool.submit(oracle_trajectories, P, u0, v0, [fs[m] for m in sample], steps, len(sample))
+        ens = pkg.Ensemble(cfg)
+        ens.set_initial_state(u0, v0)
+        E = ens.get_ensemble().cpu().numpy()
+        assert np.abs(E - Eo).max() <= 1e-12 * np.abs(Eo).max()
+        chosen = ens.autotune(200)
+        ens.forward_ensemble(w)
+        assert (ens.member_status() == 0).all()
+        assert ens.diagnostics()["max_div"] <= 1e-10
+        states = {m: tuple(t.cpu().numpy() for t in ens.get_state(m)) for m in range(N + 1)}
+        ens.close()
+        ref = fut.result()
+    for m in range(N + 1):
+        assert divergence_max(P, states[m][0], states[m][1]) <= 1e-10, (m, chosen)
     for m, r in zip(sample, ref):
-        u, v, _ = (t.cpu().numpy() for t in ens.get_state(m))
-        assert vel_rel(u, v, r[0], r[1]) <= 1e-4
-    assert ens.diagnostics()["max_div"] <= 1e-10
-    assert (ens.member_status() == 0).all()
-    ens.close()
+        u, v, _ = states[m]
+        assert vel_rel(u, v, r[0], r[1]) <= 1e-4, (m, chosen)
 
 
 @pytest.mark.parametrize("precision", [pkg.FP64_BATCHED, pkg.MIXED])
