@@ -114,6 +114,9 @@ def _configure(L):
                                        c_int, c_int, c_int, c_int, _dp, _dp,
                                        ctypes.POINTER(c_double), c_void_p]),
         "orc_envar_step": (None, [c_int, _dp, _dp, c_double, c_double, _dp, ctypes.POINTER(c_double)]),
+        "orc_sensor_anomalies": (None, [c_int, c_int, _dp, c_double, _dp, _dp]),
+        "orc_gauss_newton_step": (c_int, [c_int, c_int, _dp, _dp, _dp, c_double, _dp, c_void_p, c_void_p]),
+        "orc_lbfgs_direction": (None, [c_int, c_int, _dp, _dp, _dp, c_double, _dp]),
         "orc_domain_observation": (c_int, [P, _dp, _dp, _dp, _dp, c_int, c_int, _dp]),
         "orc_envar_gradient_domain": (c_int, [P, _dp, _dp, _dp, c_int, c_int, _dp, _dp, c_double, c_int,
                                               c_int, c_int, _dp, _dp]),
@@ -513,3 +516,37 @@ def envar_gradient_domain(P: Params, u0, v0, E, w, eps: float, n_steps: int, n_w
     if rc != 0:
         raise RuntimeError(f"oracle domain gradient failed ({rc})")
     return g, yy
+
+
+def sensor_anomalies(series, eps: float):
+    """Sensor-space Y of Eq. (fdapprox) and h_0: series [N+1][n_window][8] -> (Y [N][8 n_w], h0)."""
+    series = np.ascontiguousarray(series, dtype=np.float64)
+    N, nw = series.shape[0] - 1, series.shape[1]
+    Y, h0 = np.zeros((N, 8 * nw)), np.zeros(8 * nw)
+    lib().orc_sensor_anomalies(N, nw, series.reshape(-1), float(eps), Y, h0)
+    return Y, h0
+
+
+def gauss_newton_step(Y, h0, w, alpha: float = 1.0):
+    """Sec. 3.3.1 Gauss-Newton: (w + alpha dw, H_GN, g) with H_GN = Y^T Y + (N-1) I,
+    g = Y^T h0 + (N-1) w, dw = -H_GN^{-1} g."""
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    N, nobs = Y.shape
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out, H, g = np.zeros(N), np.zeros((N, N)), np.zeros(N)
+    rc = lib().orc_gauss_newton_step(N, nobs, Y, np.ascontiguousarray(h0, dtype=np.float64), w, float(alpha), out,
+                                     H.ctypes.data_as(c_void_p), g.ctypes.data_as(c_void_p))
+    if rc != 0:
+        raise ValueError("Gauss-Newton Hessian is not positive definite")
+    return out, H, g
+
+
+def lbfgs_direction(S, Yh, g, gamma: float):
+    """L-BFGS direction -H g (two-loop recursion) from pairs S, Yh [m][N], oldest first."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    N = len(g)
+    S = np.ascontiguousarray(np.reshape(S, (-1, N)), dtype=np.float64)
+    Yh = np.ascontiguousarray(np.reshape(Yh, (-1, N)), dtype=np.float64)
+    p = np.zeros(N)
+    lib().orc_lbfgs_direction(N, S.shape[0], S.reshape(-1), Yh.reshape(-1), g, float(gamma), p)
+    return p

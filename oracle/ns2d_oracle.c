@@ -1297,6 +1297,120 @@ int orc_envar_gradient_domain(const orc_params *P, const double *region, const d
     return 0;
 }
 
+/* ------------------------ reduced-space optimisers ---------------------- */
+/* Sensor-space observation anomalies of Eq. (fdapprox): h_m = series_m - its window mean
+ * (8 n_window observations, R = I, y = 0), Y[i] = (h_{i+1} - h_0)/eps, i = 0..N-1, stored
+ * row-wise [N][nobs]; h0 receives h_0 (nobs). */
+void orc_sensor_anomalies(int N, int n_window, const double *series, double eps, double *Y, double *h0)
+{
+    size_t nobs = (size_t)n_window * 8;
+    double *h = (double *)xcalloc(nobs, sizeof(double));
+    for (int m = 0; m <= N; ++m) {
+        const double *sm = series + (size_t)m * nobs;
+        double *dst = (m == 0) ? h0 : h;
+        for (int c = 0; c < 8; ++c) {
+            double mean = 0.0;
+            for (int t = 0; t < n_window; ++t) mean += sm[(size_t)t * 8 + c];
+            mean /= n_window;
+            for (int t = 0; t < n_window; ++t) dst[(size_t)t * 8 + c] = sm[(size_t)t * 8 + c] - mean;
+        }
+        if (m == 0) continue;
+        for (size_t k = 0; k < nobs; ++k) Y[(size_t)(m - 1) * nobs + k] = (h[k] - h0[k]) / eps;
+    }
+    free(h);
+}
+
+/* Dense Cholesky A = L L^T (lower, row-major n x n, in place); returns -1 if A is not positive
+ * definite.  Then solve A x = b. */
+static int cholesky(int n, double *A)
+{
+    for (int j = 0; j < n; ++j) {
+        double d = A[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+        if (!(d > 0.0)) return -1;
+        d = sqrt(d);
+        A[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double a = A[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) a -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+            A[(size_t)i * n + j] = a / d;
+        }
+    }
+    return 0;
+}
+static void cholesky_solve(int n, const double *L, const double *b, double *x)
+{
+    for (int i = 0; i < n; ++i) {
+        double a = b[i];
+        for (int k = 0; k < i; ++k) a -= L[(size_t)i * n + k] * x[k];
+        x[i] = a / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double a = x[i];
+        for (int k = i + 1; k < n; ++k) a -= L[(size_t)k * n + i] * x[k];
+        x[i] = a / L[(size_t)i * n + i];
+    }
+}
+
+/* Gauss-Newton step of Sec. 3.3.1: H_GN = Y^T R^{-1} Y + (N-1) I (Eq. Hessian_EnVar, R = I),
+ * g = Y^T (Hq_0 - y) + (N-1) w (Eq. gradient_EnVar, y = 0), dw = -H_GN^{-1} g (Eq. update_Newton),
+ * w_out = w + alpha dw.  Y: [N][nobs]; H_out (may be NULL): H_GN, row-major N x N; g_out (may be
+ * NULL): g.  Returns -1 if H_GN is not positive definite. */
+int orc_gauss_newton_step(int N, int nobs, const double *Y, const double *h0, const double *w, double alpha,
+                          double *w_out, double *H_out, double *g_out)
+{
+    double *H = (double *)xcalloc((size_t)N * N, sizeof(double));
+    double *g = (double *)xcalloc((size_t)N, sizeof(double));
+    double *dw = (double *)xcalloc((size_t)N, sizeof(double));
+    for (int i = 0; i < N; ++i) {
+        double gi = 0.0;
+        for (size_t k = 0; k < (size_t)nobs; ++k) gi += Y[(size_t)i * nobs + k] * h0[k];
+        g[i] = gi + (double)(N - 1) * w[i];
+        for (int j = 0; j < N; ++j) {
+            double a = 0.0;
+            for (size_t k = 0; k < (size_t)nobs; ++k) a += Y[(size_t)i * nobs + k] * Y[(size_t)j * nobs + k];
+            H[(size_t)i * N + j] = a + (i == j ? (double)(N - 1) : 0.0);
+        }
+    }
+    if (H_out) memcpy(H_out, H, sizeof(double) * (size_t)N * N);
+    if (g_out) memcpy(g_out, g, sizeof(double) * (size_t)N);
+    int rc = cholesky(N, H);
+    if (rc == 0) {
+        cholesky_solve(N, H, g, dw);
+        for (int i = 0; i < N; ++i) w_out[i] = w[i] - alpha * dw[i];
+    }
+    free(H); free(g); free(dw);
+    return rc;
+}
+
+/* L-BFGS search direction of Sec. 3.3.1 (Eq. update_BFGS): p = -H g with H the limited-memory BFGS
+ * inverse-Hessian approximation built from the m most recent pairs s_k = w_{k+1} - w_k,
+ * y_k = g_{k+1} - g_k (oldest first, rows of S and Yh, [m][N]) on the initial matrix gamma I,
+ * evaluated by the two-loop recursion (Nocedal and Wright, Numerical Optimization, Alg. 7.4). */
+void orc_lbfgs_direction(int N, int m, const double *S, const double *Yh, const double *g, double gamma, double *p)
+{
+    double *q = (double *)xcalloc((size_t)N, sizeof(double));
+    double *a = (double *)xcalloc((size_t)(m > 0 ? m : 1), sizeof(double));
+    for (int i = 0; i < N; ++i) q[i] = g[i];
+    for (int k = m - 1; k >= 0; --k) {
+        const double *s = S + (size_t)k * N, *y = Yh + (size_t)k * N;
+        double sy = 0.0, sq = 0.0;
+        for (int i = 0; i < N; ++i) { sy += s[i] * y[i]; sq += s[i] * q[i]; }
+        a[k] = sq / sy;
+        for (int i = 0; i < N; ++i) q[i] -= a[k] * y[i];
+    }
+    for (int i = 0; i < N; ++i) q[i] *= gamma;
+    for (int k = 0; k < m; ++k) {
+        const double *s = S + (size_t)k * N, *y = Yh + (size_t)k * N;
+        double sy = 0.0, yq = 0.0;
+        for (int i = 0; i < N; ++i) { sy += s[i] * y[i]; yq += y[i] * q[i]; }
+        double b = yq / sy;
+        for (int i = 0; i < N; ++i) q[i] += s[i] * (a[k] - b);
+    }
+    for (int i = 0; i < N; ++i) p[i] = -q[i];
+    free(q); free(a);
+}
+
 typedef struct {
     const orc_params *P;
     const double *region, *u0, *v0, *E, *w;

@@ -679,6 +679,73 @@ def test_envar_step_update_and_total_cost():
 
 
 # --------------------------------------------------------------------------
+# Reduced-space optimisers (Sec. 3.3.1, Eq. Hessian_EnVar, update_Newton, update_BFGS).
+# --------------------------------------------------------------------------
+def test_gauss_newton_is_exact_in_one_step_for_linear_dynamics():
+    """Stokes flow and the sensor cost: h(w) is affine, so J(w) = 1/2||h0 + Y w||^2 + (N-1)/2 w^T w is
+    quadratic with Hessian exactly Y^T Y + (N-1) I; one Gauss-Newton step lands on its minimiser, where
+    the EnVar gradient (new forward runs at the new w) vanishes."""
+    P = oracle.cavity_params(32, 16, 300.0, advection=0)
+    N, sigma, a, eps = 3, 0.1, 0.05, 1e-2
+    E = oracle.ensemble_seeded(P, sigma, a, N, 1000)
+    u0, v0 = synth.cavity_ic(32, 16)
+    n_steps, n_window = 80, 40
+    w = np.array([0.3, -0.2, 0.1])
+    out = oracle.envar_gradient(P, u0, v0, E, w, eps, n_steps, n_window, cost_mode=oracle.COST_SENSORS,
+                                nthreads=4, want_series=True)
+    Y, h0 = oracle.sensor_anomalies(out["series"], eps)
+    w1, H, g = oracle.gauss_newton_step(Y, h0, w, 1.0)
+    np.testing.assert_allclose(g, oracle.sensor_gradient(out["series"], w, eps), rtol=1e-12)
+    np.testing.assert_allclose(H, H.T, rtol=0, atol=1e-14 * np.abs(H).max())
+    assert np.linalg.eigvalsh(H - (N - 1) * np.eye(N)).min() >= -1e-12 * np.abs(H).max()
+    out1 = oracle.envar_gradient(P, u0, v0, E, w1, eps, n_steps, n_window, cost_mode=oracle.COST_SENSORS,
+                                 nthreads=4, want_series=True)
+    g1 = oracle.sensor_gradient(out1["series"], w1, eps)
+    assert np.abs(g1).max() <= 1e-7 * np.abs(g).max(), (g1, g)
+    # and the minimum is below the start (J = J_obs + J_prior of Eq. J_w)
+    assert out1["J"][0] + out1["J_prior"] < out["J"][0] + out["J_prior"]
+
+
+def test_gauss_newton_hessian_matches_dense_definition():
+    rng = np.random.default_rng(21)
+    N, nw = 5, 12
+    series = rng.standard_normal((N + 1, nw, 8))
+    eps = 0.1
+    Y, h0 = oracle.sensor_anomalies(series, eps)
+    h = series - series.mean(axis=1, keepdims=True)
+    Yref = ((h[1:] - h[0]) / eps).reshape(N, -1)
+    np.testing.assert_allclose(Y, Yref, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(h0, h[0].reshape(-1), rtol=1e-13, atol=1e-14)
+    w = rng.standard_normal(N)
+    w1, H, g = oracle.gauss_newton_step(Y, h0, w, 0.5)
+    Href = Yref @ Yref.T + (N - 1) * np.eye(N)
+    np.testing.assert_allclose(H, Href, rtol=1e-12)
+    np.testing.assert_allclose(w1, w - 0.5 * np.linalg.solve(Href, Yref @ h[0].reshape(-1) + (N - 1) * w),
+                               rtol=1e-10)
+
+
+def test_lbfgs_two_loop_equals_dense_bfgs_update():
+    """The two-loop recursion reproduces the dense BFGS inverse update
+    H+ = (I - rho s y^T) H (I - rho y s^T) + rho s s^T applied to gamma I, pair by pair."""
+    rng = np.random.default_rng(5)
+    N, m = 6, 4
+    A = rng.standard_normal((N, N))
+    A = A @ A.T + N * np.eye(N)
+    S = rng.standard_normal((m, N))
+    Yh = S @ A                       # curvature pairs of a convex quadratic: s^T y > 0
+    g = rng.standard_normal(N)
+    gamma = 0.37
+    H = gamma * np.eye(N)
+    for s, y in zip(S, Yh):
+        rho = 1.0 / (y @ s)
+        V = np.eye(N) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    np.testing.assert_allclose(oracle.lbfgs_direction(S, Yh, g, gamma), -H @ g, rtol=1e-11)
+    # with no pairs the direction is steepest descent scaled by gamma
+    np.testing.assert_allclose(oracle.lbfgs_direction(np.zeros((0, N)), np.zeros((0, N)), g, gamma), -gamma * g)
+
+
+# --------------------------------------------------------------------------
 # Costs (Sec. 4.1, Eq. specific_cost_function; Eq. kinenergy): closed forms.
 # --------------------------------------------------------------------------
 def test_costs_closed_form_on_stokes_decay():
