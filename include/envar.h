@@ -183,6 +183,34 @@ int envar_step(envar_handle h, double alpha, double *w_inout_host, double *J0_ou
  * unperturbed member is not detected here: check envar_member_status after the step. */
 int envar_step_device(envar_handle h, double alpha, double *w_inout_dev, double *J0_out_dev);
 
+/* Gauss-Newton EnVar iteration (Sec. 3.3.1, Eq. Hessian_EnVar and Eq. update_Newton): forward
+ * ensemble at w, the sensor-space Y of Eq. (fdapprox) (members with a nonzero status word give a
+ * zero column), H_GN = Y^T R^{-1} Y + (N-1) I with R = I, g of Eq. (gradient_EnVar), and
+ * w <- w - alpha H_GN^{-1} g (alpha = 1: the full Gauss-Newton step).  Needs the SENSORS cost.
+ * w_inout_host: N doubles (host, in/out).  J0_out_host (nullable): J(w) before the update.
+ * ENVAR_ESTATE (w unchanged) if member 0 failed or H_GN is not positive definite. */
+int envar_gn_step(envar_handle h, double alpha, double *w_inout_host, double *J0_out_host);
+
+/* H_GN = Y^T Y + (N-1) I of the last forward run (N x N row-major, host); SENSORS cost only. */
+int envar_gn_hessian(envar_handle h, double *H_host);
+
+/* Limited-memory BFGS EnVar iteration (Sec. 3.3.1, Eq. update_BFGS): forward ensemble at w and g;
+ * the pair (w - w_prev, g - g_prev) of the previous call joins the history when its curvature is
+ * positive; the direction p = -H g comes from the two-loop recursion over the newest `memory`
+ * pairs on the initial matrix (s^T y / y^T y) I, or (1/(N-1)) I without pairs (the inverse prior
+ * Hessian); the step length a = 1, 1/2, 1/4, ... (at most 12 trials) is the first that meets the
+ * Armijo condition J(w + a p) <= J(w) + 1e-4 a g^T p, each trial cost J = J_obs + (N-1)/2 w^T w
+ * from one forward run of the unperturbed member alone.  Either cost mode.
+ * w_inout_host: N doubles (host, in/out).  J0_out_host (nullable): J(w) before the update;
+ * alpha_out_host (nullable): the accepted step length; evals_out_host (nullable): trial runs.
+ * ENVAR_ESTATE (w unchanged, history kept but no pair pending) if no trial met the condition or
+ * member 0 failed.  Leaves member slot 0 holding the last trial run. */
+int envar_lbfgs_step(envar_handle h, double *w_inout_host, double *J0_out_host, double *alpha_out_host,
+                     int *evals_out_host);
+
+/* Clear the L-BFGS history and set its length (1 .. 64 pairs; the first envar_lbfgs_step uses 8). */
+int envar_lbfgs_reset(envar_handle h, int memory);
+
 /* Run ONE member with a given control vector f (n_ctrl doubles, device) over
  * n_steps and return its observation cost (host).  Member slot 0 is used. */
 int envar_forward_control(envar_handle h, const double *f_dev, double *J_host);

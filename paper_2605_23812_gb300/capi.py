@@ -72,6 +72,10 @@ def lib():
         "envar_gradient": [H, c_void_p, c_void_p],
         "envar_gradient_scalar": [H, c_void_p],
         "envar_excluded_members": [H, ctypes.POINTER(c_int)],
+        "envar_gn_step": [H, c_double, c_void_p, c_void_p],
+        "envar_gn_hessian": [H, c_void_p],
+        "envar_lbfgs_step": [H, c_void_p, c_void_p, c_void_p, c_void_p],
+        "envar_lbfgs_reset": [H, c_int],
         "envar_step": [H, c_double, c_void_p, c_void_p],
         "envar_step_device": [H, c_double, c_void_p, c_void_p],
         "envar_forward_control": [H, c_void_p, c_void_p],
@@ -219,6 +223,30 @@ class Ensemble:
         J0 = np.zeros(1)
         self._check(lib().envar_step(self._h, float(alpha), _np_ptr(w), _np_ptr(J0)), "envar_step")
         return w, float(J0[0])
+
+    def gn_step(self, alpha, w):
+        """Gauss-Newton EnVar iteration (SENSORS cost): returns (w_new, J(w))."""
+        w = np.ascontiguousarray(w, dtype=np.float64).copy()
+        J0 = np.zeros(1)
+        self._check(lib().envar_gn_step(self._h, float(alpha), _np_ptr(w), _np_ptr(J0)), "envar_gn_step")
+        return w, float(J0[0])
+
+    def gn_hessian(self):
+        H = np.zeros((self.N, self.N))
+        self._check(lib().envar_gn_hessian(self._h, _np_ptr(H)), "envar_gn_hessian")
+        return H
+
+    def lbfgs_step(self, w):
+        """L-BFGS EnVar iteration with Armijo backtracking: returns (w_new, J(w), step length, trials)."""
+        w = np.ascontiguousarray(w, dtype=np.float64).copy()
+        J0, a = np.zeros(1), np.zeros(1)
+        n = c_int()
+        self._check(lib().envar_lbfgs_step(self._h, _np_ptr(w), _np_ptr(J0), _np_ptr(a), ctypes.byref(n)),
+                    "envar_lbfgs_step")
+        return w, float(J0[0]), float(a[0]), n.value
+
+    def lbfgs_reset(self, memory: int = 8):
+        self._check(lib().envar_lbfgs_reset(self._h, int(memory)), "envar_lbfgs_reset")
 
     def step_device(self, alpha, w_dev, J0_dev=None):
         """envar_step on device-resident tensors (w_dev updated in place)."""

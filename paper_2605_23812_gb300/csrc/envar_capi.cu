@@ -88,6 +88,15 @@ struct envar_handle_s {
     cudaEvent_t ev_fork = nullptr, ev_join[ENVAR_MAX_GROUPS] = {};
     cudaEvent_t ev_solved0 = nullptr;   // member 0's pressure increment is final (group 0)
     int cimg_bytes = 0;
+    // reduced-space optimisers (allocated on first use)
+    double *d_Y = nullptr, *d_h0 = nullptr, *d_smean = nullptr, *d_H = nullptr, *d_L = nullptr, *d_x = nullptr;
+    int *d_info = nullptr;
+    int lb_m = 0, lb_count = 0, lb_head = 0;
+    bool lb_have_prev = false;
+    double *d_lbS = nullptr, *d_lbY = nullptr, *d_lbsy = nullptr, *d_lbq = nullptr, *d_lba = nullptr;
+    double *d_lbp = nullptr, *d_lbgp = nullptr, *d_wprev = nullptr, *d_gprev = nullptr, *d_wt = nullptr;
+    double *d_prior_t = nullptr;
+    int *d_lborder = nullptr;
     char err[512] = {0};
 };
 
@@ -523,6 +532,7 @@ static int alloc_buffers(envar_handle h)
     DA(h->d_status, N + 1);
     CK(cudaMemset(h->d_status, 0, sizeof(int) * (N + 1)));
     DA(h->d_w, std::max(N, 1)); DA(h->d_g, std::max(N, 1)); DA(h->d_jprior, 1); DA(h->d_gscalar, std::max(N, 1));
+    DA(h->d_wt, std::max(N, 1));
     CK(cudaMemset(h->d_w, 0, sizeof(double) * std::max(N, 1)));
     return ENVAR_OK;
 }
@@ -1076,6 +1086,200 @@ extern "C" int envar_step_device(envar_handle h, double alpha, double *w_inout, 
     launch_update_w(h->N, h->d_w, h->d_g, alpha / std::max(h->N - 1, 1), h->st);
     CK(cudaMemcpyAsync(w_inout, h->d_w, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+// ------------------------------------------------------------------------------------ optimisers
+// Sec. 3.3.1: Gauss-Newton with H_GN = Y^T Y + (N-1) I (Eq. Hessian_EnVar, update_Newton) on the
+// sensor-space Y of Eq. (fdapprox), and L-BFGS (Eq. update_BFGS) with an Armijo line search.
+
+static int gn_buffers(envar_handle h)
+{
+    if (h->d_Y) return ENVAR_OK;
+    const int N = h->N;
+    const long long nobs = 8LL * h->cfg.n_window;
+    DA(h->d_Y, (size_t)N * nobs); DA(h->d_h0, nobs); DA(h->d_smean, (size_t)(N + 1) * 8);
+    DA(h->d_H, (size_t)N * N); DA(h->d_L, (size_t)N * N); DA(h->d_x, N); DA(h->d_info, 1);
+    return ENVAR_OK;
+}
+
+// H_GN and g of the last forward run into d_H, d_g (device).
+static int gn_assemble(envar_handle h)
+{
+    if (int rc = gn_buffers(h)) return rc;
+    const long long nobs = 8LL * h->cfg.n_window;
+    launch_sensor_anomalies(h->N, h->cfg.n_window, h->d_series, h->cfg.eps, h->d_status, h->d_smean, h->d_Y, h->d_h0,
+                            h->st);
+    launch_gram(h->N, nobs, h->d_Y, h->d_h0, h->d_w, h->d_H, h->d_g, h->st);
+    return ENVAR_OK;
+}
+
+static int gn_check(envar_handle h, const char *what)
+{
+    if (h->cfg.cost_mode != ENVAR_COST_SENSORS || h->cfg.n_window < 1 || h->N < 1) {
+        set_err(h, "%s: Gauss-Newton needs the SENSORS observation operator, n_window >= 1 and N >= 1", what);
+        return ENVAR_EINVAL;
+    }
+    return ENVAR_OK;
+}
+
+extern "C" int envar_gn_hessian(envar_handle h, double *H_host)
+{
+    if (!h || !H_host) return ENVAR_EINVAL;
+    if (int rc = gn_check(h, "envar_gn_hessian")) return rc;
+    if (!h->have_forward) { set_err(h, "envar_gn_hessian: no forward run"); return ENVAR_ESTATE; }
+    if (int rc = gn_assemble(h)) return rc;
+    CK(cudaMemcpyAsync(H_host, h->d_H, sizeof(double) * h->N * h->N, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+extern "C" int envar_gn_step(envar_handle h, double alpha, double *w_inout, double *J0_out)
+{
+    if (!h || !w_inout) return ENVAR_EINVAL;
+    if (int rc = gn_check(h, "envar_gn_step")) return rc;
+    if (!h->have_ic) { set_err(h, "envar_gn_step: no initial state"); return ENVAR_ESTATE; }
+    CK(cudaMemcpyAsync(h->d_w, w_inout, sizeof(double) * h->N, cudaMemcpyHostToDevice, h->st));
+    int rc = forward_members(h);
+    if (rc) return rc;
+    if ((rc = check_member0(h, "envar_gn_step"))) return rc;
+    compute_gradient(h);   // J_prior; d_g is rebuilt by the Gram kernel (same contraction)
+    if ((rc = gn_assemble(h))) return rc;
+    launch_cholesky_step(h->N, h->d_H, h->d_L, h->d_g, h->d_w, alpha, h->d_x, h->d_wt, h->d_info, h->st);
+    double J0 = 0.0, jp = 0.0;
+    int info = 0;
+    CK(cudaMemcpyAsync(&J0, h->d_Js, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&jp, h->d_jprior, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&info, h->d_info, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (info != 0) {
+        set_err(h, "envar_gn_step: H_GN is not positive definite (pivot %d)", info);
+        return ENVAR_ESTATE;
+    }
+    CK(cudaMemcpyAsync(h->d_w, h->d_wt, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(w_inout, h->d_w, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    if (J0_out) *J0_out = J0 + jp;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_lbfgs_reset(envar_handle h, int memory)
+{
+    if (!h || memory < 1 || memory > 64 || h->N < 1) return ENVAR_EINVAL;
+    if (h->lb_m != memory) {
+        const int N = h->N;
+        DA(h->d_lbS, (size_t)memory * N); DA(h->d_lbY, (size_t)memory * N); DA(h->d_lbsy, 2 * memory);
+        DA(h->d_lba, memory); DA(h->d_lborder, memory);
+        if (!h->d_lbq) {
+            DA(h->d_lbq, N); DA(h->d_lbp, N); DA(h->d_lbgp, 1); DA(h->d_wprev, N); DA(h->d_gprev, N);
+            DA(h->d_prior_t, 1);
+            if (!h->d_wt) DA(h->d_wt, N);
+        }
+        h->lb_m = memory;
+    }
+    h->lb_count = 0;
+    h->lb_head = 0;
+    h->lb_have_prev = false;
+    return ENVAR_OK;
+}
+
+// J(w_t) = J_obs of member 0 alone with forcing E w_t, plus the prior (N-1)/2 w_t^T w_t (Eq. J_w).
+static int trial_cost(envar_handle h, const double *wt, double *J)
+{
+    launch_member_forcing(1, 0, h->N, h->nrect, h->d_Erect, wt, h->cfg.eps, h->d_frect, h->ms.frect, h->st);
+    reset_members(h, 1);
+    int rc = run_steps(h, 1, h->cfg.n_steps);
+    if (rc) return rc;
+    enqueue_cost(h, 1, h->d_Jd_slot, h->d_Js_slot, h->d_Yd_slot);
+    const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js_slot : h->d_Jd_slot;
+    double jo = 0.0, jp = 0.0;
+    MemberCtl c0{};
+    CK(cudaMemcpyAsync(&jo, src, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&jp, h->d_prior_t, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&c0, h->d_ctl, sizeof(MemberCtl), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    *J = (c0.status != 0) ? HUGE_VAL : jo + jp;   // a failed trial run is rejected by the line search
+    return ENVAR_OK;
+}
+
+extern "C" int envar_lbfgs_step(envar_handle h, double *w_inout, double *J0_out, double *alpha_out, int *evals_out)
+{
+    if (!h || !w_inout) return ENVAR_EINVAL;
+    if (!h->have_ic) { set_err(h, "envar_lbfgs_step: no initial state"); return ENVAR_ESTATE; }
+    if (h->N < 1) { set_err(h, "envar_lbfgs_step: ensemble is empty"); return ENVAR_ESTATE; }
+    int rc = 0;
+    if (h->lb_m == 0 && (rc = envar_lbfgs_reset(h, 8))) return rc;
+    const int N = h->N, m = h->lb_m;
+    CK(cudaMemcpyAsync(h->d_w, w_inout, sizeof(double) * N, cudaMemcpyHostToDevice, h->st));
+    if ((rc = forward_members(h))) return rc;
+    if ((rc = check_member0(h, "envar_lbfgs_step"))) return rc;
+    compute_gradient(h);
+    // curvature pair from the previous iteration
+    if (h->lb_have_prev) {
+        const int slot = h->lb_head;
+        launch_lbfgs_pair(N, h->d_w, h->d_wprev, h->d_g, h->d_gprev, slot, h->d_lbS, h->d_lbY, h->d_lbsy, m, h->st);
+        double sy[2] = {0.0, 0.0};
+        CK(cudaMemcpyAsync(&sy[0], h->d_lbsy + slot, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(&sy[1], h->d_lbsy + m + slot, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        if (sy[0] > 1e-10 * std::sqrt(sy[1])) {   // keep only pairs of positive curvature
+            h->lb_head = (h->lb_head + 1) % m;
+            h->lb_count = std::min(h->lb_count + 1, m);
+        }
+    }
+    std::vector<int> order((size_t)h->lb_count);
+    for (int r = 0; r < h->lb_count; ++r) order[r] = (h->lb_head - h->lb_count + r + m) % m;
+    if (h->lb_count) CK(cudaMemcpyAsync(h->d_lborder, order.data(), sizeof(int) * h->lb_count, cudaMemcpyHostToDevice,
+                                        h->st));
+    const double gamma0 = 1.0 / std::max(N - 1, 1);   // inverse of the prior Hessian (N-1) I
+    launch_lbfgs_direction(N, h->lb_count, h->d_lborder, h->d_lbS, h->d_lbY, h->d_g, gamma0, h->d_lbq, h->d_lba,
+                           h->d_lbp, h->d_lbgp, h->st);
+    CK(cudaMemcpyAsync(h->d_wprev, h->d_w, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->d_gprev, h->d_g, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->st));
+    const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js : h->d_Jd;
+    double J0 = 0.0, jp = 0.0, gp = 0.0;
+    CK(cudaMemcpyAsync(&J0, src, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&jp, h->d_jprior, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&gp, h->d_lbgp, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const double Jw = J0 + jp;
+    if (!(gp < 0.0)) {
+        // not a descent direction: drop the history and take the prior-preconditioned gradient step
+        h->lb_count = 0;
+        launch_lbfgs_direction(N, 0, h->d_lborder, h->d_lbS, h->d_lbY, h->d_g, gamma0, h->d_lbq, h->d_lba, h->d_lbp,
+                               h->d_lbgp, h->st);
+        CK(cudaMemcpyAsync(&gp, h->d_lbgp, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+    }
+    // Armijo backtracking: J(w + a p) <= J(w) + c1 a g^T p, a = 1, 1/2, ...
+    const double c1 = 1e-4;
+    double a = 1.0, Jt = 0.0;
+    int evals = 0;
+    bool ok = false;
+    for (int k = 0; k < 12 && !ok; ++k, a *= 0.5) {
+        launch_trial_point(N, h->d_w, h->d_lbp, a, h->d_wt, h->d_prior_t, h->st);
+        if ((rc = trial_cost(h, h->d_wt, &Jt))) return rc;
+        ++evals;
+        ok = Jt <= Jw + c1 * a * gp;
+        if (ok) break;
+    }
+    h->have_forward = false;   // slot 0 now holds the last trial run
+    h->last_member_slot0 = -2;
+    if (evals_out) *evals_out = evals;
+    if (J0_out) *J0_out = Jw;
+    if (!ok) {
+        set_err(h, "envar_lbfgs_step: no step length met the Armijo condition (g^T p = %g)", gp);
+        h->lb_have_prev = false;
+        return ENVAR_ESTATE;
+    }
+    CK(cudaMemcpyAsync(h->d_w, h->d_wt, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(w_inout, h->d_wt, sizeof(double) * N, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    h->lb_have_prev = true;
+    if (alpha_out) *alpha_out = a;
     return ENVAR_OK;
 }
 

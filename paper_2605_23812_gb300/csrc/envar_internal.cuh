@@ -338,4 +338,17 @@ void launch_update_w(int N, double *w, const double *g, double step, cudaStream_
 void launch_d2f(long long n, const double *a, float *b, cudaStream_t st);
 void launch_total_cost(const double *J, const double *jp, double *out, cudaStream_t st);
 
+// Reduced-space optimisers (k_optim.cu)
+void launch_sensor_anomalies(int N, int nw, const double *series, double eps, const int *status, double *mean,
+                             double *Y, double *h0, cudaStream_t st);
+void launch_gram(int N, long long nobs, const double *Y, const double *h0, const double *w, double *H, double *g,
+                 cudaStream_t st);
+void launch_cholesky_step(int N, const double *A, double *Lw, const double *g, const double *w, double alpha, double *x,
+                          double *w_out, int *info, cudaStream_t st);
+void launch_lbfgs_pair(int N, const double *w, const double *wp, const double *g, const double *gp, int slot,
+                       double *S, double *Yh, double *sy, int m, cudaStream_t st);
+void launch_lbfgs_direction(int N, int count, const int *order, const double *S, const double *Yh, const double *g,
+                            double gamma0, double *q, double *alpha, double *p, double *gp, cudaStream_t st);
+void launch_trial_point(int N, const double *w, const double *p, double a, double *wt, double *prior, cudaStream_t st);
+
 } // namespace envar

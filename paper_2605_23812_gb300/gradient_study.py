@@ -1,7 +1,8 @@
 """Gradient accuracy of the batched mixed-precision EnVar estimate against the FP64 discrete adjoint.
 
     python -m paper_2605_23812_gb300.gradient_study [--nx 512 --ny 256 --Re 7500 --spinup 20000
-                                                     --horizon 10000 --members 16,32,64 --snapshots 64]
+                                                     --horizon 10000 --members 16,32,64,128,256
+                                                     --snapshots 64 --fd-directions 16]
 
 The open cavity is first spun up from the seeded initial state (mixed precision, no forcing); the
 spun-up state is the initial state of every run below.  The cost is the DOMAIN fluctuation energy
@@ -9,12 +10,15 @@ over the whole horizon (Sec. 4.1), the forcing is zero (w = 0, the first EnVar i
 
   * reference: dJ/df by the discrete adjoint of the FP64 stepper (Sec. 3.2) with binomial
     checkpointing;
-  * EnVar: for each ensemble size N, the mixed-precision batched gradient g_i = (J_i - J_0) / eps
-    (Eq. fdapprox, Eq. gradient_EnVar at w = 0), which estimates E_i^T dJ/df.
+  * the adjoint itself against central differences of the FP64 forward model in --fd-directions
+    random control directions d_k (one FP64 batched ensemble whose members carry +h d_k and -h d_k);
+  * EnVar: for each ensemble size N, the mixed-precision batched gradient of Eq. (gradient_EnVar) at
+    w = 0, g = Y^T h_0 with Y from Eq. (fdapprox) (the explicit contraction), and for comparison the
+    scalar-anomaly form (J_i - J_0)/eps, both estimates of E^T dJ/df.
 
-Printed per N (one JSON line each): the cosine and relative L2 error between g and E^T dJ/df (the
-ensemble-space comparison: EnVar only sees the span of E), the cosine between the f-space
-directions E g / (N - 1) and dJ/df, and the times of the EnVar gradient and the adjoint.
+Printed (one JSON line each): the adjoint's FD check, then per N the cosine and relative L2 error
+between g and E^T dJ/df (the ensemble-space comparison: EnVar only sees the span of E), for both
+forms, the cosine between the f-space directions E g / (N - 1) and dJ/df, and the times.
 """
 from __future__ import annotations
 
@@ -34,7 +38,9 @@ def main():
     ap.add_argument("--Re", type=float, default=7500.0)
     ap.add_argument("--spinup", type=int, default=20000)
     ap.add_argument("--horizon", type=int, default=10000)
-    ap.add_argument("--members", default="16,32,64")
+    ap.add_argument("--members", default="16,32,64,128,256")
+    ap.add_argument("--fd-directions", type=int, default=16)
+    ap.add_argument("--fd-step", type=float, default=1e-3)
     ap.add_argument("--snapshots", type=int, default=64)
     ap.add_argument("--eps", type=float, default=1e-2)
     args = ap.parse_args()
@@ -72,6 +78,33 @@ def main():
     g_adj = g_adj.cpu().numpy()
     stats = adj.adjoint_stats()
     adj.close()
+    print(json.dumps({"adjoint": {"J": J_adj, "seconds": t_adj, "stats": stats, "snapshots": args.snapshots}}),
+          flush=True)
+
+    if args.fd_directions > 0:
+        # central differences of the same FP64 forward model along random unit directions: the
+        # members of one batched ensemble carry +h d_k (k < K) and -h d_k (k >= K), w = 0, eps = h
+        K, hstep = args.fd_directions, args.fd_step
+        rng = np.random.default_rng(2024)
+        D = rng.standard_normal((g_adj.size, K))
+        D /= np.linalg.norm(D, axis=0)
+        fd = pkg.Ensemble(pkg.default_config(nx, ny, Re=args.Re, n_steps=T, n_window=T, n_members=2 * K,
+                                             precision=pkg.FP64_BATCHED, div_tol=3e-10, max_outer=20, max_inner=30,
+                                             inner_rtol=1e-6, eps=hstep), stream=stream)
+        fd.set_initial_state(u0, v0)
+        fd.set_ensemble(np.concatenate([D, -D], axis=1))
+        t0 = time.perf_counter()
+        fd.forward_ensemble(np.zeros(2 * K))
+        torch.cuda.synchronize()
+        t_fd = time.perf_counter() - t0
+        J, _ = fd.cost()
+        cfd = (J[1:K + 1] - J[K + 1:]) / (2 * hstep)
+        adj_dir = D.T @ g_adj
+        print(json.dumps({"adjoint_fd_check": {
+            "directions": K, "h": hstep, "max_rel_err": float(np.abs(adj_dir - cfd).max() / np.abs(cfd).max()),
+            "cos": float(adj_dir @ cfd / (np.linalg.norm(adj_dir) * np.linalg.norm(cfd))),
+            "status_nonzero": int((fd.member_status() != 0).sum()), "seconds": t_fd}}), flush=True)
+        fd.close()
 
     for N in [int(x) for x in args.members.split(",")]:
         cfg = pkg.default_config(nx, ny, Re=args.Re, n_steps=T, n_window=T, n_members=N, precision=pkg.MIXED,
@@ -87,17 +120,22 @@ def main():
         g = ens.gradient()
         torch.cuda.synchronize()
         t_env = time.perf_counter() - t0
+        gs = ens.gradient_scalar()
         J, _ = ens.cost()
         proj = E.T @ g_adj
-        cos_w = float(g @ proj / (np.linalg.norm(g) * np.linalg.norm(proj)))
-        rel_w = float(np.linalg.norm(g - proj) / np.linalg.norm(proj))
+
+        def cos(a, b):
+            return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+
         df = E @ g / max(N - 1, 1)
-        cos_f = float(df @ g_adj / (np.linalg.norm(df) * np.linalg.norm(g_adj)))
         print(json.dumps({"grid": [nx, ny], "Re": args.Re, "horizon": T, "spinup": args.spinup, "N": N,
-                          "eps": args.eps, "cos_ensemble_space": cos_w, "rel_l2_ensemble_space": rel_w,
-                          "cos_control_space": cos_f, "J0_envar": float(J[0]), "J_adjoint_fp64": J_adj,
-                          "envar_gradient_s": t_env, "adjoint_s": t_adj, "adjoint_stats": stats,
-                          "solver": solver, "status_nonzero": int((ens.member_status() != 0).sum())}),
+                          "eps": args.eps, "cos_ensemble_space": cos(g, proj),
+                          "rel_l2_ensemble_space": float(np.linalg.norm(g - proj) / np.linalg.norm(proj)),
+                          "cos_ensemble_space_scalar_form": cos(gs, proj),
+                          "rel_l2_ensemble_space_scalar_form": float(np.linalg.norm(gs - proj) / np.linalg.norm(proj)),
+                          "cos_control_space": cos(df, g_adj), "J0_envar": float(J[0]), "J_adjoint_fp64": J_adj,
+                          "envar_gradient_s": t_env, "solver": solver,
+                          "status_nonzero": int((ens.member_status() != 0).sum())}),
               flush=True)
         ens.close()
 

@@ -1,0 +1,116 @@
+"""Reduced-space optimisers of Sec. 3.3.1 on the GPU against the oracle: the Gauss-Newton
+Hessian and step (Eq. Hessian_EnVar, Eq. update_Newton) and the L-BFGS iteration with its Armijo
+line search (Eq. update_BFGS), through the C ABI.
+
+The oracle builds every quantity from its own forward runs: Y from its sensor series, H_GN and the
+Gauss-Newton step by its dense Cholesky solve, the L-BFGS direction by its two-loop recursion, and
+the line search from its own member-0 cost evaluations.  FP64 handles; the sensor series of the two
+solvers agree to 1e-10, Y = (h_i - h_0)/eps amplifies that by 1/eps = 100, so H_GN and the steps are
+compared at 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2605_23812_gb300 as pkg
+from paper_2605_23812_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+NX, NY, N, RE, STEPS, WINDOW = 32, 16, 3, 300.0, 100, 50
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def handle():
+    cfg = pkg.default_config(NX, NY, Re=RE, n_steps=STEPS, n_window=WINDOW, n_members=N, precision=pkg.FP64_BATCHED,
+                             cost_mode=pkg.COST_SENSORS, div_tol=1e-12, max_outer=4, max_inner=40, inner_rtol=1e-12)
+    ens = pkg.Ensemble(cfg)
+    u0, v0 = synth.cavity_ic(NX, NY)
+    ens.set_initial_state(u0, v0)
+    P = oracle.cavity_params(NX, NY, RE)
+    E = oracle.ensemble_seeded(P, cfg.sigma, cfg.corr_len, N, cfg.seed)
+    ens.set_ensemble(E)
+    return ens, cfg, P, E, u0, v0
+
+
+def oracle_eval(P, E, u0, v0, w, eps):
+    out = oracle.envar_gradient(P, u0, v0, E, w, eps, STEPS, WINDOW, cost_mode=oracle.COST_SENSORS, nthreads=4,
+                                want_series=True)
+    g = oracle.sensor_gradient(out["series"], w, eps)
+    return out["J"][0] + out["J_prior"], g, out["series"]
+
+
+def test_gauss_newton_hessian_and_step_match_oracle():
+    ens, cfg, P, E, u0, v0 = handle()
+    w = synth.weights(N)
+    ens.forward_ensemble(w)
+    H = ens.gn_hessian()
+    Jref, gref, series = oracle_eval(P, E, u0, v0, w, cfg.eps)
+    Y, h0 = oracle.sensor_anomalies(series, cfg.eps)
+    w1_ref, H_ref, g_ref = oracle.gauss_newton_step(Y, h0, w, 0.8)
+    np.testing.assert_allclose(H, H_ref, rtol=1e-6)
+    w1, J0 = ens.gn_step(0.8, w)
+    assert J0 == pytest.approx(Jref, rel=1e-9)
+    np.testing.assert_allclose(w1, w1_ref, rtol=1e-6, atol=1e-9 * np.abs(w1_ref).max())
+    # the full step reduces the total cost of Eq. (J_w) in this near-linear regime
+    w2, _ = ens.gn_step(1.0, w)
+    ens.forward_ensemble(w2)
+    J2, jp2 = ens.cost()
+    assert J2[0] + jp2 < J0
+    ens.close()
+
+
+def test_gauss_newton_rejects_domain_cost():
+    cfg = pkg.default_config(NX, NY, n_steps=10, n_window=5, n_members=2, precision=pkg.FP64_BATCHED)
+    ens = pkg.Ensemble(cfg)
+    ens.set_initial_state(*synth.cavity_ic(NX, NY))
+    with pytest.raises(pkg.EnvarError, match="EINVAL"):
+        ens.gn_step(1.0, np.zeros(2))
+    ens.close()
+
+
+def test_lbfgs_iterations_match_oracle():
+    """Three L-BFGS iterations: the oracle replays them with its own gradients, its two-loop recursion
+    (initial matrix (s^T y / y^T y) I, or (1/(N-1)) I without pairs) and an Armijo backtracking search
+    on its own member-0 costs."""
+    ens, cfg, P, E, u0, v0 = handle()
+    w = synth.weights(N)
+    w_gpu = [w.copy()]
+    for _ in range(3):
+        wn, J0, a, ev = ens.lbfgs_step(w_gpu[-1])
+        w_gpu.append(wn)
+    ens.close()
+
+    eps = cfg.eps
+    S, Yh = [], []
+    wk, w_prev, g_prev = w.copy(), None, None
+    Js = []
+    for k in range(3):
+        Jw, g, _ = oracle_eval(P, E, u0, v0, wk, eps)
+        Js.append(Jw)
+        if w_prev is not None:
+            s, y = wk - w_prev, g - g_prev
+            if s @ y > 1e-10 * np.linalg.norm(s) * np.linalg.norm(y):
+                S.append(s)
+                Yh.append(y)
+        gamma = (S[-1] @ Yh[-1]) / (Yh[-1] @ Yh[-1]) if S else 1.0 / (N - 1)
+        p = oracle.lbfgs_direction(np.array(S).reshape(-1, N), np.array(Yh).reshape(-1, N), g, gamma)
+        assert g @ p < 0
+        a = 1.0
+        for _ in range(12):
+            wt = wk + a * p
+            fu, fv = oracle.control_to_faces(P, E @ wt)
+            Jt = oracle.member_run(P, u0, v0, STEPS, WINDOW, fu, fv)["J_sensor"] + 0.5 * (N - 1) * wt @ wt
+            if Jt <= Jw + 1e-4 * a * (g @ p):
+                break
+            a *= 0.5
+        w_prev, g_prev = wk, g
+        wk = wt
+        np.testing.assert_allclose(w_gpu[k + 1], wk, rtol=1e-6, atol=1e-9 * np.abs(wk).max())
+    # Armijo: the total cost decreases along the iterations
+    assert Js[1] < Js[0] and Js[2] < Js[1]
