@@ -140,6 +140,18 @@ int envar_set_ensemble(envar_handle h, const double *E_dev, int n_ctrl, int N);
 /* Copy the ensemble matrix out (n_ctrl x N column-major, device). */
 int envar_get_ensemble(envar_handle h, double *E_dev);
 
+/* Replace E by the eigenvector ensemble of Sec. 3.3.2: B = U Sigma U^T with U^T M_f U = I and
+ * E = U_N Sigma_N^{1/2} sqrt(N-1) (Eq. eigenvm1), B the prior covariance of Eq. (covarianceB) on the
+ * control cells (sigma_i = sigma, a_x = a_y = corr_len, c_xy = infinity).  On the uniform grid
+ * M_f = dx dy I drops out, so the members are sqrt(lambda_k (N-1)) v_k for the Euclidean eigenpairs
+ * of the one-component covariance B_s; both forcing components share B_s, and the members take its
+ * eigenvectors in decreasing eigenvalue order, each first as an fx field (member 2r) and then as an
+ * fy field (member 2r+1); each eigenvector's largest-magnitude entry is positive.  The eigenpairs
+ * come from Lanczos with full reorthogonalisation on B_s applied through its Kronecker factors
+ * (B_s is never formed) and a Jacobi diagonalisation of the projected matrix.  lambda_host
+ * (nullable): N doubles, the eigenvalue of each member.  Allocates and frees temporary device memory. */
+int envar_eigen_ensemble(envar_handle h, double *lambda_host);
+
 /* N+1 forward evaluations of Fig. (envar_loop): member 0 with forcing E w,
  * member i with E w + eps E_i (Eq. fdapprox), each over n_steps from the
  * initial state, accumulating the window cost in-kernel (Welford for DOMAIN,
@@ -277,6 +289,30 @@ int envar_apply_preconditioner(envar_handle h, const double *r_dev, double *z_de
  * wrong handle kind or argument, ENVAR_ENOMEM when the checkpoints do not fit, ENVAR_ESTATE when a
  * forward step or an adjoint solve failed (non-finite state, CFL, unconverged solve). */
 int envar_adjoint_gradient(envar_handle h, const double *f_dev, double *gf_dev, int max_snapshots, double *J_host);
+
+/* H^1 smoothing of a control-space gradient (Sec. 4.2, Eq. lsob): (I - l_sob^2 Lap) gs = (1 + l_sob^2) g
+ * for each forcing component, Lap the 5-point Laplacian on the control cells with no flux through the
+ * boundary of the control set (a neighbour outside it contributes nothing).  g_dev, gs_dev: n_ctrl
+ * doubles (device), layout of a column of E.  Conjugate gradients to 1e-13 relative residual; ENVAR_ESTATE
+ * if that is not reached. */
+int envar_h1_smooth(envar_handle h, const double *g_dev, double *gs_dev, double l_sob);
+
+/* One iteration of the adjoint approach (Sec. 3.2, the paragraph after Eq. gradient_forcing, with the
+ * regularisation of Sec. 4.2): J(f) and dJ/df by envar_adjoint_gradient (DOMAIN cost, no prior term:
+ * the deterministic statement of the problem), the L2 gradient dJ/df / (dx dy) (M_f = dx dy I on the
+ * uniform grid), its H^1 smoothing with length l_sob (Eq. lsob; the paper uses 0.02), and an L-BFGS
+ * update of f along p = -H g_H1 from the newest pairs (f - f_prev, g_H1 - g_H1_prev) (at most 8 unless
+ * envar_adjoint_lbfgs_reset set otherwise).  The step length is the first of a0, a0/2, ... (at most 12
+ * trials, each one forward run of member slot 0) that meets the Armijo condition
+ * J(f + a p) <= J(f) + 1e-4 a (dJ/df . p); a0 = 1 with curvature pairs, else the length that moves f
+ * by first_step in the max norm.  f_inout_dev: n_ctrl doubles (device, in/out).  J_out_host (nullable):
+ * J(f) before the update; alpha_out_host, evals_out_host (nullable): step length and trial runs.
+ * Needs what envar_adjoint_gradient needs.  ENVAR_ESTATE (f unchanged) if no trial met the condition. */
+int envar_adjoint_lbfgs_step(envar_handle h, double *f_inout_dev, int max_snapshots, double l_sob, double first_step,
+                             double *J_out_host, double *alpha_out_host, int *evals_out_host);
+
+/* Clear the history of envar_adjoint_lbfgs_step and set its length (1 .. 64 pairs). */
+int envar_adjoint_lbfgs_reset(envar_handle h, int memory);
 
 /* Counters of the last envar_adjoint_gradient call: forward steps run (initial sweep included),
  * reverse steps, checkpoint stores and restores. */

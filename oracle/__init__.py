@@ -550,3 +550,76 @@ def lbfgs_direction(S, Yh, g, gamma: float):
     p = np.zeros(N)
     lib().orc_lbfgs_direction(N, S.shape[0], S.reshape(-1), Yh.reshape(-1), g, float(gamma), p)
     return p
+
+
+# ----------------------------------------------------------------------------
+# eigenvector ensemble (Sec. 3.3.2, Eq. eigenvm1)
+# ----------------------------------------------------------------------------
+def covariance_B(P: Params, sigma: float, a: float, region=CAVITY_REGION):
+    """Dense prior covariance of one forcing component on the control cells, Eq. (covarianceB) with
+    sigma_i = sigma, a_x = a_y = a and c_xy = infinity: B_ij = sigma^2 exp(-dx^2/a^2 - dy^2/a^2)."""
+    ci, cj = control_cells(P, region)
+    x = P.x0 + (ci + 0.5) * P.dx
+    y = P.y0 + (cj + 0.5) * P.dy
+    d2 = (x[:, None] - x[None, :]) ** 2 + (y[:, None] - y[None, :]) ** 2
+    return sigma * sigma * np.exp(-d2 / (a * a))
+
+
+def eigen_ensemble(P: Params, sigma: float, a: float, N: int, region=CAVITY_REGION):
+    """Sec. 3.3.2: B = U Sigma U^T with U^T M_f U = I and E = U_N Sigma_N^{1/2} sqrt(N - 1)
+    (Eq. eigenvm1).  On this uniform grid M_f = dx dy I, which cancels: E = V_N Lambda_N^{1/2} sqrt(N-1)
+    with (V, Lambda) the Euclidean eigenpairs of B.  The control vector holds two independent
+    components with the same covariance, so B = diag(B_s, B_s): each eigenpair of B_s appears twice,
+    and the columns of E take the eigenvectors of B_s in decreasing eigenvalue order, each first as an
+    fx field and then as an fy field.  Each eigenvector's sign makes its largest-magnitude entry
+    positive.  Returns (E [n_ctrl x N], the N eigenvalues of B used)."""
+    Bs = covariance_B(P, sigma, a, region)
+    lam, V = np.linalg.eigh(Bs)
+    order = np.argsort(lam)[::-1]
+    lam, V = lam[order], V[:, order]
+    n = Bs.shape[0]
+    E = np.zeros((2 * n, N))
+    lams = np.zeros(N)
+    for k in range(N):
+        v = V[:, k // 2].copy()
+        j = int(np.argmax(np.abs(v)))
+        if v[j] < 0:
+            v = -v
+        comp = k % 2
+        E[comp * n:(comp + 1) * n, k] = np.sqrt(max(lam[k // 2], 0.0) * (N - 1)) * v
+        lams[k] = lam[k // 2]
+    return E, lams
+
+
+# ----------------------------------------------------------------------------
+# H^1 gradient smoothing of the adjoint approach (Sec. 4.2, Eq. lsob)
+# ----------------------------------------------------------------------------
+def control_laplacian(P: Params, region=CAVITY_REGION):
+    """5-point Laplacian on the control cells with no flux through the boundary of the control set
+    (a neighbour outside the set contributes nothing), as a scipy sparse matrix on one component."""
+    import scipy.sparse as sp
+    ci, cj = control_cells(P, region)
+    n = len(ci)
+    where = {(int(i), int(j)): q for q, (i, j) in enumerate(zip(ci, cj))}
+    rows, cols, vals = [], [], []
+    for q, (i, j) in enumerate(zip(ci, cj)):
+        for di, dj, h2 in ((1, 0, P.dx**2), (-1, 0, P.dx**2), (0, 1, P.dy**2), (0, -1, P.dy**2)):
+            r = where.get((int(i) + di, int(j) + dj))
+            if r is None:
+                continue
+            rows += [q, q]
+            cols += [r, q]
+            vals += [1.0 / h2, -1.0 / h2]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+def h1_smooth(P: Params, g, l_sob: float, region=CAVITY_REGION):
+    """Eq. (lsob): (I - l^2 Lap) g_H1 = (1 + l^2) g for each forcing component, Lap the control-set
+    Laplacian with no flux through its boundary.  g: [fx over control cells | fy over control cells]."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    L = control_laplacian(P, region)
+    n = L.shape[0]
+    A = (sp.identity(n, format="csc") - l_sob * l_sob * L).tocsc()
+    g = np.asarray(g, dtype=np.float64)
+    return np.concatenate([spla.spsolve(A, (1.0 + l_sob**2) * g[:n]), spla.spsolve(A, (1.0 + l_sob**2) * g[n:])])

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libenvar_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["k_flow.cu", "k_mixed.cu", "k_poisson.cu", "k_ensemble.cu", "k_adjoint.cu", "k_optim.cu", "envar_capi.cu",
+SOURCES = ["k_flow.cu", "k_mixed.cu", "k_poisson.cu", "k_ensemble.cu", "k_adjoint.cu", "k_optim.cu", "k_eigen.cu", "envar_capi.cu",
            "k_noalloc.cu"]
 
 

@@ -73,6 +73,10 @@ def lib():
         "envar_gradient_scalar": [H, c_void_p],
         "envar_excluded_members": [H, ctypes.POINTER(c_int)],
         "envar_gn_step": [H, c_double, c_void_p, c_void_p],
+        "envar_eigen_ensemble": [H, c_void_p],
+        "envar_h1_smooth": [H, c_void_p, c_void_p, c_double],
+        "envar_adjoint_lbfgs_step": [H, c_void_p, c_int, c_double, c_double, c_void_p, c_void_p, c_void_p],
+        "envar_adjoint_lbfgs_reset": [H, c_int],
         "envar_gn_hessian": [H, c_void_p],
         "envar_lbfgs_step": [H, c_void_p, c_void_p, c_void_p, c_void_p],
         "envar_lbfgs_reset": [H, c_int],
@@ -183,6 +187,12 @@ class Ensemble:
         Et = self._dev(E, (self.n_ctrl, self.N)).t().contiguous()   # column-major storage
         self.torch.cuda.current_stream().synchronize()
         self._check(lib().envar_set_ensemble(self._h, _ptr(Et), self.n_ctrl, self.N), "envar_set_ensemble")
+
+    def use_eigen_ensemble(self):
+        """Replace E by the eigenvector ensemble of Eq. (eigenvm1); returns the members' eigenvalues."""
+        lam = np.zeros(self.N)
+        self._check(lib().envar_eigen_ensemble(self._h, _np_ptr(lam)), "envar_eigen_ensemble")
+        return lam
 
     def get_ensemble(self):
         out = self.torch.empty((self.N, self.n_ctrl), dtype=self.torch.float64, device="cuda")
@@ -330,6 +340,27 @@ class Ensemble:
         self._check(lib().envar_adjoint_gradient(self._h, _ptr(ft), _ptr(g), int(max_snapshots), _np_ptr(J)),
                     "envar_adjoint_gradient")
         return float(J[0]), g
+
+    def h1_smooth(self, g, l_sob: float = 0.02):
+        """Eq. (lsob) on a control-space vector (array or tensor); returns a device tensor."""
+        gt = self._dev(g, (self.n_ctrl,))
+        out = self.torch.empty_like(gt)
+        self.torch.cuda.current_stream().synchronize()
+        self._check(lib().envar_h1_smooth(self._h, _ptr(gt), _ptr(out), float(l_sob)), "envar_h1_smooth")
+        return out
+
+    def adjoint_lbfgs_step(self, f_dev, max_snapshots: int = 64, l_sob: float = 0.02, first_step: float = 1e-3):
+        """One adjoint-approach iteration (updates the device tensor f_dev in place): (J(f), step, trials)."""
+        J, a = np.zeros(1), np.zeros(1)
+        n = c_int()
+        self.torch.cuda.current_stream().synchronize()
+        self._check(lib().envar_adjoint_lbfgs_step(self._h, _ptr(f_dev), int(max_snapshots), float(l_sob),
+                                                   float(first_step), _np_ptr(J), _np_ptr(a), ctypes.byref(n)),
+                    "envar_adjoint_lbfgs_step")
+        return float(J[0]), float(a[0]), n.value
+
+    def adjoint_lbfgs_reset(self, memory: int = 8):
+        self._check(lib().envar_adjoint_lbfgs_reset(self._h, int(memory)), "envar_adjoint_lbfgs_reset")
 
     def adjoint_stats(self):
         v = [ctypes.c_longlong() for _ in range(4)]

@@ -25,6 +25,16 @@ using namespace envar;
 
 constexpr int ENVAR_MAX_GROUPS = 4;
 
+// Limited-memory BFGS history in device memory (Sec. 3.3.1, Eq. update_BFGS): the newest `count`
+// of at most m pairs (s, y) in ring slots, with the previous iterate and gradient.
+struct LbfgsState {
+    int n = 0, m = 0, count = 0, head = 0;
+    bool have_prev = false;
+    double *S = nullptr, *Y = nullptr, *sy = nullptr, *q = nullptr, *a = nullptr, *p = nullptr, *gp = nullptr;
+    double *xprev = nullptr, *gprev = nullptr;
+    int *order = nullptr;
+};
+
 struct GraphSet {
     cudaGraphExec_t many = nullptr;   // steps_per_graph steps
     cudaGraphExec_t one = nullptr;    // one step
@@ -91,12 +101,12 @@ struct envar_handle_s {
     // reduced-space optimisers (allocated on first use)
     double *d_Y = nullptr, *d_h0 = nullptr, *d_smean = nullptr, *d_H = nullptr, *d_L = nullptr, *d_x = nullptr;
     int *d_info = nullptr;
-    int lb_m = 0, lb_count = 0, lb_head = 0;
-    bool lb_have_prev = false;
-    double *d_lbS = nullptr, *d_lbY = nullptr, *d_lbsy = nullptr, *d_lbq = nullptr, *d_lba = nullptr;
-    double *d_lbp = nullptr, *d_lbgp = nullptr, *d_wprev = nullptr, *d_gprev = nullptr, *d_wt = nullptr;
-    double *d_prior_t = nullptr;
-    int *d_lborder = nullptr;
+    double *d_wt = nullptr, *d_prior_t = nullptr;
+    LbfgsState lbw, lbf;                // L-BFGS histories: ensemble weights w, control vector f
+    int *d_cnb = nullptr;               // control-cell neighbours E, W, N, S (-1: none) [4][n_cc]
+    double *d_h1 = nullptr;             // H^1 smoothing work (3 n_cc) and adjoint-loop vectors
+    double *d_fg = nullptr, *d_fgs = nullptr, *d_fs = nullptr, *d_dm = nullptr;
+    int *d_h1it = nullptr;
     char err[512] = {0};
 };
 
@@ -412,6 +422,19 @@ static int build_geometry(envar_handle h)
             }
     h->ncc = (int)cidx.size();
     h->n_ctrl = 2 * h->ncc;
+    {   // control-cell neighbours (E, W, N, S) inside the control set, for the H^1 smoothing
+        std::vector<int> where((size_t)h->nrect, -1), nb((size_t)4 * std::max(h->ncc, 1), -1);
+        for (int q = 0; q < h->ncc; ++q) where[cidx[q]] = q;
+        for (int q = 0; q < h->ncc; ++q) {
+            const int r = cidx[q], a = r % h->nrx, b = r / h->nrx;
+            if (a + 1 < h->nrx) nb[q] = where[r + 1];
+            if (a > 0) nb[(size_t)h->ncc + q] = where[r - 1];
+            if (b + 1 < h->nry) nb[2 * (size_t)h->ncc + q] = where[r + h->nrx];
+            if (b > 0) nb[3 * (size_t)h->ncc + q] = where[r - h->nrx];
+        }
+        DA(h->d_cnb, nb.size());
+        CK(cudaMemcpy(h->d_cnb, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice));
+    }
     DA(h->d_cidx, std::max(h->ncc, 1));
     DA(h->d_rect_ctrl, h->nrect);
     CK(cudaMemcpy(h->d_cidx, cidx.data(), sizeof(int) * h->ncc, cudaMemcpyHostToDevice));
@@ -955,6 +978,37 @@ extern "C" int envar_get_ensemble(envar_handle h, double *E)
     return ENVAR_OK;
 }
 
+extern "C" int envar_eigen_ensemble(envar_handle h, double *lambda_host)
+{
+    if (!h) return ENVAR_EINVAL;
+    const int N = h->N;
+    if (N < 1) { set_err(h, "envar_eigen_ensemble: ensemble is empty"); return ENVAR_EINVAL; }
+    const int k = (N + 1) / 2;
+    if (k > h->ncc) { set_err(h, "envar_eigen_ensemble: %d eigenvectors requested, %d control cells", k, h->ncc); return ENVAR_EINVAL; }
+    int m = std::min(h->ncc, std::max(2 * k + 40, 64));
+    if (m % 2) --m;
+    if (m < k) m = k + (k % 2);
+    const size_t nd = eigen_work_doubles(h->nrx, h->nry, h->ncc, m, k);
+    void *work = nullptr;
+    cudaError_t e = cudaMalloc(&work, sizeof(double) * nd);
+    if (e != cudaSuccess) { set_err(h, "envar_eigen_ensemble: %zu bytes of work space: %s", sizeof(double) * nd, cudaGetErrorString(e)); return ENVAR_ENOMEM; }
+    std::vector<double> lam((size_t)k);
+    int sweeps = 0;
+    int rc = eigen_ensemble(h->nrx, h->nry, h->g.dx, h->g.dy, h->cfg.corr_len, h->cfg.sigma, h->ncc, h->d_cidx, N, m,
+                            h->cfg.seed, (double *)work, h->d_E, lam.data(), &sweeps, h->st);
+    if (!rc) launch_compact_to_rect(N, h->nrect, h->ncc, h->d_cidx, h->d_E, h->d_Erect, h->st);
+    e = cudaStreamSynchronize(h->st);
+    cudaFree(work);
+    if (rc) { set_err(h, "envar_eigen_ensemble: bad Lanczos size"); return ENVAR_EINVAL; }
+    if (e != cudaSuccess) { set_err(h, "envar_eigen_ensemble: %s", cudaGetErrorString(e)); return ENVAR_ECUDA; }
+    CK(cudaGetLastError());
+    if (sweeps >= 60) { set_err(h, "envar_eigen_ensemble: Jacobi did not converge"); return ENVAR_ESTATE; }
+    if (lambda_host)
+        for (int i = 0; i < N; ++i) lambda_host[i] = lam[(size_t)(i / 2)];
+    h->have_forward = false;
+    return ENVAR_OK;
+}
+
 extern "C" int envar_forward_ensemble(envar_handle h, const double *w)
 {
     if (!h) return ENVAR_EINVAL;
@@ -1165,24 +1219,57 @@ extern "C" int envar_gn_step(envar_handle h, double alpha, double *w_inout, doub
     return ENVAR_OK;
 }
 
+static int lb_setup(envar_handle h, LbfgsState &L, int n, int m)
+{
+    if (L.m != m || L.n != n) {
+        DA(L.S, (size_t)m * n); DA(L.Y, (size_t)m * n); DA(L.sy, 2 * m); DA(L.a, m); DA(L.order, m);
+        DA(L.q, n); DA(L.p, n); DA(L.gp, 1); DA(L.xprev, n); DA(L.gprev, n);
+        L.m = m;
+        L.n = n;
+    }
+    L.count = 0;
+    L.head = 0;
+    L.have_prev = false;
+    return ENVAR_OK;
+}
+
+// The pair (x - x_prev, g - g_prev) joins the history when its curvature s^T y is positive.
+static int lb_update(envar_handle h, LbfgsState &L, const double *x, const double *g)
+{
+    if (!L.have_prev) return ENVAR_OK;
+    const int slot = L.head;
+    launch_lbfgs_pair(L.n, x, L.xprev, g, L.gprev, slot, L.S, L.Y, L.sy, L.m, h->st);
+    double sy[2] = {0.0, 0.0};
+    CK(cudaMemcpyAsync(&sy[0], L.sy + slot, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&sy[1], L.sy + L.m + slot, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (sy[0] > 1e-10 * std::sqrt(sy[1])) {
+        L.head = (L.head + 1) % L.m;
+        L.count = std::min(L.count + 1, L.m);
+    }
+    return ENVAR_OK;
+}
+
+// p = -H g by the two-loop recursion (initial matrix (s^T y / y^T y) I, or gamma0 I without pairs);
+// *gp_host = g^T p.  Then x_prev, g_prev <- x, g.
+static int lb_direction(envar_handle h, LbfgsState &L, const double *x, const double *g, double gamma0, double *gp_host)
+{
+    std::vector<int> order((size_t)L.count);
+    for (int r = 0; r < L.count; ++r) order[r] = (L.head - L.count + r + L.m) % L.m;
+    if (L.count) CK(cudaMemcpyAsync(L.order, order.data(), sizeof(int) * L.count, cudaMemcpyHostToDevice, h->st));
+    launch_lbfgs_direction(L.n, L.count, L.order, L.S, L.Y, g, gamma0, L.q, L.a, L.p, L.gp, h->st);
+    CK(cudaMemcpyAsync(L.xprev, x, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(L.gprev, g, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(gp_host, L.gp, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return ENVAR_OK;
+}
+
 extern "C" int envar_lbfgs_reset(envar_handle h, int memory)
 {
     if (!h || memory < 1 || memory > 64 || h->N < 1) return ENVAR_EINVAL;
-    if (h->lb_m != memory) {
-        const int N = h->N;
-        DA(h->d_lbS, (size_t)memory * N); DA(h->d_lbY, (size_t)memory * N); DA(h->d_lbsy, 2 * memory);
-        DA(h->d_lba, memory); DA(h->d_lborder, memory);
-        if (!h->d_lbq) {
-            DA(h->d_lbq, N); DA(h->d_lbp, N); DA(h->d_lbgp, 1); DA(h->d_wprev, N); DA(h->d_gprev, N);
-            DA(h->d_prior_t, 1);
-            if (!h->d_wt) DA(h->d_wt, N);
-        }
-        h->lb_m = memory;
-    }
-    h->lb_count = 0;
-    h->lb_head = 0;
-    h->lb_have_prev = false;
-    return ENVAR_OK;
+    if (!h->d_prior_t) DA(h->d_prior_t, 1);
+    return lb_setup(h, h->lbw, h->N, memory);
 }
 
 // J(w_t) = J_obs of member 0 alone with forcing E w_t, plus the prior (N-1)/2 w_t^T w_t (Eq. J_w).
@@ -1210,60 +1297,40 @@ extern "C" int envar_lbfgs_step(envar_handle h, double *w_inout, double *J0_out,
     if (!h->have_ic) { set_err(h, "envar_lbfgs_step: no initial state"); return ENVAR_ESTATE; }
     if (h->N < 1) { set_err(h, "envar_lbfgs_step: ensemble is empty"); return ENVAR_ESTATE; }
     int rc = 0;
-    if (h->lb_m == 0 && (rc = envar_lbfgs_reset(h, 8))) return rc;
-    const int N = h->N, m = h->lb_m;
+    if (h->lbw.m == 0 && (rc = envar_lbfgs_reset(h, 8))) return rc;
+    LbfgsState &L = h->lbw;
+    const int N = h->N;
     CK(cudaMemcpyAsync(h->d_w, w_inout, sizeof(double) * N, cudaMemcpyHostToDevice, h->st));
     if ((rc = forward_members(h))) return rc;
     if ((rc = check_member0(h, "envar_lbfgs_step"))) return rc;
     compute_gradient(h);
-    // curvature pair from the previous iteration
-    if (h->lb_have_prev) {
-        const int slot = h->lb_head;
-        launch_lbfgs_pair(N, h->d_w, h->d_wprev, h->d_g, h->d_gprev, slot, h->d_lbS, h->d_lbY, h->d_lbsy, m, h->st);
-        double sy[2] = {0.0, 0.0};
-        CK(cudaMemcpyAsync(&sy[0], h->d_lbsy + slot, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-        CK(cudaMemcpyAsync(&sy[1], h->d_lbsy + m + slot, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-        CK(cudaStreamSynchronize(h->st));
-        if (sy[0] > 1e-10 * std::sqrt(sy[1])) {   // keep only pairs of positive curvature
-            h->lb_head = (h->lb_head + 1) % m;
-            h->lb_count = std::min(h->lb_count + 1, m);
-        }
-    }
-    std::vector<int> order((size_t)h->lb_count);
-    for (int r = 0; r < h->lb_count; ++r) order[r] = (h->lb_head - h->lb_count + r + m) % m;
-    if (h->lb_count) CK(cudaMemcpyAsync(h->d_lborder, order.data(), sizeof(int) * h->lb_count, cudaMemcpyHostToDevice,
-                                        h->st));
+    if ((rc = lb_update(h, L, h->d_w, h->d_g))) return rc;
     const double gamma0 = 1.0 / std::max(N - 1, 1);   // inverse of the prior Hessian (N-1) I
-    launch_lbfgs_direction(N, h->lb_count, h->d_lborder, h->d_lbS, h->d_lbY, h->d_g, gamma0, h->d_lbq, h->d_lba,
-                           h->d_lbp, h->d_lbgp, h->st);
-    CK(cudaMemcpyAsync(h->d_wprev, h->d_w, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(h->d_gprev, h->d_g, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->st));
-    const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js : h->d_Jd;
-    double J0 = 0.0, jp = 0.0, gp = 0.0;
-    CK(cudaMemcpyAsync(&J0, src, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(&jp, h->d_jprior, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(&gp, h->d_lbgp, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    const double Jw = J0 + jp;
+    double gp = 0.0;
+    if ((rc = lb_direction(h, L, h->d_w, h->d_g, gamma0, &gp))) return rc;
     if (!(gp < 0.0)) {
         // not a descent direction: drop the history and take the prior-preconditioned gradient step
-        h->lb_count = 0;
-        launch_lbfgs_direction(N, 0, h->d_lborder, h->d_lbS, h->d_lbY, h->d_g, gamma0, h->d_lbq, h->d_lba, h->d_lbp,
-                               h->d_lbgp, h->st);
-        CK(cudaMemcpyAsync(&gp, h->d_lbgp, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-        CK(cudaStreamSynchronize(h->st));
+        L.count = 0;
+        if ((rc = lb_direction(h, L, h->d_w, h->d_g, gamma0, &gp))) return rc;
     }
+    const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js : h->d_Jd;
+    double J0 = 0.0, jp = 0.0;
+    CK(cudaMemcpyAsync(&J0, src, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&jp, h->d_jprior, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const double Jw = J0 + jp;
     // Armijo backtracking: J(w + a p) <= J(w) + c1 a g^T p, a = 1, 1/2, ...
     const double c1 = 1e-4;
     double a = 1.0, Jt = 0.0;
     int evals = 0;
     bool ok = false;
-    for (int k = 0; k < 12 && !ok; ++k, a *= 0.5) {
-        launch_trial_point(N, h->d_w, h->d_lbp, a, h->d_wt, h->d_prior_t, h->st);
+    for (int k = 0; k < 12; ++k) {
+        launch_trial_point(N, h->d_w, L.p, a, h->d_wt, h->d_prior_t, h->st);
         if ((rc = trial_cost(h, h->d_wt, &Jt))) return rc;
         ++evals;
         ok = Jt <= Jw + c1 * a * gp;
         if (ok) break;
+        a *= 0.5;
     }
     h->have_forward = false;   // slot 0 now holds the last trial run
     h->last_member_slot0 = -2;
@@ -1271,14 +1338,119 @@ extern "C" int envar_lbfgs_step(envar_handle h, double *w_inout, double *J0_out,
     if (J0_out) *J0_out = Jw;
     if (!ok) {
         set_err(h, "envar_lbfgs_step: no step length met the Armijo condition (g^T p = %g)", gp);
-        h->lb_have_prev = false;
+        L.have_prev = false;
         return ENVAR_ESTATE;
     }
     CK(cudaMemcpyAsync(h->d_w, h->d_wt, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(w_inout, h->d_wt, sizeof(double) * N, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
-    h->lb_have_prev = true;
+    L.have_prev = true;
+    if (alpha_out) *alpha_out = a;
+    return ENVAR_OK;
+}
+
+// ------------------------------------------------------------------------------------ adjoint loop
+// Sec. 3.2 (the paragraph after Eq. gradient_forcing) with the H^1 regularisation of Sec. 4.2.
+
+extern "C" int envar_h1_smooth(envar_handle h, const double *g_dev, double *gs_dev, double l_sob)
+{
+    if (!h || !g_dev || !gs_dev || !(l_sob >= 0.0)) return ENVAR_EINVAL;
+    const int n = h->ncc;
+    if (!h->d_h1) { DA(h->d_h1, 3 * (size_t)n); DA(h->d_h1it, 2); }
+    for (int comp = 0; comp < 2; ++comp)
+        launch_h1_cg(n, h->d_cnb, h->g.dx, h->g.dy, l_sob, g_dev + (size_t)comp * n, gs_dev + (size_t)comp * n, h->d_h1,
+                     1e-13, 4 * n + 100, h->d_h1it + comp, h->st);
+    int it[2] = {0, 0};
+    CK(cudaMemcpyAsync(it, h->d_h1it, sizeof(int) * 2, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    if (it[0] < 0 || it[1] < 0) { set_err(h, "envar_h1_smooth: CG did not converge"); return ENVAR_ESTATE; }
+    return ENVAR_OK;
+}
+
+// J_obs of one forward run of member slot 0 with control forcing f (device) into *J (host).
+static int control_cost(envar_handle h, const double *f, double *J)
+{
+    launch_compact_to_rect(1, h->nrect, h->ncc, h->d_cidx, f, h->d_frect, h->st);
+    if (h->mixed) launch_d2f(2 * (long long)h->nrect, h->d_frect, h->ms.frect, h->st);
+    reset_members(h, 1);
+    int rc = run_steps(h, 1, h->cfg.n_steps);
+    if (rc) return rc;
+    enqueue_cost(h, 1, h->d_Jd_slot, h->d_Js_slot, h->d_Yd_slot);
+    const double *src = (h->cfg.cost_mode == ENVAR_COST_SENSORS) ? h->d_Js_slot : h->d_Jd_slot;
+    MemberCtl c0{};
+    CK(cudaMemcpyAsync(J, src, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&c0, h->d_ctl, sizeof(MemberCtl), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    h->last_member_slot0 = -2;
+    if (c0.status) *J = HUGE_VAL;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_adjoint_lbfgs_reset(envar_handle h, int memory)
+{
+    if (!h || memory < 1 || memory > 64) return ENVAR_EINVAL;
+    return lb_setup(h, h->lbf, h->n_ctrl, memory);
+}
+
+extern "C" int envar_adjoint_lbfgs_step(envar_handle h, double *f_inout, int max_snapshots, double l_sob,
+                                        double first_step, double *J_out, double *alpha_out, int *evals_out)
+{
+    if (!h || !f_inout || !(l_sob >= 0.0) || !(first_step > 0.0)) return ENVAR_EINVAL;
+    int rc = 0;
+    if (h->lbf.m == 0 && (rc = envar_adjoint_lbfgs_reset(h, 8))) return rc;
+    LbfgsState &L = h->lbf;
+    const int n = h->n_ctrl;
+    if (!h->d_fg) { DA(h->d_fg, n); DA(h->d_fgs, n); DA(h->d_fs, n); DA(h->d_dm, 2); }
+    // J and dJ/df by the discrete adjoint, the L2 gradient (M_f = dx dy I) and its H^1 smoothing
+    double J = 0.0;
+    if ((rc = envar_adjoint_gradient(h, f_inout, h->d_fg, max_snapshots, &J))) return rc;
+    launch_scale_vec(n, 1.0 / h->g.hxy, h->d_fg, h->d_fs, h->st);
+    if ((rc = envar_h1_smooth(h, h->d_fs, h->d_fgs, l_sob))) return rc;
+    if ((rc = lb_update(h, L, f_inout, h->d_fgs))) return rc;
+    double gp = 0.0, dm[2] = {0.0, 0.0};
+    if ((rc = lb_direction(h, L, f_inout, h->d_fgs, 1.0, &gp))) return rc;
+    // the Armijo slope is the directional derivative of J itself: dJ/df . p
+    launch_dot_max(n, h->d_fg, L.p, h->d_dm, h->st);
+    CK(cudaMemcpyAsync(dm, h->d_dm, sizeof(double) * 2, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (!(dm[0] < 0.0)) {
+        L.count = 0;
+        if ((rc = lb_direction(h, L, f_inout, h->d_fgs, 1.0, &gp))) return rc;
+        launch_dot_max(n, h->d_fg, L.p, h->d_dm, h->st);
+        CK(cudaMemcpyAsync(dm, h->d_dm, sizeof(double) * 2, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+    }
+    // without curvature pairs the smoothed gradient carries no step length: the first trial moves
+    // the control by first_step in the max norm
+    double a = (L.count == 0 && dm[1] > 0.0) ? first_step / dm[1] : 1.0;
+    const double c1 = 1e-4;
+    double Jt = 0.0;
+    int evals = 0;
+    bool ok = false;
+    for (int k = 0; k < 12; ++k) {
+        // f_t = f + a p into d_fs
+        CK(cudaMemcpyAsync(h->d_fs, f_inout, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+        launch_axpy_vec(n, a, L.p, h->d_fs, h->st);
+        if ((rc = control_cost(h, h->d_fs, &Jt))) return rc;
+        ++evals;
+        ok = Jt <= J + c1 * a * dm[0];
+        if (ok) break;
+        a *= 0.5;
+    }
+    h->have_forward = false;
+    if (evals_out) *evals_out = evals;
+    if (J_out) *J_out = J;
+    if (!ok) {
+        set_err(h, "envar_adjoint_lbfgs_step: no step length met the Armijo condition");
+        L.have_prev = false;
+        return ENVAR_ESTATE;
+    }
+    CK(cudaMemcpyAsync(f_inout, h->d_fs, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    L.have_prev = true;
     if (alpha_out) *alpha_out = a;
     return ENVAR_OK;
 }

@@ -350,5 +350,16 @@ void launch_lbfgs_pair(int N, const double *w, const double *wp, const double *g
 void launch_lbfgs_direction(int N, int count, const int *order, const double *S, const double *Yh, const double *g,
                             double gamma0, double *q, double *alpha, double *p, double *gp, cudaStream_t st);
 void launch_trial_point(int N, const double *w, const double *p, double a, double *wt, double *prior, cudaStream_t st);
+void launch_h1_cg(int n, const int *nb, double dx, double dy, double l_sob, const double *g, double *x, double *work,
+                  double rtol, int max_it, int *iters, cudaStream_t st);
+void launch_scale_vec(long long n, double a, const double *x, double *y, cudaStream_t st);
+void launch_axpy_vec(long long n, double a, const double *x, double *y, cudaStream_t st);
+void launch_dot_max(long long n, const double *a, const double *b, double *out, cudaStream_t st);
+
+// Eigenvector ensemble (k_eigen.cu)
+size_t eigen_work_doubles(int nrx, int nry, int ncc, int m, int k);
+int eigen_ensemble(int nrx, int nry, double dx, double dy, double a, double sigma, int ncc, const int *cidx, int N,
+                   int m, unsigned long long seed, double *work, double *E, double *lam_host, int *sweeps_host,
+                   cudaStream_t st);
 
 } // namespace envar

@@ -1,10 +1,14 @@
-// k_optim.cu -- reduced-space optimisers of Sec. 3.3.1 on the device: the Gauss-Newton Hessian
-// H_GN = Y^T R^{-1} Y + (N-1) I (Eq. Hessian_EnVar, R = I) from the sensor-space observation
-// anomalies of Eq. (fdapprox), its Cholesky solve for the step dw = -H_GN^{-1} g (Eq. update_Newton),
-// and the two-loop recursion of the limited-memory BFGS direction (Eq. update_BFGS).
+// k_optim.cu -- optimisers on the device: the Gauss-Newton Hessian H_GN = Y^T R^{-1} Y + (N-1) I of
+// Sec. 3.3.1 (Eq. Hessian_EnVar, R = I) from the sensor-space observation anomalies of Eq. (fdapprox),
+// its Cholesky solve for the step dw = -H_GN^{-1} g (Eq. update_Newton), the two-loop recursion of
+// the limited-memory BFGS direction (Eq. update_BFGS; in the ensemble weights w or, for the adjoint
+// approach of Sec. 3.2, in the control vector f), and the H^1 smoothing of the adjoint gradient of
+// Sec. 4.2 (Eq. lsob).
 //
-// Sizes: N <= 256 perturbations, n_obs = 8 n_window sensor observations.  All of it is small next
-// to one forward run; each kernel is one launch with no host round trip.
+// Sizes: N <= 256 perturbations, n_obs = 8 n_window sensor observations, n_ctrl <= 2 x 46 082
+// control values.  All of it is small next to one forward run; each kernel is one launch.
+#include <algorithm>
+
 #include "envar_internal.cuh"
 
 namespace envar {
@@ -251,6 +255,126 @@ __global__ void k_trial_point(int N, const double *__restrict__ w, const double 
 void launch_trial_point(int N, const double *w, const double *p, double a, double *wt, double *prior, cudaStream_t st)
 {
     k_trial_point<<<1, 256, 0, st>>>(N, w, p, a, wt, prior);
+    count_launches(1);
+}
+
+} // namespace envar
+
+namespace envar {
+
+// ------------------------------------------------------------------------------ H^1 smoothing
+// Eq. (lsob): (I - l^2 Lap) x = (1 + l^2) g on the n control cells of one forcing component, Lap
+// the 5-point Laplacian with no flux through the boundary of the control set (nb[4][n]: the E, W,
+// N, S neighbour control cell or -1).  Conjugate gradients in one block (the operator is SPD, with
+// condition number at most 1 + 8 l^2 / h^2), until |r| <= rtol |b| or max_it iterations; *iters
+// receives the iterations, negative if the tolerance was not met.
+__device__ __forceinline__ double h1_apply(int q, const double *__restrict__ x, const int *__restrict__ nb, int n,
+                                           double cxl, double cyl)
+{
+    const double xq = x[q];
+    double lap = 0.0;
+    const int e = nb[q], w = nb[n + q], no = nb[2 * n + q], so = nb[3 * n + q];
+    if (e >= 0) lap += cxl * (x[e] - xq);
+    if (w >= 0) lap += cxl * (x[w] - xq);
+    if (no >= 0) lap += cyl * (x[no] - xq);
+    if (so >= 0) lap += cyl * (x[so] - xq);
+    return xq - lap;
+}
+
+__global__ void __launch_bounds__(1024) k_h1_cg(int n, const int *__restrict__ nb, double cxl, double cyl, double scale,
+                                                const double *__restrict__ g, double *__restrict__ x,
+                                                double *__restrict__ r, double *__restrict__ p, double *__restrict__ Ap,
+                                                double rtol, int max_it, int *iters)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double bb = 0.0;
+    for (int q = tid; q < n; q += nt) {
+        const double b = scale * g[q];
+        x[q] = 0.0;
+        r[q] = b;
+        p[q] = b;
+        bb += b * b;
+    }
+    bb = block_reduce(bb, false);
+    double rr = bb;
+    int it = 0;
+    bool done = !(bb > 0.0);
+    while (!done && it < max_it) {
+        double pAp = 0.0;
+        for (int q = tid; q < n; q += nt) {
+            const double a = h1_apply(q, p, nb, n, cxl, cyl);
+            Ap[q] = a;
+            pAp += p[q] * a;
+        }
+        pAp = block_reduce(pAp, false);
+        const double alpha = rr / pAp;
+        double rr1 = 0.0;
+        for (int q = tid; q < n; q += nt) {
+            x[q] += alpha * p[q];
+            r[q] -= alpha * Ap[q];
+            rr1 += r[q] * r[q];
+        }
+        rr1 = block_reduce(rr1, false);
+        ++it;
+        done = rr1 <= rtol * rtol * bb;
+        const double beta = rr1 / rr;
+        rr = rr1;
+        if (!done)
+            for (int q = tid; q < n; q += nt) p[q] = r[q] + beta * p[q];
+        __syncthreads();
+    }
+    if (tid == 0) *iters = done ? it : -it;
+}
+
+void launch_h1_cg(int n, const int *nb, double dx, double dy, double l_sob, const double *g, double *x, double *work,
+                  double rtol, int max_it, int *iters, cudaStream_t st)
+{
+    const double l2 = l_sob * l_sob;
+    k_h1_cg<<<1, 1024, 0, st>>>(n, nb, l2 / (dx * dx), l2 / (dy * dy), 1.0 + l2, g, x, work, work + n, work + 2 * n,
+                               rtol, max_it, iters);
+    count_launches(1);
+}
+
+// y = a x (elementwise scale), and the directional derivative d = g^T p of two n-vectors.
+__global__ void k_scale_vec(long long n, double a, const double *__restrict__ x, double *__restrict__ y)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = a * x[i];
+}
+void launch_scale_vec(long long n, double a, const double *x, double *y, cudaStream_t st)
+{
+    const int grid = (int)std::min<long long>((n + 255) / 256, 1024);
+    k_scale_vec<<<grid, 256, 0, st>>>(n, a, x, y);
+    count_launches(1);
+}
+
+// y += a x
+__global__ void k_axpy_vec(long long n, double a, const double *__restrict__ x, double *__restrict__ y)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+void launch_axpy_vec(long long n, double a, const double *x, double *y, cudaStream_t st)
+{
+    const int grid = (int)std::min<long long>((n + 255) / 256, 1024);
+    k_axpy_vec<<<grid, 256, 0, st>>>(n, a, x, y);
+    count_launches(1);
+}
+
+__global__ void k_dot_max(long long n, const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ out)
+{
+    double d = 0.0, m = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        d += a[i] * b[i];
+        m = fmax(m, fabs(b[i]));
+    }
+    d = block_reduce(d, false);
+    m = block_reduce(m, true);
+    if (threadIdx.x == 0) { out[0] = d; out[1] = m; }
+}
+void launch_dot_max(long long n, const double *a, const double *b, double *out, cudaStream_t st)
+{
+    k_dot_max<<<1, 1024, 0, st>>>(n, a, b, out);
     count_launches(1);
 }
 

@@ -679,6 +679,90 @@ def test_envar_step_update_and_total_cost():
 
 
 # --------------------------------------------------------------------------
+# Eigenvector ensemble (Sec. 3.3.2, Eq. eigenvm1)
+# --------------------------------------------------------------------------
+def test_eigen_ensemble_separable_rectangle_reduces_to_1d_kernels():
+    """A control region entirely in the open channel (no mask): B_s = sigma^2 K_x (x) K_y, so its
+    eigenvalues are sigma^2 times products of the 1-D kernels' eigenvalues and its leading eigenvector
+    is the Kronecker product of the 1-D leading eigenvectors (1-D kernels from the formula, 1-D
+    eigenpairs from the library routine)."""
+    P = oracle.cavity_params(64, 32, 1000.0)
+    region = (-1.0, -0.4, 0.1, 0.5)
+    sigma, a, N = 0.1, 0.1, 6
+    E, lam = oracle.eigen_ensemble(P, sigma, a, N, region)
+    ia, ib, ja, jb = oracle.control_rect(P, region)
+    x = P.x0 + (np.arange(ia, ib + 1) + 0.5) * P.dx
+    y = P.y0 + (np.arange(ja, jb + 1) + 0.5) * P.dy
+    lx, Vx = np.linalg.eigh(np.exp(-(x[:, None] - x[None, :]) ** 2 / a**2))
+    ly, Vy = np.linalg.eigh(np.exp(-(y[:, None] - y[None, :]) ** 2 / a**2))
+    prods = np.sort(np.outer(ly, lx).ravel())[::-1] * sigma**2
+    np.testing.assert_allclose(lam[::2], prods[:N // 2], rtol=1e-10)
+    v1 = np.kron(Vy[:, -1], Vx[:, -1])            # row-major cells: y outer, x inner
+    e1 = E[: len(v1), 0] / np.linalg.norm(E[: len(v1), 0])
+    assert abs(abs(e1 @ v1) - 1.0) < 1e-10
+
+
+def test_eigen_ensemble_invariants_on_the_cavity_region():
+    """Eigen-equation residual against Eq. (covarianceB) evaluated here, orthogonality of the members,
+    the scaling of Eq. (eigenvm1), and E E^T/(N-1) as the best rank-N approximation of B (its
+    spectral-norm error is the next eigenvalue)."""
+    P = oracle.cavity_params(64, 32, 1000.0)
+    sigma, a, N = 0.1, 0.05, 8
+    E, lam = oracle.eigen_ensemble(P, sigma, a, N)
+    ci, cj = oracle.control_cells(P)
+    xs, ys = P.x0 + (ci + 0.5) * P.dx, P.y0 + (cj + 0.5) * P.dy
+    Bs = sigma**2 * np.exp(-((xs[:, None] - xs[None, :]) ** 2 + (ys[:, None] - ys[None, :]) ** 2) / a**2)
+    n = len(ci)
+    for k in range(N):
+        comp = k % 2
+        v = E[comp * n:(comp + 1) * n, k]
+        assert np.all(E[(1 - comp) * n:(2 - comp) * n, k] == 0.0)
+        assert np.linalg.norm(Bs @ v - lam[k] * v) <= 1e-10 * lam[0] * np.linalg.norm(v)
+        assert np.linalg.norm(v) ** 2 == pytest.approx(lam[k] * (N - 1), rel=1e-12)
+    G = E.T @ E
+    assert np.abs(G - np.diag(np.diag(G))).max() <= 1e-12 * np.abs(G).max()
+    assert np.all(np.diff(lam[::2]) <= 0)
+    lam_all = np.sort(np.linalg.eigvalsh(Bs))[::-1]
+    err = np.linalg.norm(Bs - E[:n, ::2] @ E[:n, ::2].T / (N - 1), 2)
+    assert err == pytest.approx(lam_all[N // 2], rel=1e-8)
+
+
+# --------------------------------------------------------------------------
+# H^1 smoothing of the adjoint gradient (Sec. 4.2, Eq. lsob)
+# --------------------------------------------------------------------------
+def test_h1_smoothing_closed_forms():
+    """On a control set that is a full rectangle, the no-flux Laplacian has the cosine eigenvectors
+    cos(pi k (x - x_a)/L_x) cos(pi l (y - y_a)/L_y) sampled at the cell centres with eigenvalues
+    -(4/dx^2) sin^2(pi k dx/(2 L_x)) - (4/dy^2) sin^2(pi l dy/(2 L_y)), so Eq. (lsob) scales such a
+    mode by (1 + l^2)/(1 + l^2 |lambda|); a constant is scaled by 1 + l^2."""
+    P = oracle.cavity_params(64, 32, 1000.0)
+    region = (-1.0, -0.4, 0.1, 0.5)
+    ci, cj = oracle.control_cells(P, region)
+    ia, ib, ja, jb = oracle.control_rect(P, region)
+    Lx, Ly = (ib - ia + 1) * P.dx, (jb - ja + 1) * P.dy
+    xr, yr = (ci - ia + 0.5) * P.dx, (cj - ja + 0.5) * P.dy
+    l = 0.02
+    for k, m in ((0, 0), (1, 0), (2, 3)):
+        mode = np.cos(np.pi * k * xr / Lx) * np.cos(np.pi * m * yr / Ly)
+        lam = (4 / P.dx**2) * np.sin(np.pi * k * P.dx / (2 * Lx)) ** 2 + (4 / P.dy**2) * np.sin(np.pi * m * P.dy / (2 * Ly)) ** 2
+        g = np.concatenate([mode, -2.0 * mode])
+        gs = oracle.h1_smooth(P, g, l, region)
+        np.testing.assert_allclose(gs, g * (1 + l * l) / (1 + l * l * lam), rtol=1e-10, atol=1e-12)
+
+
+def test_h1_smoothing_operator_is_symmetric_and_smoothing():
+    P = oracle.cavity_params(64, 32, 1000.0)
+    n = len(oracle.control_cells(P)[0])
+    rng = np.random.default_rng(8)
+    a, b = rng.standard_normal(2 * n), rng.standard_normal(2 * n)
+    Sa, Sb = oracle.h1_smooth(P, a, 0.02), oracle.h1_smooth(P, b, 0.02)
+    assert abs(Sa @ b - a @ Sb) <= 1e-12 * np.linalg.norm(Sa) * np.linalg.norm(b)
+    assert a @ Sa > 0
+    # a rough field loses energy to the filter, a smooth one keeps it
+    assert np.linalg.norm(Sa) < np.linalg.norm(a)
+
+
+# --------------------------------------------------------------------------
 # Reduced-space optimisers (Sec. 3.3.1, Eq. Hessian_EnVar, update_Newton, update_BFGS).
 # --------------------------------------------------------------------------
 def test_gauss_newton_is_exact_in_one_step_for_linear_dynamics():
