@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define ENVAR_ABI_VERSION 2
+#define ENVAR_ABI_VERSION 3
 
 enum {
     ENVAR_OK = 0,
@@ -106,6 +106,13 @@ typedef struct envar_config {
     int member_groups;       /* batched runs: member groups whose time steps run as concurrent
                                 branches of the captured graph; 0 = automatic (4 from 24 member
                                 slots, 2 from 8), 1 .. 4 */
+    int lip_slip;            /* 1: the lower wall of the channel (y = 0) is free slip outside
+                                noslip_span and no slip inside it (the slip segments of Sec. 4.4);
+                                0: no slip everywhere */
+    double noslip_span[2];   /* x range of the no-slip part of the lower wall (default -0.4, 1.75) */
+    int forcing_y_only;      /* 1: forcing in the y-momentum equation only (Sec. 4.1): the prior
+                                variance of the fx entries is zero, so the drawn or eigenvector
+                                ensemble has zero fx rows */
 } envar_config;
 
 typedef struct envar_handle_s *envar_handle;
@@ -146,7 +153,8 @@ int envar_get_ensemble(envar_handle h, double *E_dev);
  * M_f = dx dy I drops out, so the members are sqrt(lambda_k (N-1)) v_k for the Euclidean eigenpairs
  * of the one-component covariance B_s; both forcing components share B_s, and the members take its
  * eigenvectors in decreasing eigenvalue order, each first as an fx field (member 2r) and then as an
- * fy field (member 2r+1); each eigenvector's largest-magnitude entry is positive.  The eigenpairs
+ * fy field (member 2r+1), or, with forcing_y_only, only as fy fields (member r); each eigenvector's
+ * largest-magnitude entry is positive.  The eigenpairs
  * come from Lanczos with full reorthogonalisation on B_s applied through its Kronecker factors
  * (B_s is never formed) and a Jacobi diagonalisation of the projected matrix.  lambda_host
  * (nullable): N doubles, the eigenvalue of each member.  Allocates and frees temporary device memory. */

@@ -47,6 +47,7 @@ class Params(ctypes.Structure):
         ("inlet_delta", c_double), ("conv_speed", c_double),
         ("cg_rtol", c_double), ("cg_maxit", c_int),
         ("ch_lo", c_double), ("ch_hi", c_double),
+        ("lip_slip", c_int), ("slip_lo", c_double), ("slip_hi", c_double),
     ]
 
     @property
@@ -171,21 +172,24 @@ class planted_mistake:
 # parameter helpers
 # ----------------------------------------------------------------------------
 def cavity_params(nx: int, ny: int, Re: float, cfl: float = 0.3, box=CAVITY_BOX,
-                  cg_rtol: float = 1e-13, cg_maxit: int = 100000, advection: int = 1) -> Params:
+                  cg_rtol: float = 1e-13, cg_maxit: int = 100000, advection: int = 1, inlet_delta: float = 0.1,
+                  lip_slip: int = 0, noslip_span=(-0.4, 1.75)) -> Params:
     """Open-cavity workload: box [-1.2,2.5]x[-1,1], cavity [0,1]x[-1,0] (Fig. 1 with
-    the synthetic workload's channel height), inlet erf(y/0.1), convective outlet,
-    free-slip top, no-slip walls; dt = cfl * min(dx, dy) with U = 1."""
+    the synthetic workload's channel height), inlet erf(y/inlet_delta), convective outlet,
+    free-slip top, no-slip walls (or, with lip_slip, free slip on the lower wall outside
+    noslip_span, Sec. 4.4); dt = cfl * min(dx, dy) with U = 1."""
     x0, x1, y0, y1 = box
     dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
     return Params(nx=nx, ny=ny, x0=x0, x1=x1, y0=y0, y1=y1, Re=Re, dt=cfl * min(dx, dy),
-                  bc_x=0, bc_y=0, geometry=0, advection=advection, inlet_delta=0.1, conv_speed=1.0,
-                  cg_rtol=cg_rtol, cg_maxit=cg_maxit, ch_lo=0.0, ch_hi=0.0)
+                  bc_x=0, bc_y=0, geometry=0, advection=advection, inlet_delta=inlet_delta, conv_speed=1.0,
+                  cg_rtol=cg_rtol, cg_maxit=cg_maxit, ch_lo=0.0, ch_hi=0.0, lip_slip=lip_slip,
+                  slip_lo=noslip_span[0], slip_hi=noslip_span[1])
 
 
 def make_params(**kw) -> Params:
     base = dict(nx=16, ny=16, x0=0.0, x1=1.0, y0=0.0, y1=1.0, Re=100.0, dt=1e-3, bc_x=1, bc_y=1,
                 geometry=1, advection=1, inlet_delta=0.1, conv_speed=1.0, cg_rtol=1e-13,
-                cg_maxit=100000, ch_lo=0.0, ch_hi=0.0)
+                cg_maxit=100000, ch_lo=0.0, ch_hi=0.0, lip_slip=0, slip_lo=0.0, slip_hi=0.0)
     base.update(kw)
     return Params(**base)
 
@@ -565,14 +569,15 @@ def covariance_B(P: Params, sigma: float, a: float, region=CAVITY_REGION):
     return sigma * sigma * np.exp(-d2 / (a * a))
 
 
-def eigen_ensemble(P: Params, sigma: float, a: float, N: int, region=CAVITY_REGION):
+def eigen_ensemble(P: Params, sigma: float, a: float, N: int, region=CAVITY_REGION, y_only: bool = False):
     """Sec. 3.3.2: B = U Sigma U^T with U^T M_f U = I and E = U_N Sigma_N^{1/2} sqrt(N - 1)
     (Eq. eigenvm1).  On this uniform grid M_f = dx dy I, which cancels: E = V_N Lambda_N^{1/2} sqrt(N-1)
     with (V, Lambda) the Euclidean eigenpairs of B.  The control vector holds two independent
     components with the same covariance, so B = diag(B_s, B_s): each eigenpair of B_s appears twice,
     and the columns of E take the eigenvectors of B_s in decreasing eigenvalue order, each first as an
-    fx field and then as an fy field.  Each eigenvector's sign makes its largest-magnitude entry
-    positive.  Returns (E [n_ctrl x N], the N eigenvalues of B used)."""
+    fx field and then as an fy field (with y_only, forcing in the y-momentum equation only, the fx
+    variance is zero and every column is an fy field).  Each eigenvector's sign makes its
+    largest-magnitude entry positive.  Returns (E [n_ctrl x N], the N eigenvalues of B used)."""
     Bs = covariance_B(P, sigma, a, region)
     lam, V = np.linalg.eigh(Bs)
     order = np.argsort(lam)[::-1]
@@ -581,13 +586,14 @@ def eigen_ensemble(P: Params, sigma: float, a: float, N: int, region=CAVITY_REGI
     E = np.zeros((2 * n, N))
     lams = np.zeros(N)
     for k in range(N):
-        v = V[:, k // 2].copy()
+        r = k if y_only else k // 2
+        v = V[:, r].copy()
         j = int(np.argmax(np.abs(v)))
         if v[j] < 0:
             v = -v
-        comp = k % 2
-        E[comp * n:(comp + 1) * n, k] = np.sqrt(max(lam[k // 2], 0.0) * (N - 1)) * v
-        lams[k] = lam[k // 2]
+        comp = 1 if y_only else k % 2
+        E[comp * n:(comp + 1) * n, k] = np.sqrt(max(lam[r], 0.0) * (N - 1)) * v
+        lams[k] = lam[r]
     return E, lams
 
 

@@ -71,6 +71,10 @@ typedef struct {
     double cg_rtol;      /* CG stops when ||r||_2 <= cg_rtol * ||rhs||_2 */
     int cg_maxit;
     double ch_lo, ch_hi; /* channel bounds for geometry 2 / 3 */
+    int lip_slip;        /* 1: a solid face under a fluid face (a lower wall) whose x lies outside
+                            [slip_lo, slip_hi] reflects evenly (free slip) instead of oddly (no slip):
+                            the slip segments of the paper's lower wall (Sec. 4.4) */
+    double slip_lo, slip_hi;
 } orc_params;
 
 enum { FK_WALL = 0, FK_UNKNOWN = 1, FK_INLET = 2, FK_OUTLET = 3, FK_SOLID = 4, FK_COPY = 5 };
@@ -305,6 +309,15 @@ void orc_set_face_forcing(orc_sim *s, const double *fu, const double *fv)
     for (size_t k = 0; k < nv_; ++k) s->fv[k] = (fv && s->vk[k] == FK_UNKNOWN) ? fv[k] : 0.0;
 }
 
+/* Reflection sign of the tangential velocity across a lower wall at face column i: -1 (no slip),
+ * or +1 on the slip segments (Sec. 4.4). */
+static double lower_wall_sign(const orc_sim *s, int i)
+{
+    if (!s->P.lip_slip) return -1.0;
+    double x = s->P.x0 + (double)i * s->dx;
+    return (x < s->P.slip_lo || x > s->P.slip_hi) ? 1.0 : -1.0;
+}
+
 /* --------------------------------------------------------------------- */
 /* Ghost filling: copy the state into padded arrays, then give every      */
 /* stencil position outside the fluid the value its boundary rule implies. */
@@ -324,7 +337,7 @@ static void fill_ghosts(orc_sim *s, const double *u, const double *v)
             int up = (j + 1 < ny) && s->uk[IU(s, i, j + 1)] == FK_UNKNOWN;
             int dn = (j - 1 >= 0) && s->uk[IU(s, i, j - 1)] == FK_UNKNOWN;
             if (up && dn) { fprintf(stderr, "oracle: one-cell-thick solid layer is not supported\n"); abort(); }
-            UG(s, i, j) = up ? -u[IU(s, i, j + 1)] : (dn ? -u[IU(s, i, j - 1)] : 0.0);
+            UG(s, i, j) = up ? lower_wall_sign(s, i) * u[IU(s, i, j + 1)] : (dn ? -u[IU(s, i, j - 1)] : 0.0);
         }
     for (int j = 0; j <= ny; ++j)
         for (int i = 0; i < nx; ++i) {
@@ -1554,7 +1567,7 @@ static void fill_ghosts_adjoint(orc_sim *s, double *Ub, double *Vb, double *lu, 
             if (s->uk[IU(s, i, j)] != FK_SOLID) continue;
             int up = (j + 1 < ny) && s->uk[IU(s, i, j + 1)] == FK_UNKNOWN;
             int dn = (j - 1 >= 0) && s->uk[IU(s, i, j - 1)] == FK_UNKNOWN;
-            if (up) lu[IU(s, i, j + 1)] -= UB(i, j);
+            if (up) lu[IU(s, i, j + 1)] += lower_wall_sign(s, i) * UB(i, j);
             else if (dn) lu[IU(s, i, j - 1)] -= UB(i, j);
             UB(i, j) = 0.0;
         }

@@ -38,6 +38,7 @@ class Config(ctypes.Structure):
         ("max_outer", c_int), ("max_inner", c_int), ("inner_rtol", c_double),
         ("nu_pre", c_int), ("nu_post", c_int), ("coarse_sweeps", c_int), ("steps_per_graph", c_int),
         ("member_groups", c_int),
+        ("lip_slip", c_int), ("noslip_span", c_double * 2), ("forcing_y_only", c_int),
     ]
 
 
@@ -116,6 +117,8 @@ def default_config(nx: int, ny: int, **kw) -> Config:
     for k, v in kw.items():
         if k == "region":
             c.region = (c_double * 4)(*v)
+        elif k == "noslip_span":
+            c.noslip_span = (c_double * 2)(*v)
         else:
             setattr(c, k, v)
     return c

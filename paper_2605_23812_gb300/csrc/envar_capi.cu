@@ -166,6 +166,7 @@ extern "C" int envar_default_config(envar_config *c, int nx, int ny)
     c->precision = ENVAR_MIXED; c->cost_mode = ENVAR_COST_DOMAIN;
     c->div_tol = 1e-10; c->max_outer = 4; c->max_inner = 6; c->inner_rtol = 1e-4;
     c->nu_pre = 2; c->nu_post = 2; c->coarse_sweeps = 8; c->steps_per_graph = 10;
+    c->lip_slip = 0; c->noslip_span[0] = -0.4; c->noslip_span[1] = 1.75; c->forcing_y_only = 0;
     return ENVAR_OK;
 }
 
@@ -221,6 +222,15 @@ static int build_geometry(envar_handle h)
             }
             vk[(size_t)j * P + i] = k;
         }
+    // slip segments of the lower wall: a solid face under a fluid face reflects evenly
+    if (c.lip_slip)
+        for (int j = 0; j + 1 < ny; ++j)
+            for (int i = 0; i <= nx; ++i) {
+                const double xf = c.x0 + (double)i * dx;
+                if (uk[(size_t)j * P + i] == FK_SOLID && uk[(size_t)(j + 1) * P + i] == FK_UNK &&
+                    (xf < c.noslip_span[0] || xf > c.noslip_span[1]))
+                    uk[(size_t)j * P + i] = FK_SLIP;
+            }
     // the mirror rule needs a solid layer at least two faces thick
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i <= nx; ++i)
@@ -475,6 +485,10 @@ static int generate_ensemble(envar_handle h)
     launch_normals(h->cfg.seed, 0ULL, 0LL, (long long)nz, Z, h->st);
     launch_conv_sampler(N, h->nrx, h->nry, nxix, nxiy, Gx, Gy, Z, h->d_rect_ctrl, h->cfg.sigma, h->d_Erect, T, h->st);
     launch_rect_to_compact(N, h->nrect, h->ncc, h->d_cidx, h->d_Erect, h->d_E, h->st);
+    if (h->cfg.forcing_y_only) {   // zero prior variance on the fx entries
+        CK(cudaMemset2DAsync(h->d_E, sizeof(double) * h->n_ctrl, 0, sizeof(double) * h->ncc, N, h->st));
+        launch_compact_to_rect(N, h->nrect, h->ncc, h->d_cidx, h->d_E, h->d_Erect, h->st);
+    }
     CK(cudaStreamSynchronize(h->st));
     cudaFree(Gx); cudaFree(Gy); cudaFree(Z); cudaFree(T);
     CK(cudaGetLastError());
@@ -983,7 +997,8 @@ extern "C" int envar_eigen_ensemble(envar_handle h, double *lambda_host)
     if (!h) return ENVAR_EINVAL;
     const int N = h->N;
     if (N < 1) { set_err(h, "envar_eigen_ensemble: ensemble is empty"); return ENVAR_EINVAL; }
-    const int k = (N + 1) / 2;
+    const int y_only = h->cfg.forcing_y_only ? 1 : 0;
+    const int k = y_only ? N : (N + 1) / 2;
     if (k > h->ncc) { set_err(h, "envar_eigen_ensemble: %d eigenvectors requested, %d control cells", k, h->ncc); return ENVAR_EINVAL; }
     int m = std::min(h->ncc, std::max(2 * k + 40, 64));
     if (m % 2) --m;
@@ -994,8 +1009,8 @@ extern "C" int envar_eigen_ensemble(envar_handle h, double *lambda_host)
     if (e != cudaSuccess) { set_err(h, "envar_eigen_ensemble: %zu bytes of work space: %s", sizeof(double) * nd, cudaGetErrorString(e)); return ENVAR_ENOMEM; }
     std::vector<double> lam((size_t)k);
     int sweeps = 0;
-    int rc = eigen_ensemble(h->nrx, h->nry, h->g.dx, h->g.dy, h->cfg.corr_len, h->cfg.sigma, h->ncc, h->d_cidx, N, m,
-                            h->cfg.seed, (double *)work, h->d_E, lam.data(), &sweeps, h->st);
+    int rc = eigen_ensemble(h->nrx, h->nry, h->g.dx, h->g.dy, h->cfg.corr_len, h->cfg.sigma, h->ncc, h->d_cidx, N,
+                            y_only, m, h->cfg.seed, (double *)work, h->d_E, lam.data(), &sweeps, h->st);
     if (!rc) launch_compact_to_rect(N, h->nrect, h->ncc, h->d_cidx, h->d_E, h->d_Erect, h->st);
     e = cudaStreamSynchronize(h->st);
     cudaFree(work);
@@ -1004,7 +1019,7 @@ extern "C" int envar_eigen_ensemble(envar_handle h, double *lambda_host)
     CK(cudaGetLastError());
     if (sweeps >= 60) { set_err(h, "envar_eigen_ensemble: Jacobi did not converge"); return ENVAR_ESTATE; }
     if (lambda_host)
-        for (int i = 0; i < N; ++i) lambda_host[i] = lam[(size_t)(i / 2)];
+        for (int i = 0; i < N; ++i) lambda_host[i] = lam[(size_t)(y_only ? i : i / 2)];
     h->have_forward = false;
     return ENVAR_OK;
 }

@@ -13,7 +13,9 @@
 
 namespace envar {
 
-enum FaceKind : uint8_t { FK_ZERO = 0, FK_UNK = 1, FK_INLET = 2, FK_OUTLET = 3, FK_SOLID = 4 };
+// FK_SOLID faces take the odd mirror of their fluid-side neighbour inside stencils (no slip),
+// FK_SLIP faces the even one (free slip: the slip segments of the lower wall).
+enum FaceKind : uint8_t { FK_ZERO = 0, FK_UNK = 1, FK_INLET = 2, FK_OUTLET = 3, FK_SOLID = 4, FK_SLIP = 5 };
 
 constexpr int MAX_LEVELS = 12;
 // Level-0 tile of the Poisson / stencil kernels: 64 x 16 cells per 256-thread block.
@@ -359,7 +361,7 @@ void launch_dot_max(long long n, const double *a, const double *b, double *out, 
 // Eigenvector ensemble (k_eigen.cu)
 size_t eigen_work_doubles(int nrx, int nry, int ncc, int m, int k);
 int eigen_ensemble(int nrx, int nry, double dx, double dy, double a, double sigma, int ncc, const int *cidx, int N,
-                   int m, unsigned long long seed, double *work, double *E, double *lam_host, int *sweeps_host,
-                   cudaStream_t st);
+                   int y_only, int m, unsigned long long seed, double *work, double *E, double *lam_host,
+                   int *sweeps_host, cudaStream_t st);
 
 } // namespace envar

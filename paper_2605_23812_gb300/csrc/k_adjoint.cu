@@ -112,8 +112,12 @@ __global__ void k_adj_tend(Grid g, const double *__restrict__ u, const double *_
             // or uc itself (free-slip top)
             long long cn = c + P, cs = c - P;
             double sn = 1.0, ss = 1.0;
-            if (j + 1 == g.ny) { cn = c; sn = 1.0; } else if (g.uk[c + P] == FK_SOLID) { cn = c; sn = -1.0; }
-            if (j == 0) { cs = c; ss = -1.0; } else if (g.uk[c - P] == FK_SOLID) { cs = c; ss = -1.0; }
+            if (j + 1 == g.ny) { cn = c; sn = 1.0; }
+            else if (g.uk[c + P] == FK_SOLID) { cn = c; sn = -1.0; }
+            else if (g.uk[c + P] == FK_SLIP) { cn = c; sn = 1.0; }
+            if (j == 0) { cs = c; ss = -1.0; }
+            else if (g.uk[c - P] == FK_SOLID) { cs = c; ss = -1.0; }
+            else if (g.uk[c - P] == FK_SLIP) { cs = c; ss = 1.0; }
             const double un = sn * u[cn], us = ss * u[cs];
             const double vn = v[c + P - 1] + v[c + P], vs = v[c - 1] + v[c];
             const double dUc = -(2.0 * (uc + ue) - 2.0 * (uw + uc)) * i4dx - (vn - vs) * i4dy - 2.0 * nx2 - 2.0 * ny2;

@@ -212,8 +212,9 @@ __global__ void k_gather_ritz(int m, int k, const double *__restrict__ S, const 
 
 // Ritz vector r (row r of v = Sk Q): normalised, sign so that its largest-magnitude entry is
 // positive, scaled by sqrt(lambda_r (N-1)); written as members 2r (fx) and 2r+1 (fy) of E
-// (n_ctrl x N column-major, zero elsewhere), when those members exist.  One block per r.
-__global__ void k_ritz_members(int n, int N, const double *__restrict__ lam, const double *__restrict__ v,
+// (n_ctrl x N column-major, zero elsewhere), when those members exist, or, with y_only, as the fy
+// member r.  One block per r.
+__global__ void k_ritz_members(int n, int N, int y_only, const double *__restrict__ lam, const double *__restrict__ v,
                                double *__restrict__ E)
 {
     const int r = blockIdx.x;
@@ -246,8 +247,8 @@ __global__ void k_ritz_members(int n, int N, const double *__restrict__ lam, con
     const double sgn = (vr[s_idx[0]] < 0.0) ? -1.0 : 1.0;
     const double scale = sgn * sqrt(fmax(lam[r], 0.0) * (double)(N - 1)) / sqrt(nrm);
     const long long nctrl = 2LL * n;
-    for (int comp = 0; comp < 2; ++comp) {
-        const int k = 2 * r + comp;
+    for (int comp = y_only ? 1 : 0; comp < 2; ++comp) {
+        const int k = y_only ? r : 2 * r + comp;
         if (k >= N) break;
         double *Ek = E + (long long)k * nctrl;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -272,10 +273,10 @@ size_t eigen_work_doubles(int nrx, int nry, int ncc, int m, int k)
 // work: eigen_work_doubles(...) doubles of device memory.  Returns the Jacobi sweeps used (host
 // read) through *sweeps_host, and the k eigenvalues through lam_host (either may be NULL).
 int eigen_ensemble(int nrx, int nry, double dx, double dy, double a, double sigma, int ncc, const int *cidx, int N,
-                   int m, unsigned long long seed, double *work, double *E, double *lam_host, int *sweeps_host,
-                   cudaStream_t st)
+                   int y_only, int m, unsigned long long seed, double *work, double *E, double *lam_host,
+                   int *sweeps_host, cudaStream_t st)
 {
-    const int k = (N + 1) / 2;
+    const int k = y_only ? N : (N + 1) / 2;
     if (m % 2) --m;
     if (m < 2 || k > m) return -1;
     EigenWork W;
@@ -332,7 +333,7 @@ int eigen_ensemble(int nrx, int nry, double dx, double dy, double a, double sigm
     k_gather_ritz<<<cdiv(m * k, 256), 256, 0, st>>>(m, k, W.V, W.idx, W.Sk);
     count_launches(3);
     gemm_nn(k, ncc, m, W.Sk, W.Q, W.vr, st);
-    k_ritz_members<<<k, 1024, 0, st>>>(ncc, N, W.lam, W.vr, E);
+    k_ritz_members<<<k, 1024, 0, st>>>(ncc, N, y_only, W.lam, W.vr, E);
     count_launches(1);
     if (lam_host) cudaMemcpyAsync(lam_host, W.lam, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
     if (sweeps_host) cudaMemcpyAsync(sweeps_host, W.sweeps, sizeof(int), cudaMemcpyDeviceToHost, st);

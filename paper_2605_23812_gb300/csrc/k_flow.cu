@@ -15,8 +15,9 @@
 //
 // Boundary rules inside the stencils: a face with one fluid neighbour cell is a wall (normal
 // velocity 0, stored as 0); a face with no fluid neighbour takes the mirror value of the
-// fluid-side face (no slip by reflection); free slip at the top, no slip at the bottom, v = 0
-// at the inlet by reflection and dv/dx = 0 at the outlet.
+// fluid-side face (no slip by odd reflection; free slip by even reflection on the slip segments of
+// the lower wall); free slip at the top, no slip at the bottom, v = 0 at the inlet by reflection
+// and dv/dx = 0 at the outlet.
 #include "envar_internal.cuh"
 #include "../../include/envar.h"
 
@@ -153,8 +154,9 @@ __global__ void __launch_bounds__(256) k_predict(Grid g, const double *__restric
         double out;
         if (k == FK_UNK) {
             TR uc = (TR)um[c], ue = (TR)um[c + 1], uw = (TR)um[c - 1];
-            TR un = (j + 1 == g.ny) ? uc : (g.uk[c + P] == FK_SOLID ? -uc : (TR)um[c + P]);
-            TR usv = (j == 0) ? -uc : (g.uk[c - P] == FK_SOLID ? -uc : (TR)um[c - P]);
+            const uint8_t kn = (j + 1 < g.ny) ? g.uk[c + P] : FK_ZERO, ks = (j > 0) ? g.uk[c - P] : FK_ZERO;
+            TR un = (j + 1 == g.ny) ? uc : (kn == FK_SOLID ? -uc : (kn == FK_SLIP ? uc : (TR)um[c + P]));
+            TR usv = (j == 0) ? -uc : (ks == FK_SOLID ? -uc : (ks == FK_SLIP ? uc : (TR)um[c - P]));
             TR vnw = (TR)vm[c + P - 1], vne = (TR)vm[c + P], vsw = (TR)vm[c - 1], vse = (TR)vm[c];
             TR fe = uc + ue, fw = uw + uc;
             TR adv = (fe * fe - fw * fw) * i4dx + ((uc + un) * (vnw + vne) - (usv + uc) * (vsw + vse)) * i4dy;

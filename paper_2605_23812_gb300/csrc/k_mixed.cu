@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(256) k_predict_mx(Grid g, MixConst K, MixState
     if (has_u) {  // u face (i, j)
         f2 out{0.f, 0.f};
         if (ku == FK_UNK) {
-            const float un = (j + 1 == g.ny) ? uc : (kuN == FK_SOLID ? -uc : un0);
-            const float usv = (j == 0) ? -uc : (kuS == FK_SOLID ? -uc : us0);
+            const float un = (j + 1 == g.ny) ? uc : (kuN == FK_SOLID ? -uc : (kuN == FK_SLIP ? uc : un0));
+            const float usv = (j == 0) ? -uc : (kuS == FK_SOLID ? -uc : (kuS == FK_SLIP ? uc : us0));
             const float fe = uc + ue, fw = uw + uc;
             const float adv = (fe * fe - fw * fw) * K.i4dx + ((uc + un) * (vnw + vn) - (usv + uc) * (vsw + vc)) * K.i4dy;
             const float dif = K.nudx2 * (ue - 2.f * uc + uw) + K.nudy2 * (un - 2.f * uc + usv);

@@ -142,6 +142,10 @@ extern "C" int envar_draw_ensemble_noalloc(const envar_config *cfg, double *E_de
         launch_conv_sampler(1, nrx, nry, nxix, nxiy, Gx, Gy, Z, dr, c.sigma, Er, T, st);
         launch_rect_to_compact(1, nrect, ncc, dc, Er, E_dev + (size_t)k * n_ctrl, st);
     }
+    if (c.forcing_y_only) {   // zero prior variance on the fx entries, as envar_init does
+        e = cudaMemset2DAsync(E_dev, sizeof(double) * n_ctrl, 0, sizeof(double) * ncc, N, st);
+        if (e != cudaSuccess) return fail(ENVAR_ECUDA, "cudaMemset2DAsync", e);
+    }
     e = cudaPeekAtLastError();
     if (e != cudaSuccess) return fail(ENVAR_ECUDA, "ensemble draw launch", e);
     // the host vectors above are read by the copies: wait for them before returning

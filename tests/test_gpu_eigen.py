@@ -22,15 +22,16 @@ def _built():
     __graft_entry__.build()
 
 
-@pytest.mark.parametrize("nx,ny,N", [(128, 64, 8), (256, 128, 32), (128, 64, 7)])
-def test_eigen_ensemble_matches_oracle(nx, ny, N):
-    cfg = pkg.default_config(nx, ny, n_members=N, n_steps=2, n_window=1, precision=pkg.FP64_BATCHED)
+@pytest.mark.parametrize("nx,ny,N,y_only", [(128, 64, 8, 0), (256, 128, 32, 0), (128, 64, 7, 0), (128, 64, 8, 1)])
+def test_eigen_ensemble_matches_oracle(nx, ny, N, y_only):
+    cfg = pkg.default_config(nx, ny, n_members=N, n_steps=2, n_window=1, precision=pkg.FP64_BATCHED,
+                             forcing_y_only=y_only)
     ens = pkg.Ensemble(cfg)
     lam = ens.use_eigen_ensemble()
     E = ens.get_ensemble().cpu().numpy()
     ens.close()
     P = oracle.cavity_params(nx, ny, cfg.Re)
-    Eo, lamo = oracle.eigen_ensemble(P, cfg.sigma, cfg.corr_len, N)
+    Eo, lamo = oracle.eigen_ensemble(P, cfg.sigma, cfg.corr_len, N, y_only=bool(y_only))
     np.testing.assert_allclose(lam, lamo, rtol=1e-9)
     for k in range(N):
         a, b = E[:, k], Eo[:, k]

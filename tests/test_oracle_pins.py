@@ -173,6 +173,33 @@ def test_free_slip_top_pin_fails_on_a_no_slip_top(tmp_path):
 
 
 # --------------------------------------------------------------------------
+# Slip segments of the lower wall (Sec. 4.4, the paper's boundary conditions): a channel buried in
+# the mask with a slip lower wall and a no-slip upper wall is the free-slip half channel upside down,
+# u_j = (fx Re / 2)(y'_j (2H - y'_j) + h^2/4) with y' measured down from the upper wall.
+# --------------------------------------------------------------------------
+def _slip_channel_drift(lip_slip):
+    lo, hi = 0.25, 0.75
+    P = oracle.make_params(nx=8, ny=32, x0=0.0, x1=0.5, y0=0.0, y1=1.0, Re=50.0, dt=2e-3, bc_x=1, bc_y=2,
+                           geometry=2, ch_lo=lo, ch_hi=hi, lip_slip=lip_slip, slip_lo=1e9, slip_hi=2e9)
+    fx, H = 0.3, hi - lo
+    _, yu, _, _ = face_coords(P)
+    yp = hi - yu
+    prof = np.where((yu > lo) & (yu < hi), 0.5 * fx * P.Re * (yp * (2 * H - yp) + 0.25 * P.dy**2), 0.0)
+    u = np.repeat(prof[:, None], P.nx + 1, axis=1)
+    v = np.zeros((P.ny + 1, P.nx))
+    s = oracle.Sim(P)
+    s.set_state(u, v)
+    s.set_forcing(np.full_like(u, fx), np.zeros_like(v))
+    s.step(25)
+    return np.abs(s.state()[0] - u).max() / np.abs(u).max()
+
+
+def test_lower_wall_slip_segments_fixed_point():
+    assert _slip_channel_drift(1) <= 1e-12
+    assert _slip_channel_drift(0) > 1e-4      # the no-slip lower wall does not hold this profile
+
+
+# --------------------------------------------------------------------------
 # Convective outlet (the workload's outlet reading of Sec. 4.4: du/dt + Uc du/dx = 0 at the
 # outflow face with Uc = 1, then a uniform flux shift).  A channel periodic in y carries a
 # divergence-free disturbance u = 1 + e a(x) cos(ky), v = -e a'(x) sin(ky)/k on the uniform
