@@ -113,6 +113,10 @@ typedef struct envar_config {
     int forcing_y_only;      /* 1: forcing in the y-momentum equation only (Sec. 4.1): the prior
                                 variance of the fx entries is zero, so the drawn or eigenvector
                                 ensemble has zero fx rows */
+    int conditional_refinement; /* 1 (default): in the captured time step the pressure solve's
+                                refinement loop is a conditional WHILE graph node, run as often as
+                                the slowest member of the group needs (at most max_outer); 0: the
+                                loop is unrolled to max_outer refinements */
 } envar_config;
 
 typedef struct envar_handle_s *envar_handle;
@@ -345,6 +349,31 @@ int envar_autotune(envar_handle h, int probe_steps, double *best_ms_per_step, in
 
 /* The handle's configuration as currently used (after envar_autotune, its solver parameters). */
 int envar_get_config(envar_handle h, envar_config *cfg);
+
+/* Batches of uneven member groups (spec pattern 1: members of uneven grid sizes and horizons
+ * advancing together).  A batch advances several batched handles -- each its own grid size, Reynolds
+ * number, horizon, ensemble and solver parameters (tune each with envar_autotune first) -- in one
+ * captured CUDA graph per chunk, which holds the next c_k time steps of every handle k as parallel
+ * branches (each handle's member groups branch further).  c_k = n_steps_k / n_chunks with n_chunks
+ * the largest common divisor of the horizons that leaves at least 10 steps per chunk to the shortest
+ * one (or all of it if shorter), so every handle ends on the last chunk.  The graph is captured at the
+ * first envar_batch_forward; create a new batch after changing a handle's solver parameters. */
+typedef struct envar_batch_s *envar_batch;
+
+/* handles: n distinct batched handles (FP64_BATCHED or MIXED), kept by the caller and valid for the
+ * batch's lifetime.  cuda_stream: the batch's stream (NULL: a new one).  ENVAR_EINVAL if the
+ * horizons share no common step that keeps a chunk under 400 steps of the longest horizon. */
+int envar_batch_create(envar_batch *b, envar_handle *handles, int n, void *cuda_stream);
+int envar_batch_destroy(envar_batch b);
+
+/* The N_k + 1 forward runs of every handle of the batch (envar_forward_ensemble of each, run
+ * together): w_devs[k] is handle k's weights (N_k doubles, device).  Afterwards envar_cost,
+ * envar_gradient and the other per-run queries of each handle refer to this run.  Synchronises
+ * every handle's stream. */
+int envar_batch_forward(envar_batch b, const double *const *w_devs);
+
+/* Chunks per forward run and, per handle (n ints, nullable), time steps per chunk. */
+int envar_batch_info(envar_batch b, int *n_chunks, int *steps_per_chunk);
 
 /* Draw the ensemble matrix E without allocating device memory.  The paper has no counterpart:
  * this is for callers that cannot let a library call cudaMalloc (a framework whose caching

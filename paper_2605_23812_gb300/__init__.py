@@ -7,9 +7,9 @@ thin ctypes binding (with ``adjoint_cost``, a torch autograd function whose
 backward is the discrete adjoint); ``synth`` holds the seeded synthetic inputs.
 """
 from .capi import (COST_DOMAIN, COST_SENSORS, FP64_BATCHED, FP64_PLAIN, MIXED, ST_ADJOINT, ST_CFL, ST_DIVERGENCE,
-                   ST_NONFINITE, Config, Ensemble, EnvarError, adjoint_cost, default_config, header_symbols, lib,
+                   ST_NONFINITE, Batch, Config, Ensemble, EnvarError, adjoint_cost, default_config, header_symbols, lib,
                    revolve_plan)
 
-__all__ = ["Config", "Ensemble", "EnvarError", "adjoint_cost", "default_config", "header_symbols", "lib",
+__all__ = ["Batch", "Config", "Ensemble", "EnvarError", "adjoint_cost", "default_config", "header_symbols", "lib",
            "revolve_plan", "FP64_PLAIN", "FP64_BATCHED", "MIXED", "COST_DOMAIN", "COST_SENSORS", "ST_NONFINITE",
            "ST_DIVERGENCE", "ST_CFL", "ST_ADJOINT"]

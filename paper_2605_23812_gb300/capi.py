@@ -39,6 +39,7 @@ class Config(ctypes.Structure):
         ("nu_pre", c_int), ("nu_post", c_int), ("coarse_sweeps", c_int), ("steps_per_graph", c_int),
         ("member_groups", c_int),
         ("lip_slip", c_int), ("noslip_span", c_double * 2), ("forcing_y_only", c_int),
+        ("conditional_refinement", c_int),
     ]
 
 
@@ -75,6 +76,10 @@ def lib():
         "envar_excluded_members": [H, ctypes.POINTER(c_int)],
         "envar_gn_step": [H, c_double, c_void_p, c_void_p],
         "envar_eigen_ensemble": [H, c_void_p],
+        "envar_batch_create": [ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_int, c_void_p],
+        "envar_batch_destroy": [c_void_p],
+        "envar_batch_forward": [c_void_p, ctypes.POINTER(c_void_p)],
+        "envar_batch_info": [c_void_p, ctypes.POINTER(c_int), c_void_p],
         "envar_h1_smooth": [H, c_void_p, c_void_p, c_double],
         "envar_adjoint_lbfgs_step": [H, c_void_p, c_int, c_double, c_double, c_void_p, c_void_p, c_void_p],
         "envar_adjoint_lbfgs_reset": [H, c_int],
@@ -369,6 +374,49 @@ class Ensemble:
         v = [ctypes.c_longlong() for _ in range(4)]
         self._check(lib().envar_adjoint_stats(self._h, *[ctypes.byref(x) for x in v]), "envar_adjoint_stats")
         return dict(zip(("forward_steps", "reverse_steps", "stores", "restores"), (x.value for x in v)))
+
+
+class Batch:
+    """Uneven member groups (handles of different grids, Reynolds numbers and horizons) advancing
+    together, one CUDA graph per chunk (envar_batch_* in include/envar.h)."""
+
+    def __init__(self, ensembles, stream=None):
+        import torch
+        self.torch = torch
+        self.ens = list(ensembles)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        hs = (c_void_p * len(self.ens))(*[e._h for e in self.ens])
+        b = c_void_p()
+        rc = lib().envar_batch_create(ctypes.byref(b), hs, len(self.ens), c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise EnvarError(f"envar_batch_create: {ERRORS.get(rc, rc)}: {lib().envar_last_error(None).decode()}")
+        self._b = b
+
+    def forward(self, ws):
+        """ws: one weight vector per handle (arrays or device tensors)."""
+        wt = [e._dev(w, (e.N,)) for e, w in zip(self.ens, ws)]
+        ptrs = (c_void_p * len(wt))(*[c_void_p(t.data_ptr()) for t in wt])
+        self.torch.cuda.synchronize()
+        rc = lib().envar_batch_forward(self._b, ptrs)
+        if rc != 0:
+            raise EnvarError(f"envar_batch_forward: {ERRORS.get(rc, rc)}: {lib().envar_last_error(self.ens[0]._h).decode()}")
+
+    def info(self):
+        n = c_int()
+        per = np.zeros(len(self.ens), dtype=np.int32)
+        lib().envar_batch_info(self._b, ctypes.byref(n), _np_ptr(per))
+        return n.value, per
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().envar_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def revolve_plan(n_steps: int, n_slots: int):

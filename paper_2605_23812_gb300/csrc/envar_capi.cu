@@ -167,6 +167,7 @@ extern "C" int envar_default_config(envar_config *c, int nx, int ny)
     c->div_tol = 1e-10; c->max_outer = 4; c->max_inner = 6; c->inner_rtol = 1e-4;
     c->nu_pre = 2; c->nu_post = 2; c->coarse_sweeps = 8; c->steps_per_graph = 10;
     c->lip_slip = 0; c->noslip_span[0] = -0.4; c->noslip_span[1] = 1.75; c->forcing_y_only = 0;
+    c->conditional_refinement = 1;
     return ENVAR_OK;
 }
 
@@ -553,6 +554,8 @@ static int alloc_buffers(envar_handle h)
     h->pt.stride = M;
     DA(h->pt.part, (size_t)RS_COUNT * M * h->pt.nblk);
     DA(h->pt.red, M);
+    DA(h->pb.refine_count, M);
+    CK(cudaMemset(h->pb.refine_count, 0, sizeof(int) * M));
     CK(cudaMemset(h->pt.red, 0, sizeof(MemberRed) * M));
     DA(h->d_ctl, M);
     CK(cudaMemset(h->d_ctl, 0, sizeof(MemberCtl) * M));
@@ -609,6 +612,7 @@ static MemberView member_view(envar_handle h, int m0)
     v.pb.b = ds(v.pb.b, o); v.pb.x = ds(v.pb.x, o);
     v.pb.r = vs(v.pb.r, o); v.pb.e = vs(v.pb.e, o); v.pb.z = vs(v.pb.z, o); v.pb.q = vs(v.pb.q, o);
     v.pb.pv = vs(v.pb.pv, o); v.pb.pv1 = vs(v.pb.pv1, o);
+    v.pb.refine_count = h->pb.refine_count ? h->pb.refine_count + m0 : nullptr;
     for (int l = 0; l < h->nlev; ++l) {
         const long long ol = (long long)m0 * h->lev[l].S;
         v.pb.lev_e[l] = vs(v.pb.lev_e[l], ol);
@@ -711,8 +715,9 @@ static int capture(envar_handle h, int M, int nsteps, cudaGraphExec_t *out, long
     for (int s = 0; s < nsteps; ++s) enqueue_step(h, M);
     set_capturing(false);
     cudaError_t e = cudaStreamEndCapture(h->st, &graph);
-    if (e != cudaSuccess) {
-        set_err(h, "graph capture failed: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess || capture_failed()) {
+        if (e == cudaSuccess) cudaGraphDestroy(graph);
+        set_err(h, "graph capture failed: %s", e != cudaSuccess ? cudaGetErrorString(e) : "conditional loop body");
         return ENVAR_ECUDA;
     }
     size_t nn = 0;
@@ -818,6 +823,25 @@ static int forward_members(envar_handle h)
     return ENVAR_OK;
 }
 
+// ------------------------------------------------------------------------------------ batches
+// Several handles -- member groups of different grid sizes, Reynolds numbers and horizons -- advance
+// together: one CUDA graph per chunk holds every handle's next c_k time steps as parallel branches
+// (each handle's own member groups branch further inside), and c_k is proportional to the handle's
+// horizon, so all handles finish on the same chunk.
+struct envar_batch_s {
+    std::vector<envar_handle> h;
+    std::vector<int> per_chunk;       // time steps of each handle per chunk
+    int n_chunks = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;
+    long long graph_kernels = 0;
+    cudaEvent_t ev = nullptr;
+    std::vector<cudaEvent_t> ev_h;
+};
+
+static long long gcd_ll(long long a, long long b) { while (b) { long long t = a % b; a = b; b = t; } return a; }
+
 // ------------------------------------------------------------------------------------ API
 extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda_stream)
 {
@@ -904,6 +928,7 @@ extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda
             K.nudx2 = (float)(g.nu / (g.dx * g.dx)); K.nudy2 = (float)(g.nu / (g.dy * g.dy));
             K.dxf = (float)g.dx; K.dyf = (float)g.dy;
             pc.df_outer = h->mixed ? 1 : 0;
+            pc.conditional_loop = c.conditional_refinement ? 1 : 0;
             pc.mc = K;
         }
         if (h->mixed) prepare_poisson_kernels<float>(); else prepare_poisson_kernels<double>();
@@ -989,6 +1014,153 @@ extern "C" int envar_get_ensemble(envar_handle h, double *E)
     if (!h || !E) return ENVAR_EINVAL;
     CK(cudaMemcpyAsync(E, h->d_E, sizeof(double) * (size_t)h->n_ctrl * h->N, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaStreamSynchronize(h->st));
+    return ENVAR_OK;
+}
+
+extern "C" int envar_batch_create(envar_batch *out, envar_handle *handles, int n, void *cuda_stream)
+{
+    if (!out || !handles || n < 1) return ENVAR_EINVAL;
+    *out = nullptr;
+    long long g = 0;
+    int min_steps = 0;
+    for (int k = 0; k < n; ++k) {
+        envar_handle h = handles[k];
+        if (!h || !h->batched) {
+            set_err(nullptr, "envar_batch_create: handle %d is missing or not batched (FP64_PLAIN)", k);
+            return ENVAR_EINVAL;
+        }
+        for (int j = 0; j < k; ++j)
+            if (handles[j] == h) { set_err(nullptr, "envar_batch_create: handle %d appears twice", k); return ENVAR_EINVAL; }
+        g = gcd_ll(g, h->cfg.n_steps);
+        min_steps = k ? std::min(min_steps, h->cfg.n_steps) : h->cfg.n_steps;
+    }
+    // the fewest chunks (largest graphs) that keep at least 10 steps of the shortest horizon per chunk
+    long long chunks = g;
+    for (long long d = 1; d <= g; ++d)
+        if (g % d == 0 && min_steps / (g / d) >= std::min(10, min_steps)) { chunks = g / d; break; }
+    int maxc = 0;
+    for (int k = 0; k < n; ++k) maxc = std::max<long long>(maxc, handles[k]->cfg.n_steps / chunks);
+    if (maxc > 400) {
+        set_err(nullptr, "envar_batch_create: horizons share too small a common step (%lld chunks, %d steps per chunk)",
+                chunks, maxc);
+        return ENVAR_EINVAL;
+    }
+    envar_batch b = new envar_batch_s();
+    b->h.assign(handles, handles + n);
+    b->n_chunks = (int)chunks;
+    for (int k = 0; k < n; ++k) b->per_chunk.push_back((int)(handles[k]->cfg.n_steps / chunks));
+    if (cuda_stream) b->st = (cudaStream_t)cuda_stream;
+    else if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) == cudaSuccess) b->own_stream = true;
+    bool ok = b->st && cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) == cudaSuccess;
+    b->ev_h.assign(n, nullptr);
+    for (int k = 0; ok && k < n; ++k) ok = cudaEventCreateWithFlags(&b->ev_h[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        set_err(nullptr, "envar_batch_create: stream or event creation failed");
+        envar_batch_destroy(b);
+        return ENVAR_ECUDA;
+    }
+    *out = b;
+    return ENVAR_OK;
+}
+
+extern "C" int envar_batch_destroy(envar_batch b)
+{
+    if (!b) return ENVAR_OK;
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->ev) cudaEventDestroy(b->ev);
+    for (cudaEvent_t e : b->ev_h) if (e) cudaEventDestroy(e);
+    if (b->own_stream) cudaStreamDestroy(b->st);
+    delete b;
+    return ENVAR_OK;
+}
+
+// One chunk: every handle's next per_chunk[k] steps, forked from and joined to the batch stream.
+static int batch_capture(envar_batch b)
+{
+    envar_handle h0 = b->h[0];
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { set_err(h0, "batch capture: %s", cudaGetErrorString(e)); return ENVAR_ECUDA; }
+    set_capturing(true);
+    cudaEventRecord(b->ev, b->st);
+    for (size_t k = 0; k < b->h.size(); ++k) {
+        envar_handle h = b->h[k];
+        cudaStreamWaitEvent(h->st, b->ev, 0);
+        for (int s = 0; s < b->per_chunk[k]; ++s) enqueue_step(h, h->Mall);
+        cudaEventRecord(b->ev_h[k], h->st);
+        cudaStreamWaitEvent(b->st, b->ev_h[k], 0);
+    }
+    set_capturing(false);
+    e = cudaStreamEndCapture(b->st, &graph);
+    if (e != cudaSuccess || capture_failed()) {
+        if (e == cudaSuccess) cudaGraphDestroy(graph);
+        set_err(h0, "batch capture failed: %s", e != cudaSuccess ? cudaGetErrorString(e) : "conditional loop body");
+        return ENVAR_ECUDA;
+    }
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+    b->graph_kernels = 0;
+    for (size_t k = 0; k < nn; ++k) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++b->graph_kernels;
+    }
+    e = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { b->graph = nullptr; set_err(h0, "batch graph instantiate: %s", cudaGetErrorString(e)); return ENVAR_ECUDA; }
+    return ENVAR_OK;
+}
+
+extern "C" int envar_batch_forward(envar_batch b, const double *const *w_devs)
+{
+    if (!b || !w_devs) return ENVAR_EINVAL;
+    for (envar_handle h : b->h)
+        if (!h->have_ic) { set_err(h, "envar_batch_forward: no initial state"); return ENVAR_ESTATE; }
+    // the solver parameters of a handle may have changed (envar_autotune): recapture then
+    if (!b->graph) { int rc = batch_capture(b); if (rc) return rc; }
+    for (size_t k = 0; k < b->h.size(); ++k) {
+        envar_handle h = b->h[k];
+        h->ctl_all.assign(h->N + 1, MemberCtl{});
+        if (h->N > 0) {
+            if (!w_devs[k]) return ENVAR_EINVAL;
+            CK(cudaMemcpyAsync(h->d_w, w_devs[k], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
+        }
+        launch_member_forcing(h->Mall, 0, h->N, h->nrect, h->d_Erect, h->d_w, h->cfg.eps, h->d_frect, h->ms.frect,
+                              h->st);
+        reset_members(h, h->Mall);
+        CK(cudaEventRecord(b->ev_h[k], h->st));
+        CK(cudaStreamWaitEvent(b->st, b->ev_h[k], 0));
+    }
+    envar_handle h = b->h[0];   // error messages of the batch's own stream work go to the first handle
+    for (int c = 0; c < b->n_chunks; ++c) {
+        CK(cudaGraphLaunch(b->graph, b->st));
+        g_graph_kernels += b->graph_kernels;
+    }
+    CK(cudaEventRecord(b->ev, b->st));
+    for (envar_handle hk : b->h) {
+        h = hk;
+        CK(cudaStreamWaitEvent(h->st, b->ev, 0));
+        enqueue_cost(h, h->Mall, h->d_Jd, h->d_Js, h->d_Yd);
+        launch_copy_status(h->d_ctl, h->N + 1, h->d_status, h->st);
+        CK(cudaMemcpyAsync(h->ctl_all.data(), h->d_ctl, sizeof(MemberCtl) * (h->N + 1), cudaMemcpyDeviceToHost, h->st));
+    }
+    for (envar_handle hk : b->h) {
+        h = hk;
+        CK(cudaStreamSynchronize(h->st));
+        h->have_forward = true;
+    }
+    CK(cudaGetLastError());
+    return ENVAR_OK;
+}
+
+extern "C" int envar_batch_info(envar_batch b, int *n_chunks, int *steps_per_chunk)
+{
+    if (!b) return ENVAR_EINVAL;
+    if (n_chunks) *n_chunks = b->n_chunks;
+    if (steps_per_chunk)
+        for (size_t k = 0; k < b->per_chunk.size(); ++k) steps_per_chunk[k] = b->per_chunk[k];
     return ENVAR_OK;
 }
 
@@ -1572,7 +1744,7 @@ extern "C" int envar_kernel_launches(envar_handle h, long long *count)
 {
     (void)h;
     if (!count) return ENVAR_EINVAL;
-    *count = launches_so_far() + g_graph_kernels.load();
+    *count = launches_so_far() + g_graph_kernels.load() + (long long)conditional_body_launches();
     return ENVAR_OK;
 }
 
@@ -1767,8 +1939,10 @@ struct AdjointExec {
             enqueue_reverse(fi != 0, wi != 0);
             set_capturing(false);
             cudaError_t e = cudaStreamEndCapture(h->st, &graph);
-            if (e != cudaSuccess) {
-                set_err(h, "adjoint graph capture failed: %s", cudaGetErrorString(e));
+            if (e != cudaSuccess || capture_failed()) {
+                if (e == cudaSuccess) cudaGraphDestroy(graph);
+                set_err(h, "adjoint graph capture failed: %s",
+                        e != cudaSuccess ? cudaGetErrorString(e) : "conditional loop body");
                 return ENVAR_ECUDA;
             }
             e = cudaGraphInstantiate(&ge, graph, 0);

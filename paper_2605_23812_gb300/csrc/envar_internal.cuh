@@ -206,6 +206,10 @@ static inline int round_up(int a, int b) { return cdiv(a, b) * b; }
 void count_launches(long long n);
 long long launches_so_far();
 void set_capturing(bool on);
+long long captured_launches();          // launches recorded into graphs by this thread so far
+void note_capture_failure();            // a capture step failed: the graph must not be used
+bool capture_failed();
+unsigned long long conditional_body_launches();   // kernels run by conditional graph-node bodies
 
 // ------------------------------------------------------------- launchers
 // Flow kernels (k_flow.cu).  TR = tendency precision (float in mixed mode).
@@ -250,6 +254,7 @@ struct PoissonBufs {
     void *lev_e[MAX_LEVELS];        // level >= 1 correction (TM)
     void *lev_f[MAX_LEVELS];        // level >= 1 right-hand side (TM)
     void *lev_t[MAX_LEVELS];        // pre-smoothed guess of each tiled level (level 0 included)
+    int *refine_count;              // refinements done in the current step (one counter per member group)
 };
 struct PoissonCfg {
     int nlev;                       // number of levels
@@ -259,6 +264,7 @@ struct PoissonCfg {
     double inner_rtol2;             // inner_rtol^2
     double rtol_abs;                // outer stop: max |r| <= rtol_abs (r = b - A x, FV form)
     int df_outer;                   // 1: outer residual / update in df64 (mixed mode)
+    int conditional_loop;           // 1: refinement loop as a conditional WHILE graph node when captured
     MixConst mc;
     const unsigned char *cimg;      // coarse-block shared-memory image of the coarse levels' constants
     int cimg_bytes;                 // its size (a multiple of 16)

@@ -27,12 +27,22 @@ namespace envar {
 
 static std::atomic<long long> g_launches{0};
 static thread_local bool g_capturing = false;
+static thread_local long long g_captured = 0;      // launches recorded into graphs (this thread)
+static thread_local bool g_capture_failed = false;
 void count_launches(long long n)
 {
     if (!g_capturing) g_launches += n;
+    else g_captured += n;
 }
 long long launches_so_far() { return g_launches.load(); }
-void set_capturing(bool on) { g_capturing = on; }
+void set_capturing(bool on)
+{
+    g_capturing = on;
+    if (on) g_capture_failed = false;
+}
+long long captured_launches() { return g_captured; }
+void note_capture_failure() { g_capture_failed = true; }
+bool capture_failed() { return g_capture_failed; }
 
 // ---------------------------------------------------------------------------- reset
 __global__ void k_broadcast(const double *__restrict__ src, double *__restrict__ dst, long long S, int M)

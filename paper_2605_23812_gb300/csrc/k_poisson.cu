@@ -790,32 +790,43 @@ template <bool WARP> __device__ __forceinline__ void csync()
     if (WARP) __syncwarp(); else __syncthreads();
 }
 
-// Loops over a level: row j by warp (stride = warps in use), column by lane (stride 32), so no
-// thread divides by the level's width.
+// Loops over a level's global rows (staging in and out): row j by warp (stride = warps in use),
+// column by lane (stride 32), so no thread divides by the level's width and loads coalesce.
 #define CL_ROWS(j, tid, nt, ny) for (int j = (tid) >> 5; j < (ny); j += (nt) >> 5)
 #define CL_COLS(i, tid, n) for (int i = (tid) & 31; i < (n); i += 32)
 
-// one Gauss-Seidel half-sweep over the cells of one colour ((i + j) & 1 == colour)
+// Flat loops over the cells of a level in shared memory: item t -> (row t / w, column t % w), the
+// quotient by a multiply-high with m = floor((2^32 - 1) / w) + 1, exact for 2 <= w and t w < 2^32
+// (coarse levels have w >= 2 cells per colour row and fewer than 2^16 cells).
+__device__ __forceinline__ unsigned int div_magic(int w) { return 0xFFFFFFFFu / (unsigned int)w + 1u; }
+__device__ __forceinline__ int qdiv(int t, unsigned int m) { return (int)__umulhi((unsigned int)t, m); }
+
+// smoothing update e = acc / d: FP32 with the fast reciprocal (pre- and post-smoothing use the same
+// per-cell factor, so the V-cycle stays symmetric), FP64 exact
+__device__ __forceinline__ float gs_div(float a, float d) { return __fdividef(a, d); }
+__device__ __forceinline__ double gs_div(double a, double d) { return a / d; }
+
+// one Gauss-Seidel half-sweep over the cells of one colour ((i + j) & 1 == colour): every thread
+// takes cells t, t + nt, ... of the colour's cells in row-major order
 template <class T>
 __device__ __forceinline__ void cl_sweep(const CLev<T> &L, int colour, int tid, int nt)
 {
     const int hx = (L.nx + 1) >> 1;
-    CL_ROWS(j, tid, nt, L.ny) {
-        const int par = (j + colour) & 1;
-        CL_COLS(i2, tid, hx) {
-            const int i = 2 * i2 + par;
-            if (i >= L.nx) continue;
-            const int q = j * L.nx + i, w = j * (L.nx + 1) + i;
-            const T cW = L.cw[w], cE = L.cw[w + 1], cS = L.cs[q], cN = L.cs[q + L.nx];
-            const T d = cW + cE + cS + cN;
-            if (d == (T)0) continue;
-            T acc = L.f[q];
-            if (i > 0) acc += cW * L.e[q - 1];
-            if (i + 1 < L.nx) acc += cE * L.e[q + 1];
-            if (j > 0) acc += cS * L.e[q - L.nx];
-            if (j + 1 < L.ny) acc += cN * L.e[q + L.nx];
-            L.e[q] = acc / d;
-        }
+    const unsigned int m = div_magic(hx);
+    const int n = hx * L.ny;
+    for (int t = tid; t < n; t += nt) {
+        const int j = qdiv(t, m), i = 2 * (t - j * hx) + ((j + colour) & 1);
+        if (i >= L.nx) continue;
+        const int q = j * L.nx + i, w = j * (L.nx + 1) + i;
+        const T cW = L.cw[w], cE = L.cw[w + 1], cS = L.cs[q], cN = L.cs[q + L.nx];
+        const T d = cW + cE + cS + cN;
+        if (d == (T)0) continue;
+        T acc = L.f[q];
+        if (i > 0) acc += cW * L.e[q - 1];
+        if (i + 1 < L.nx) acc += cE * L.e[q + 1];
+        if (j > 0) acc += cS * L.e[q - L.nx];
+        if (j + 1 < L.ny) acc += cN * L.e[q + L.nx];
+        L.e[q] = gs_div(acc, d);
     }
 }
 
@@ -830,7 +841,9 @@ __device__ void cl_descend(const CoarseArgs &ca, unsigned char *smem, int l, int
         cl_sweep<T>(V, 0, tid, nt); csync<WARP>();
         cl_sweep<T>(V, 1, tid, nt); csync<WARP>();
     }
-    CL_ROWS(J, tid, nt, C.ny) CL_COLS(I, tid, C.nx) {
+    const unsigned int mc = div_magic(C.nx);
+    for (int t = tid; t < C.nx * C.ny; t += nt) {
+        const int J = qdiv(t, mc), I = t - J * C.nx;
         T sum = (T)0;
         for (int dj = 0; dj < 2; ++dj)
             for (int di = 0; di < 2; ++di) {
@@ -844,7 +857,7 @@ __device__ void cl_descend(const CoarseArgs &ca, unsigned char *smem, int l, int
                 if (j + 1 < V.ny) ax -= cN * V.e[qq + V.nx];
                 sum += V.f[qq] - ax;
             }
-        C.f[J * C.nx + I] = sum;
+        C.f[t] = sum;
     }
     csync<WARP>();
 }
@@ -872,8 +885,9 @@ template <class T, bool WARP>
 __device__ void cl_ascend(const CoarseArgs &ca, unsigned char *smem, int l, int tid, int nt)
 {
     const CLev<T> V = clev<T>(ca, smem, l), C = clev<T>(ca, smem, l + 1);
-    CL_ROWS(j, tid, nt, V.ny) CL_COLS(i, tid, V.nx) {
-        const int q = j * V.nx + i;
+    const unsigned int mv = div_magic(V.nx);
+    for (int q = tid; q < V.nx * V.ny; q += nt) {
+        const int j = qdiv(q, mv), i = q - j * V.nx;
         if (V.fl[q]) V.e[q] += C.e[(j >> 1) * C.nx + (i >> 1)];
     }
     csync<WARP>();
@@ -1079,41 +1093,142 @@ void prepare_poisson_kernels()
 template void prepare_poisson_kernels<float>();
 template void prepare_poisson_kernels<double>();
 
+// Kernels run by the bodies of conditional nodes (each body's last kernel adds the body's size).
+__device__ unsigned long long g_body_launches = 0;
+unsigned long long conditional_body_launches()
+{
+    unsigned long long v = 0;
+    cudaMemcpyFromSymbol(&v, g_body_launches, sizeof(v));
+    return v;
+}
+
+// Loop condition of the refinement loop captured as a conditional WHILE node: run another
+// refinement while some member of the group is above the tolerance and fewer than max_outer
+// refinements were made in this step (reset = 1 before the loop starts the count at zero).  The
+// count bounds the loop whatever the members' state.  body_kernels > 0: this launch closes a body
+// of that many kernels (itself included), which is added to the device launch counter.
+__global__ void k_refine_condition(const MemberCtl *__restrict__ ctl, int M, int *count, int max_outer, int reset,
+                                   int body_kernels, cudaGraphConditionalHandle handle)
+{
+    __shared__ int s_any;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    int any = 0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) any |= !ctl[m].outer_done;
+    if (any) atomicOr(&s_any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int c = reset ? 0 : *count + 1;
+        *count = c;
+        cudaGraphSetConditional(handle, (s_any && c < max_outer) ? 1u : 0u);
+        if (body_kernels > 0) atomicAdd(&g_body_launches, (unsigned long long)body_kernels);
+    }
+}
+
+template <class TM>
+static void outer_residual(const Grid &g, const Level &L0, int M, const PoissonBufs &B, const PoissonCfg &pc, RedCtx rc,
+                           MemberCtl *ctl, int count_it, cudaStream_t st)
+{
+    if (pc.df_outer) {
+        launch_outer_residual_mx(g, L0, pc.mc, M, B.ms, (float *)B.r, (float *)B.e, rc, ctl, pc.rtol_abs, count_it, st);
+    } else {
+        dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
+        k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, (TM *)B.r, (TM *)B.e, rc, ctl, pc.rtol_abs,
+                                                          count_it);
+        count_launches(1);
+    }
+}
+
+// One refinement: V-cycle-preconditioned inner CG on r = b - A x, then x += e.
+template <class TM>
+static void refinement(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc, RedCtx rc,
+                       MemberCtl *ctl, cudaStream_t st)
+{
+    const Level &L0 = lev[0];
+    TM *r = (TM *)B.r, *e = (TM *)B.e, *z = (TM *)B.z, *q = (TM *)B.q;
+    TM *pv[2] = {(TM *)B.pv, (TM *)B.pv1};
+    vcycle<TM>(g, lev, M, B, pc, rc, ctl, 0, 0, 1, st);
+    for (int k = 0; k < pc.max_inner; ++k) {
+        launch_spmv<TM>(g, L0, M, z, pv[k & 1], pv[(k + 1) & 1], q, rc, ctl, k, st);
+        launch_axpy<TM>(g, M, e, r, pv[(k + 1) & 1], q, rc, ctl, k, st);
+        count_launches(2);
+        if (k + 1 == pc.max_inner) break;   // the last update needs no new preconditioned residual
+        vcycle<TM>(g, lev, M, B, pc, rc, ctl, 1, k, 0, st);
+        k_inner_check<<<cdiv(M, 32), 32, 0, st>>>(rc, ctl, k, pc.inner_rtol2, M);
+        count_launches(1);
+    }
+    if (pc.df_outer) {
+        launch_outer_update_mx(g, M, B.ms, (const float *)e, ctl, st);
+    } else {
+        dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
+        k_outer_update<TM><<<grd, TILE_THREADS, 0, st>>>(g, B.x, e, ctl);
+        count_launches(1);
+    }
+}
+
+// The pressure solve of one time step.  Inside a stream capture (the step graphs) the refinement
+// loop is a conditional WHILE node whose body is one refinement and the residual after it: it
+// runs as many refinements as the slowest member of the group needs (at most max_outer), with no
+// launches for refinements nobody needs.  Outside a capture the loop is unrolled to max_outer
+// refinements, converged members' blocks returning at once.
 template <class TM>
 void launch_pressure_solve(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc,
                            const Partials &pt, MemberCtl *ctl, cudaStream_t st)
 {
     RedCtx rc = make_ctx(pt);
     const Level &L0 = lev[0];
-    dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
-    TM *r = (TM *)B.r, *e = (TM *)B.e, *z = (TM *)B.z, *q = (TM *)B.q;
-    TM *pv[2] = {(TM *)B.pv, (TM *)B.pv1};
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t ndeps = 0;
+    bool conditional = pc.conditional_loop && B.refine_count &&
+                       cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, &edata, &ndeps) == cudaSuccess &&
+                       cs == cudaStreamCaptureStatusActive;
+    if (conditional) {
+        outer_residual<TM>(g, L0, M, B, pc, rc, ctl, 1, st);
+        cudaGraphConditionalHandle handle;
+        conditional = cudaGraphConditionalHandleCreate(&handle, graph, 0, 0) == cudaSuccess;
+        if (conditional) {
+            k_refine_condition<<<1, 128, 0, st>>>(ctl, M, B.refine_count, pc.max_outer, 1, 0, handle);
+            count_launches(1);
+            cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, &edata, &ndeps);
+            cudaGraphNodeParams np{};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = handle;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            cudaStream_t bs = nullptr;
+            bool ok = cudaGraphAddNode(&node, graph, deps, edata, ndeps, &np) == cudaSuccess &&
+                      cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                          cudaSuccess &&
+                      cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess;
+            if (ok) {
+                cudaGraph_t body = np.conditional.phGraph_out[0];
+                ok = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                     cudaSuccess;
+                if (ok) {
+                    const long long c0 = captured_launches();
+                    refinement<TM>(g, lev, M, B, pc, rc, ctl, bs);
+                    outer_residual<TM>(g, L0, M, B, pc, rc, ctl, 1, bs);
+                    const int nb = (int)(captured_launches() - c0) + 1;
+                    k_refine_condition<<<1, 128, 0, bs>>>(ctl, M, B.refine_count, pc.max_outer, 0, nb, handle);
+                    count_launches(1);
+                    ok = cudaStreamEndCapture(bs, &body) == cudaSuccess;
+                }
+            }
+            if (bs) cudaStreamDestroy(bs);
+            // a conditional node without its full body could loop without end: the step graph
+            // must not be instantiated then
+            if (!ok) note_capture_failure();
+            return;
+        }
+    }
     for (int o = 0; o <= pc.max_outer; ++o) {
-        if (pc.df_outer) {
-            launch_outer_residual_mx(g, L0, pc.mc, M, B.ms, (float *)r, (float *)e, rc, ctl, pc.rtol_abs,
-                                     o < pc.max_outer ? 1 : 0, st);
-        } else {
-            k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, r, e, rc, ctl, pc.rtol_abs,
-                                                              o < pc.max_outer ? 1 : 0);
-            count_launches(1);
-        }
+        outer_residual<TM>(g, L0, M, B, pc, rc, ctl, o < pc.max_outer ? 1 : 0, st);
         if (o == pc.max_outer) break;
-        vcycle<TM>(g, lev, M, B, pc, rc, ctl, 0, 0, 1, st);
-        for (int k = 0; k < pc.max_inner; ++k) {
-            launch_spmv<TM>(g, L0, M, z, pv[k & 1], pv[(k + 1) & 1], q, rc, ctl, k, st);
-            launch_axpy<TM>(g, M, e, r, pv[(k + 1) & 1], q, rc, ctl, k, st);
-            count_launches(2);
-            if (k + 1 == pc.max_inner) break;   // the last update needs no new preconditioned residual
-            vcycle<TM>(g, lev, M, B, pc, rc, ctl, 1, k, 0, st);
-            k_inner_check<<<cdiv(M, 32), 32, 0, st>>>(rc, ctl, k, pc.inner_rtol2, M);
-            count_launches(1);
-        }
-        if (pc.df_outer) {
-            launch_outer_update_mx(g, M, B.ms, (const float *)e, ctl, st);
-        } else {
-            k_outer_update<TM><<<grd, TILE_THREADS, 0, st>>>(g, B.x, e, ctl);
-            count_launches(1);
-        }
+        refinement<TM>(g, lev, M, B, pc, rc, ctl, st);
     }
 }
 

@@ -360,3 +360,59 @@ def test_autotune_keeps_the_divergence_target():
         outs.append((u, v))
         ens.close()
     assert vel_rel(outs[1][0], outs[1][1], outs[0][0], outs[0][1]) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", [pkg.FP64_BATCHED, pkg.MIXED])
+def test_conditional_refinement_loop_is_exact_and_skips_work(precision):
+    """The refinement loop as a conditional WHILE graph node runs only the refinements some member of
+    the group needs; converged members never change, so the results equal the unrolled loop's bit for
+    bit, with fewer kernel launches."""
+    nx, ny, N = 64, 32, 8
+    out = []
+    for cond in (0, 1):
+        cfg = pkg.default_config(nx, ny, Re=1000.0, n_steps=24, n_window=8, n_members=N, precision=precision,
+                                 max_outer=8, conditional_refinement=cond, steps_per_graph=10)
+        ens = pkg.Ensemble(cfg)
+        ens.set_initial_state(*synth.cavity_ic(nx, ny))
+        w = synth.weights(N)
+        ens.forward_ensemble(w)   # captures the graphs
+        n0 = pkg.capi.kernel_launches()
+        ens.forward_ensemble(w)
+        launches = pkg.capi.kernel_launches() - n0
+        J, _ = ens.cost()
+        u, v, p = (t.cpu().numpy() for t in ens.get_state(N))
+        out.append((J, u, v, p, launches, ens.diagnostics()["max_div"]))
+        assert (ens.member_status() == 0).all()
+        ens.close()
+    (J0, u0, v0, p0, l0, d0), (J1, u1, v1, p1, l1, d1) = out
+    assert np.array_equal(J0, J1) and np.array_equal(u0, u1) and np.array_equal(v0, v1) and np.array_equal(p0, p1)
+    assert d0 == d1
+    assert l1 < 0.8 * l0, (l0, l1)
+
+
+def test_chaotic_configuration_statistics_mixed_against_fp64():
+    """The chaotic-regime configuration (1024x512, Re 15000) shortened to 600 + 600 steps with N = 8:
+    the mixed-precision batched path against the FP64 batched path (itself tied to the oracle at
+    1e-10), at the statistics tolerances of that regime: the time-mean fluctuation energy of every
+    member within 2 %, and the EnVar gradient with cosine >= 0.95."""
+    nx, ny, N = 1024, 512, 8
+    out = {}
+    for prec in (pkg.FP64_BATCHED, pkg.MIXED):
+        # the FP64 reference at its own rounding floor (a few FP64 solves at this size end just above
+        # 1e-10 however many refinements they get); the mixed path at the 1e-10 target
+        kw = dict(max_outer=12, max_inner=8, inner_rtol=1e-4, div_tol=1e-9) if prec == pkg.FP64_BATCHED else \
+            dict(div_tol=1e-10)
+        cfg = pkg.default_config(nx, ny, Re=15000.0, n_steps=1200, n_window=600, n_members=N, precision=prec, **kw)
+        ens = pkg.Ensemble(cfg)
+        ens.set_initial_state(*synth.cavity_ic(nx, ny))
+        w = synth.weights(N)
+        ens.forward_ensemble(w)
+        J, _ = ens.cost()
+        out[prec] = (J, ens.gradient(), ens.member_status())
+        ens.close()
+    J64, g64, s64 = out[pkg.FP64_BATCHED]
+    Jmx, gmx, smx = out[pkg.MIXED]
+    assert (smx == 0).all() and (s64 == 0).all()
+    assert np.abs(Jmx / J64 - 1.0).max() <= 0.02, (Jmx, J64)
+    cos = float(gmx @ g64 / (np.linalg.norm(gmx) * np.linalg.norm(g64)))
+    assert cos >= 0.95, cos
