@@ -506,7 +506,8 @@ static int alloc_buffers(envar_handle h)
         MixState &ms = h->ms;
         DA(ms.uh, n0); DA(ms.ul, n0); DA(ms.vh, n0); DA(ms.vl, n0);
         DA(ms.ush, n0); DA(ms.usl, n0); DA(ms.vsh, n0); DA(ms.vsl, n0);
-        DA(ms.p, n0); DA(ms.Ru, n0); DA(ms.Rv, n0);
+        DA(ms.p, n0); DA(ms.Ru, 2 * n0); DA(ms.Rv, 2 * n0);
+        ms.rstride = (long long)n0;
         DA(ms.bh, n0); DA(ms.bl, n0); DA(ms.xh, n0); DA(ms.xl, n0);
         if (h->cfg.cost_mode == ENVAR_COST_DOMAIN) DA(ms.wf, 6 * n0);
         if (h->cfg.cost_mode == ENVAR_COST_DOMAIN && h->N > 0) DA(ms.wd, 4 * n0);
@@ -652,8 +653,7 @@ static void enqueue_range(envar_handle h, int M, const MemberView &v, cudaStream
     if (h->mixed) {
         if (part == 0) {
             launch_outflow_mx(g, M, v.ms, v.ubc, v.ctl, st);
-            launch_predict_mx(g, h->mc, M, v.ms, v.ubc, h->d_inh, h->d_inl, v.ctl, st);
-            launch_rhs_mx(g, h->mc, M, v.ms, st);
+            launch_predict_rhs_mx(g, h->mc, M, v.ms, v.ubc, h->d_inh, h->d_inl, v.ctl, st);
             launch_pressure_solve<float>(g, h->lev, M, v.pb, h->pc, v.pt, v.ctl, st);
         } else {
             launch_correct_mx(g, h->mc, M, v.ms, h->ms, h->x0, h->y0, want_wf, v.series, v.pt, v.ctl, h->cfg.div_tol,
@@ -1764,7 +1764,7 @@ extern "C" int envar_time_kernel(envar_handle h, int which, int reps, double *ms
         switch (which) {
         case 0:
             if (h->mixed)
-                launch_predict_mx(g, h->mc, M, h->ms, h->d_ubc, h->d_inh, h->d_inl, h->d_ctl, h->st);
+                launch_predict_rhs_mx(g, h->mc, M, h->ms, h->d_ubc, h->d_inh, h->d_inl, h->d_ctl, h->st);
             else
                 launch_predict<double>(g, M, h->d_u, h->d_v, h->d_p, (double *)h->d_Ru, (double *)h->d_Rv, h->d_us,
                                        h->d_vs, h->d_ubc, h->d_frect, h->d_ctl, h->st);
@@ -1780,7 +1780,7 @@ extern "C" int envar_time_kernel(envar_handle h, int which, int reps, double *ms
                            h->pt, h->d_ctl, h->cfg.div_tol, h->nfluid, h->st);
             return 0;
         case 8:
-            if (h->mixed) launch_rhs_mx(g, h->mc, M, h->ms, h->st);
+            if (h->mixed) launch_predict_rhs_mx(g, h->mc, M, h->ms, h->d_ubc, h->d_inh, h->d_inl, h->d_ctl, h->st);
             else launch_rhs(g, M, h->d_us, h->d_vs, h->pb.b, h->d_ctl, h->st);
             return 0;
         default:

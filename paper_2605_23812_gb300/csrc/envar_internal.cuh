@@ -90,7 +90,8 @@ struct MixState {
     float *uh, *ul, *vh, *vl;       // velocity u^n, v^n (df64)
     float *ush, *usl, *vsh, *vsl;   // predictor u*, v* (df64)
     float *p;                       // pressure (FP32)
-    float *Ru, *Rv;                 // previous tendency (FP32, AB2)
+    float *Ru, *Rv;                 // tendencies (FP32, AB2), two buffers each: +0 and +rstride
+    long long rstride;              // offset of the second tendency buffer (elements)
     float *bh, *bl, *xh, *xl;       // Poisson right-hand side and solution (df64)
     float *wf;                      // Welford per member: 6 planes (mean_u, mean_v, M2; hi/lo)
     float *wd;                      // Welford of d = u - u_0 per member: 4 planes (mean_du, mean_dv, M2 hi/lo)
@@ -303,9 +304,8 @@ void launch_reset_mx(const Grid &g, int M, const MixState &ic, const MixState &s
 void launch_export_mx(const Grid &g, const MixState &s, long long off, double *uo, double *vo, double *po,
                       cudaStream_t st);
 void launch_outflow_mx(const Grid &g, int M, const MixState &s, double *ubc, MemberCtl *ctl, cudaStream_t st);
-void launch_predict_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const double *ubc, const float *inh,
-                       const float *inl, const MemberCtl *ctl, cudaStream_t st);
-void launch_rhs_mx(const Grid &g, const MixConst &K, int M, const MixState &s, cudaStream_t st);
+void launch_predict_rhs_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const double *ubc,
+                           const float *inh, const float *inl, const MemberCtl *ctl, cudaStream_t st);
 void launch_outer_residual_mx(const Grid &g, const Level &L0, const MixConst &K, int M, const MixState &s, float *r,
                               float *e, const RedCtx &rc, MemberCtl *ctl, double rtol_abs, int count_it,
                               cudaStream_t st);

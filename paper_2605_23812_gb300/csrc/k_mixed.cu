@@ -66,6 +66,8 @@ void launch_reset_mx(const Grid &g, int M, const MixState &ic, const MixState &s
     cudaMemsetAsync(s.xl, 0, fb, st);
     cudaMemsetAsync(s.Ru, 0, fb, st);
     cudaMemsetAsync(s.Rv, 0, fb, st);
+    cudaMemsetAsync(s.Ru + s.rstride, 0, fb, st);
+    cudaMemsetAsync(s.Rv + s.rstride, 0, fb, st);
     if (want_welford) cudaMemsetAsync(s.wf, 0, 6 * fb, st);
     if (want_welford && s.wd) cudaMemsetAsync(s.wd, 0, 4 * fb, st);
     cudaMemsetAsync(ctl, 0, sizeof(MemberCtl) * M, st);
@@ -139,123 +141,156 @@ __device__ __forceinline__ float cell_forcing_f(const Grid &g, const float *__re
     return fr[((long long)comp * g.nry + b) * g.nrx + a];
 }
 
-__global__ void __launch_bounds__(256) k_predict_mx(Grid g, MixConst K, MixState s, const double *__restrict__ ubc,
-                                                    const float *__restrict__ inh, const float *__restrict__ inl,
-                                                    const MemberCtl *__restrict__ ctl)
+// Tendencies are double-buffered by step parity (s.Ru / s.Ru + s.rstride, likewise Rv): a block
+// also computes the predictor on the first face column and row of its east and north neighbours
+// (their Poisson right-hand side needs it) and must read the previous step's tendency there while
+// the neighbouring block writes the new one.
+struct RBuf { const float *uin, *vin; float *uout, *vout; };
+__device__ __forceinline__ RBuf rbuf(const MixState &s, long long off, int step)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int m = blockIdx.z;
-    if (i > g.nx || j > g.ny) return;
-    const long long off = (long long)m * g.S;
+    const long long a = (step & 1) ? 0 : s.rstride, b = (step & 1) ? s.rstride : 0;
+    return RBuf{s.Ru + off + a, s.Rv + off + a, s.Ru + off + b, s.Rv + off + b};
+}
+
+// Predictor on u face (i, j) of member m: R = diffusion - advection (central, divergence form, FP32 on
+// the high words), u* = u^n + dt (c1 R + c0 R^{n-1}) - dt G p^n + dt f on an unknown face (df64 sum),
+// the inlet profile or the convective outlet value on boundary faces, 0 on walls.  Rout (nullable)
+// receives R.
+__device__ __forceinline__ f2 ustar_mx(const Grid &g, const MixConst &K, const MixState &s, long long off, int m, int i,
+                                       int j, const float *__restrict__ Rin, float *Rout, const double *__restrict__ ubc,
+                                       const float *__restrict__ inh, const float *__restrict__ inl, float c1, float c0)
+{
     const int P = g.P;
-    const float *__restrict__ uh = s.uh + off;
-    const float *__restrict__ ul = s.ul + off;
-    const float *__restrict__ vh = s.vh + off;
-    const float *__restrict__ vl = s.vl + off;
-    const float *__restrict__ pm = s.p + off;
-    float *__restrict__ Ru = s.Ru + off;
-    float *__restrict__ Rv = s.Rv + off;
-    const float *__restrict__ fr = s.frect + (long long)m * 2 * g.nry * g.nrx;
-    const uint8_t *__restrict__ uk = g.uk;
-    const uint8_t *__restrict__ vk = g.vk;
-    const bool has_u = j < g.ny, has_v = i < g.nx;
-    // clamped neighbour indices: every load below is in bounds and independent of the others;
-    // values at clamped positions are used only where the face kind makes them the true neighbour
-    const int jn = min(j + 1, g.ny - 1), js = max(j - 1, 0), ie = min(i + 1, g.nx), iw = max(i - 1, 0);
-    const int ivw = max(i - 1, 0), ive = min(i + 1, g.nx - 1), jvn = min(j + 1, g.ny);
     const long long c = (long long)j * P + i;
-    const long long cUN = (long long)jn * P + i, cUS = (long long)js * P + i;
-    const long long cE = (long long)j * P + ie, cW = (long long)j * P + iw;
-    const long long cVN = (long long)jvn * P + i;
-    // kinds
-    const uint8_t ku = has_u ? uk[c] : FK_ZERO, kuN = uk[cUN], kuS = uk[cUS];
-    const uint8_t kv = has_v ? vk[c] : FK_ZERO, kvE = vk[(long long)j * P + ive], kvW = vk[(long long)j * P + ivw];
-    // velocities (high words), pressure, previous tendencies
-    const float uc = uh[c], ue = uh[cE], uw = uh[cW], un0 = uh[cUN], us0 = uh[cUS];
-    const float usw = uh[(long long)js * P + i], use = uh[(long long)js * P + ie];
-    const float vc = vh[c], vn = vh[cVN], vs0 = vh[(long long)max(j - 1, 0) * P + i];
+    const uint8_t ku = g.uk[c];
+    if (ku == FK_INLET) return f2{inh[j], inl[j]};
+    if (ku == FK_OUTLET) return d_to_df(ubc[(long long)m * g.ny + j]);
+    if (ku != FK_UNK) return f2{0.f, 0.f};
+    const float *__restrict__ uh = s.uh + off;
+    const float *__restrict__ vh = s.vh + off;
+    const float *__restrict__ pm = s.p + off;
+    const int jn = min(j + 1, g.ny - 1), js = max(j - 1, 0), ie = min(i + 1, g.nx), iw = max(i - 1, 0);
+    const int jvn = min(j + 1, g.ny);
+    const uint8_t kuN = g.uk[(long long)jn * P + i], kuS = g.uk[(long long)js * P + i];
+    const float uc = uh[c], ue = uh[(long long)j * P + ie], uw = uh[(long long)j * P + iw];
+    const float un0 = uh[(long long)jn * P + i], us0 = uh[(long long)js * P + i];
+    const float vc = vh[c], vn = vh[(long long)jvn * P + i], vnw = vh[(long long)jvn * P + iw];
+    const float vsw = vh[(long long)j * P + iw];
+    const float un = (j + 1 == g.ny) ? uc : (kuN == FK_SOLID ? -uc : (kuN == FK_SLIP ? uc : un0));
+    const float usv = (j == 0) ? -uc : (kuS == FK_SOLID ? -uc : (kuS == FK_SLIP ? uc : us0));
+    const float fe = uc + ue, fw = uw + uc;
+    const float adv = (fe * fe - fw * fw) * K.i4dx + ((uc + un) * (vnw + vn) - (usv + uc) * (vsw + vc)) * K.i4dy;
+    const float dif = K.nudx2 * (ue - 2.f * uc + uw) + K.nudy2 * (un - 2.f * uc + usv);
+    const float R = dif - adv;
+    if (Rout) Rout[c] = R;
+    const float du = K.dt * (c1 * R + c0 * Rin[c]) - K.gxf * (pm[c] - pm[(long long)j * P + iw]);
+    f2 out = df_add_f(f2{uc, s.ul[off + c]}, du);
+    const float *__restrict__ fr = s.frect + (long long)m * 2 * g.nry * g.nrx;
+    const float f = 0.5f * (cell_forcing_f(g, fr, 0, i - 1, j) + cell_forcing_f(g, fr, 0, i, j));
+    if (f != 0.f) out = df_add_f(out, K.dt * f);
+    return out;
+}
+
+// Predictor on v face (i, j) of member m (as ustar_mx; v = 0 on every face but the unknown ones).
+__device__ __forceinline__ f2 vstar_mx(const Grid &g, const MixConst &K, const MixState &s, long long off, int m, int i,
+                                       int j, const float *__restrict__ Rin, float *Rout, float c1, float c0)
+{
+    const int P = g.P;
+    const long long c = (long long)j * P + i;
+    if (g.vk[c] != FK_UNK) return f2{0.f, 0.f};
+    const float *__restrict__ uh = s.uh + off;
+    const float *__restrict__ vh = s.vh + off;
+    const float *__restrict__ pm = s.p + off;
+    const int js = max(j - 1, 0), ie = min(i + 1, g.nx);
+    const int ivw = max(i - 1, 0), ive = min(i + 1, g.nx - 1), jvn = min(j + 1, g.ny);
+    const uint8_t kvE = g.vk[(long long)j * P + ive], kvW = g.vk[(long long)j * P + ivw];
+    const float uc = uh[c], ue = uh[(long long)j * P + ie];
+    const float use = uh[(long long)js * P + ie], usw = uh[(long long)js * P + i];
+    const float vc = vh[c], vn = vh[(long long)jvn * P + i], vs0 = vh[(long long)js * P + i];
     const float ve0 = vh[(long long)j * P + ive], vw0 = vh[(long long)j * P + ivw];
-    const float vnw = vh[(long long)jvn * P + iw], vsw = vh[cW];
-    const float ulc = ul[c], vlc = vl[c];
-    const float pc = pm[c], pw = pm[cW], ps = pm[(long long)max(j - 1, 0) * P + i];
-    const float Rup = Ru[c], Rvp = Rv[c];
-    const bool first = (ctl[m].step == 1);
+    const float ve = (i + 1 == g.nx) ? vc : (kvE == FK_SOLID ? -vc : ve0);
+    const float vw = (i == 0) ? -vc : (kvW == FK_SOLID ? -vc : vw0);
+    const float fn = vc + vn, fs = vs0 + vc;
+    const float adv = ((use + ue) * (vc + ve) - (usw + uc) * (vw + vc)) * K.i4dx + (fn * fn - fs * fs) * K.i4dy;
+    const float dif = K.nudx2 * (ve - 2.f * vc + vw) + K.nudy2 * (vn - 2.f * vc + vs0);
+    const float R = dif - adv;
+    if (Rout) Rout[c] = R;
+    const float dv = K.dt * (c1 * R + c0 * Rin[c]) - K.gyf * (pm[c] - pm[(long long)js * P + i]);
+    f2 out = df_add_f(f2{vc, s.vl[off + c]}, dv);
+    const float *__restrict__ fr = s.frect + (long long)m * 2 * g.nry * g.nrx;
+    const float f = 0.5f * (cell_forcing_f(g, fr, 1, i, j - 1) + cell_forcing_f(g, fr, 1, i, j));
+    if (f != 0.f) out = df_add_f(out, K.dt * f);
+    return out;
+}
+
+// K1: predictor and Poisson right-hand side in one pass.  A 32 x 8 block owns the u and v faces
+// (i, j) of its tile and writes u*, v* and the new tendencies; it also computes u* on the tile's
+// east face column and v* on its north face row into shared memory, so every cell of the tile has
+// the four faces of b = -(dy (u*_E - u*_W) + dx (v*_N - v*_S)) / dt (df64, zero in solid cells)
+// on chip; the right-hand side never re-reads u*, v*.
+constexpr int PR_TX = 32, PR_TY = 8;
+__global__ void __launch_bounds__(PR_TX *PR_TY) k_predict_rhs_mx(Grid g, MixConst K, MixState s,
+                                                                const double *__restrict__ ubc,
+                                                                const float *__restrict__ inh,
+                                                                const float *__restrict__ inl,
+                                                                const MemberCtl *__restrict__ ctl)
+{
+    __shared__ float suh[PR_TY][PR_TX + 1], sul[PR_TY][PR_TX + 1];
+    __shared__ float svh[PR_TY + 1][PR_TX], svl[PR_TY + 1][PR_TX];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * PR_TX, j0 = blockIdx.y * PR_TY;
+    const int i = i0 + tx, j = j0 + ty;
+    const int m = blockIdx.z;
+    const long long off = (long long)m * g.S;
+    const int step = ctl[m].step;
+    const bool first = (step == 1);
     const float c1 = first ? 1.f : 1.5f, c0 = first ? 0.f : -0.5f;
-
-    if (has_u) {  // u face (i, j)
-        f2 out{0.f, 0.f};
-        if (ku == FK_UNK) {
-            const float un = (j + 1 == g.ny) ? uc : (kuN == FK_SOLID ? -uc : (kuN == FK_SLIP ? uc : un0));
-            const float usv = (j == 0) ? -uc : (kuS == FK_SOLID ? -uc : (kuS == FK_SLIP ? uc : us0));
-            const float fe = uc + ue, fw = uw + uc;
-            const float adv = (fe * fe - fw * fw) * K.i4dx + ((uc + un) * (vnw + vn) - (usv + uc) * (vsw + vc)) * K.i4dy;
-            const float dif = K.nudx2 * (ue - 2.f * uc + uw) + K.nudy2 * (un - 2.f * uc + usv);
-            const float R = dif - adv;
-            Ru[c] = R;
-            const float du = K.dt * (c1 * R + c0 * Rup) - K.gxf * (pc - pw);
-            out = df_add_f(f2{uc, ulc}, du);
-            const float f = 0.5f * (cell_forcing_f(g, fr, 0, i - 1, j) + cell_forcing_f(g, fr, 0, i, j));
-            if (f != 0.f) out = df_add_f(out, K.dt * f);
-        } else if (ku == FK_INLET) {
-            out = f2{inh[j], inl[j]};
-        } else if (ku == FK_OUTLET) {
-            out = d_to_df(ubc[(long long)m * g.ny + j]);
+    const RBuf R = rbuf(s, off, step);
+    const long long c = (long long)j * g.P + i;
+    if (i <= g.nx && j < g.ny) {
+        const f2 u = ustar_mx(g, K, s, off, m, i, j, R.uin, R.uout, ubc, inh, inl, c1, c0);
+        s.ush[off + c] = u.h; s.usl[off + c] = u.l;
+        suh[ty][tx] = u.h; sul[ty][tx] = u.l;
+    }
+    if (i < g.nx && j <= g.ny) {
+        const f2 v = vstar_mx(g, K, s, off, m, i, j, R.vin, R.vout, c1, c0);
+        s.vsh[off + c] = v.h; s.vsl[off + c] = v.l;
+        svh[ty][tx] = v.h; svl[ty][tx] = v.l;
+    }
+    // the east face column and north face row belong to the neighbouring tiles: recompute them here
+    if (tx == 0) {
+        const int ie = i0 + PR_TX;
+        if (ie <= g.nx && j < g.ny) {
+            const f2 u = ustar_mx(g, K, s, off, m, ie, j, R.uin, nullptr, ubc, inh, inl, c1, c0);
+            suh[ty][PR_TX] = u.h; sul[ty][PR_TX] = u.l;
         }
-        s.ush[off + c] = out.h;
-        s.usl[off + c] = out.l;
     }
-    if (has_v) {  // v face (i, j)
-        f2 out{0.f, 0.f};
-        if (kv == FK_UNK) {
-            const float ve = (i + 1 == g.nx) ? vc : (kvE == FK_SOLID ? -vc : ve0);
-            const float vw = (i == 0) ? -vc : (kvW == FK_SOLID ? -vc : vw0);
-            const float fn = vc + vn, fs = vs0 + vc;
-            const float adv = ((use + ue) * (vc + ve) - (usw + uc) * (vw + vc)) * K.i4dx + (fn * fn - fs * fs) * K.i4dy;
-            const float dif = K.nudx2 * (ve - 2.f * vc + vw) + K.nudy2 * (vn - 2.f * vc + vs0);
-            const float R = dif - adv;
-            Rv[c] = R;
-            const float dv = K.dt * (c1 * R + c0 * Rvp) - K.gyf * (pc - ps);
-            out = df_add_f(f2{vc, vlc}, dv);
-            const float f = 0.5f * (cell_forcing_f(g, fr, 1, i, j - 1) + cell_forcing_f(g, fr, 1, i, j));
-            if (f != 0.f) out = df_add_f(out, K.dt * f);
+    if (ty == 0) {
+        const int jn = j0 + PR_TY;
+        if (i < g.nx && jn <= g.ny) {
+            const f2 v = vstar_mx(g, K, s, off, m, i, jn, R.vin, nullptr, c1, c0);
+            svh[PR_TY][tx] = v.h; svl[PR_TY][tx] = v.l;
         }
-        s.vsh[off + c] = out.h;
-        s.vsl[off + c] = out.l;
+    }
+    __syncthreads();
+    if (i < g.nx && j < g.ny) {
+        f2 b{0.f, 0.f};
+        if (g.fluid[c]) {
+            const f2 dU = df_sub(f2{suh[ty][tx + 1], sul[ty][tx + 1]}, f2{suh[ty][tx], sul[ty][tx]});
+            const f2 dV = df_sub(f2{svh[ty + 1][tx], svl[ty + 1][tx]}, f2{svh[ty][tx], svl[ty][tx]});
+            b = df_add(df_mul(dU, f2{K.kxh, K.kxl}), df_mul(dV, f2{K.kyh, K.kyl}));
+            b = f2{-b.h, -b.l};
+        }
+        s.bh[off + c] = b.h;
+        s.bl[off + c] = b.l;
     }
 }
 
-void launch_predict_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const double *ubc, const float *inh,
-                       const float *inl, const MemberCtl *ctl, cudaStream_t st)
+void launch_predict_rhs_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const double *ubc,
+                           const float *inh, const float *inl, const MemberCtl *ctl, cudaStream_t st)
 {
-    dim3 blk(32, 8), grd(cdiv(g.nx + 1, 32), cdiv(g.ny + 1, 8), M);
-    k_predict_mx<<<grd, blk, 0, st>>>(g, K, s, ubc, inh, inl, ctl);
-    count_launches(1);
-}
-
-// ---------------------------------------------------------------------------- rhs
-__global__ void __launch_bounds__(256) k_rhs_mx(Grid g, MixConst K, MixState s)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    int m = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    const long long off = (long long)m * g.S, c = off + (long long)j * g.P + i;
-    f2 b{0.f, 0.f};
-    if (g.fluid[c - off]) {
-        f2 dU = df_sub(f2{s.ush[c + 1], s.usl[c + 1]}, f2{s.ush[c], s.usl[c]});
-        f2 dV = df_sub(f2{s.vsh[c + g.P], s.vsl[c + g.P]}, f2{s.vsh[c], s.vsl[c]});
-        b = df_add(df_mul(dU, f2{K.kxh, K.kxl}), df_mul(dV, f2{K.kyh, K.kyl}));
-        b = f2{-b.h, -b.l};
-    }
-    s.bh[c] = b.h;
-    s.bl[c] = b.l;
-}
-
-void launch_rhs_mx(const Grid &g, const MixConst &K, int M, const MixState &s, cudaStream_t st)
-{
-    dim3 blk(32, 8), grd(cdiv(g.nx, 32), cdiv(g.ny, 8), M);
-    k_rhs_mx<<<grd, blk, 0, st>>>(g, K, s);
+    dim3 blk(PR_TX, PR_TY), grd(cdiv(g.nx + 1, PR_TX), cdiv(g.ny + 1, PR_TY), M);
+    k_predict_rhs_mx<<<grd, blk, 0, st>>>(g, K, s, ubc, inh, inl, ctl);
     count_launches(1);
 }
 

@@ -26,6 +26,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default solver parameters")
     ap.add_argument("--nu", type=int, default=0,
                     help="fix the smoothing sweep pairs (no autotuning: under a profiler the tuner's timings change)")
+    ap.add_argument("--max-outer", type=int, default=0, help="with --nu: the refinement cap")
+    ap.add_argument("--max-inner", type=int, default=0, help="with --nu: the inner-iteration cap")
+    ap.add_argument("--coarse-sweeps", type=int, default=0, help="with --nu: coarse-level sweep pairs")
+    ap.add_argument("--inner-rtol", type=float, default=0.0, help="with --nu: inner tolerance")
     args = ap.parse_args()
     import torch
 
@@ -37,6 +41,14 @@ def main():
                              n_members=args.members, precision=pkg.MIXED)
     if args.nu:
         cfg.nu_pre = cfg.nu_post = args.nu
+        if args.max_outer:
+            cfg.max_outer = args.max_outer
+        if args.max_inner:
+            cfg.max_inner = args.max_inner
+        if args.coarse_sweeps:
+            cfg.coarse_sweeps = args.coarse_sweeps
+        if args.inner_rtol:
+            cfg.inner_rtol = args.inner_rtol
     ens = pkg.Ensemble(cfg, stream=torch.cuda.Stream())
     ens.set_initial_state(*synth.cavity_ic(512, 256))
     if not args.nu and not args.no_autotune:   # the solver parameters the bench uses
