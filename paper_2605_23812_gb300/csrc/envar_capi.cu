@@ -1172,24 +1172,34 @@ extern "C" int envar_eigen_ensemble(envar_handle h, double *lambda_host)
     const int y_only = h->cfg.forcing_y_only ? 1 : 0;
     const int k = y_only ? N : (N + 1) / 2;
     if (k > h->ncc) { set_err(h, "envar_eigen_ensemble: %d eigenvectors requested, %d control cells", k, h->ncc); return ENVAR_EINVAL; }
-    int m = std::min(h->ncc, std::max(2 * k + 40, 64));
-    if (m % 2) --m;
-    if (m < k) m = k + (k % 2);
-    const size_t nd = eigen_work_doubles(h->nrx, h->nry, h->ncc, m, k);
+    // Lanczos steps: from max(2k + 40, 64), doubling while a kept Ritz pair is not converged, up to
+    // the control cells or 768 (the projected matrix is diagonalised in one block)
+    int mmax = std::min(h->ncc, 768);
+    mmax -= mmax % 2;
+    const int m0 = std::min(mmax, std::max(2 * k + 40, 64));
+    if (mmax < k + 2) { set_err(h, "envar_eigen_ensemble: too few control cells for %d eigenvectors", k); return ENVAR_EINVAL; }
+    const size_t nd = eigen_work_doubles(h->nrx, h->nry, h->ncc, mmax, k);
     void *work = nullptr;
     cudaError_t e = cudaMalloc(&work, sizeof(double) * nd);
     if (e != cudaSuccess) { set_err(h, "envar_eigen_ensemble: %zu bytes of work space: %s", sizeof(double) * nd, cudaGetErrorString(e)); return ENVAR_ENOMEM; }
     std::vector<double> lam((size_t)k);
-    int sweeps = 0;
+    int steps = 0;
+    double bound = 0.0;
+    const double tol = 1e-12;
     int rc = eigen_ensemble(h->nrx, h->nry, h->g.dx, h->g.dy, h->cfg.corr_len, h->cfg.sigma, h->ncc, h->d_cidx, N,
-                            y_only, m, h->cfg.seed, (double *)work, h->d_E, lam.data(), &sweeps, h->st);
+                            y_only, m0, mmax, tol, h->cfg.seed, (double *)work, h->d_E, lam.data(), &steps, &bound,
+                            h->st);
     if (!rc) launch_compact_to_rect(N, h->nrect, h->ncc, h->d_cidx, h->d_E, h->d_Erect, h->st);
     e = cudaStreamSynchronize(h->st);
     cudaFree(work);
     if (rc) { set_err(h, "envar_eigen_ensemble: bad Lanczos size"); return ENVAR_EINVAL; }
     if (e != cudaSuccess) { set_err(h, "envar_eigen_ensemble: %s", cudaGetErrorString(e)); return ENVAR_ECUDA; }
     CK(cudaGetLastError());
-    if (sweeps >= 60) { set_err(h, "envar_eigen_ensemble: Jacobi did not converge"); return ENVAR_ESTATE; }
+    if (bound > tol) {
+        set_err(h, "envar_eigen_ensemble: Ritz residual %g after %d Lanczos steps (relative to the largest eigenvalue)",
+                bound, steps);
+        return ENVAR_ESTATE;
+    }
     if (lambda_host)
         for (int i = 0; i < N; ++i) lambda_host[i] = lam[(size_t)(y_only ? i : i / 2)];
     h->have_forward = false;

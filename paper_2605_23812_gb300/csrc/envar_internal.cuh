@@ -365,9 +365,9 @@ void launch_axpy_vec(long long n, double a, const double *x, double *y, cudaStre
 void launch_dot_max(long long n, const double *a, const double *b, double *out, cudaStream_t st);
 
 // Eigenvector ensemble (k_eigen.cu)
-size_t eigen_work_doubles(int nrx, int nry, int ncc, int m, int k);
+size_t eigen_work_doubles(int nrx, int nry, int ncc, int mmax, int k);
 int eigen_ensemble(int nrx, int nry, double dx, double dy, double a, double sigma, int ncc, const int *cidx, int N,
-                   int y_only, int m, unsigned long long seed, double *work, double *E, double *lam_host,
-                   int *sweeps_host, cudaStream_t st);
+                   int y_only, int m0, int mmax, double tol, unsigned long long seed, double *work, double *E,
+                   double *lam_host, int *steps_host, double *bound_host, cudaStream_t st);
 
 } // namespace envar

@@ -10,6 +10,9 @@
 // Lanczos with full reorthogonalisation (two classical Gram-Schmidt passes per step), the
 // tridiagonal projection is diagonalised by parallel cyclic Jacobi in one block, and the Ritz
 // vectors are Q S.  All of this runs once per ensemble, before any forward run.
+#include <algorithm>
+#include <vector>
+
 #include "envar_internal.cuh"
 
 namespace envar {
@@ -258,85 +261,118 @@ __global__ void k_ritz_members(int n, int N, int y_only, const double *__restric
     }
 }
 
-struct EigenWork {
-    double *Kx, *Ky, *R, *T1, *Q, *w, *c1, *c2, *T, *V, *beta, *lam, *vr, *Sk;
-    int *idx, *sweeps;
-};
-
-size_t eigen_work_doubles(int nrx, int nry, int ncc, int m, int k)
+// Residual bound of the k kept Ritz pairs after m Lanczos steps: |B v_r - theta_r v_r| =
+// beta_m |S[m-1][idx_r]| (exact in exact arithmetic; with full reorthogonalisation a faithful
+// estimate).  bound[r] = that / theta_1.
+__global__ void k_ritz_bounds(int m, int k, const double *__restrict__ S, const int *__restrict__ idx,
+                              const double *__restrict__ lam, double beta, double *__restrict__ bound)
 {
-    return (size_t)nrx * nrx + (size_t)nry * nry + 2 * (size_t)nrx * nry + (size_t)(m + 1) * ncc + ncc +
-           2 * (size_t)(m + 2) + 2 * (size_t)m * m + m + k + (size_t)k * ncc + (size_t)k * m + (size_t)k + 8;
+    const int r = threadIdx.x;
+    if (r < k) bound[r] = fabs(beta * S[(long long)(m - 1) * m + idx[r]]) / fmax(lam[0], 1e-300);
 }
 
-// Leading k eigenpairs of B_s by m Lanczos steps; writes the N members of E (compact, column-major).
-// work: eigen_work_doubles(...) doubles of device memory.  Returns the Jacobi sweeps used (host
-// read) through *sweeps_host, and the k eigenvalues through lam_host (either may be NULL).
+// copy the leading m x m block of T (stored with row length mmax) to A (row length m)
+__global__ void k_copy_block(int m, int mmax, const double *__restrict__ T, double *__restrict__ A)
+{
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < (long long)m * m) A[e] = T[(e / m) * mmax + (e % m)];
+}
+
+size_t eigen_work_doubles(int nrx, int nry, int ncc, int mmax, int k)
+{
+    return (size_t)nrx * nrx + (size_t)nry * nry + 2 * (size_t)nrx * nry + (size_t)(mmax + 1) * ncc + ncc +
+           2 * (size_t)(mmax + 2) + 3 * (size_t)mmax * mmax + mmax + 2 * (size_t)k + (size_t)k * ncc +
+           (size_t)k * mmax + (size_t)k + 8;
+}
+
+// Leading k eigenpairs of B_s by Lanczos; writes the N members of E (compact, column-major).  The
+// Lanczos basis grows from m0 steps, doubling up to mmax (<= ncc), until every kept Ritz pair's
+// residual bound is below tol times the largest eigenvalue.  work: eigen_work_doubles(..., mmax, k)
+// doubles.  Host outputs (nullable): the k eigenvalues, the steps used, the largest bound.
 int eigen_ensemble(int nrx, int nry, double dx, double dy, double a, double sigma, int ncc, const int *cidx, int N,
-                   int y_only, int m, unsigned long long seed, double *work, double *E, double *lam_host,
-                   int *sweeps_host, cudaStream_t st)
+                   int y_only, int m0, int mmax, double tol, unsigned long long seed, double *work, double *E,
+                   double *lam_host, int *steps_host, double *bound_host, cudaStream_t st)
 {
     const int k = y_only ? N : (N + 1) / 2;
-    if (m % 2) --m;
-    if (m < 2 || k > m) return -1;
-    EigenWork W;
+    mmax -= mmax % 2;
+    m0 = std::min(m0 - m0 % 2, mmax);
+    if (m0 < 2 || k > m0) return -1;
     double *p = work;
-    W.Kx = p; p += (size_t)nrx * nrx;
-    W.Ky = p; p += (size_t)nry * nry;
-    W.R = p; p += (size_t)nrx * nry;
-    W.T1 = p; p += (size_t)nrx * nry;
-    W.Q = p; p += (size_t)(m + 1) * ncc;
-    W.w = p; p += ncc;
-    W.c1 = p; p += m + 2;
-    W.c2 = p; p += m + 2;
-    W.T = p; p += (size_t)m * m;
-    W.V = p; p += (size_t)m * m;
-    W.beta = p; p += m;
-    W.lam = p; p += k;
-    W.vr = p; p += (size_t)k * ncc;
-    W.Sk = p; p += (size_t)k * m;
-    W.idx = reinterpret_cast<int *>(p); p += k;
-    W.sweeps = reinterpret_cast<int *>(p);
+    double *Kx = p; p += (size_t)nrx * nrx;
+    double *Ky = p; p += (size_t)nry * nry;
+    double *R = p; p += (size_t)nrx * nry;
+    double *T1 = p; p += (size_t)nrx * nry;
+    double *Q = p; p += (size_t)(mmax + 1) * ncc;
+    double *w = p; p += ncc;
+    double *c1 = p; p += mmax + 2;
+    double *c2 = p; p += mmax + 2;
+    double *T = p; p += (size_t)mmax * mmax;
+    double *A = p; p += (size_t)mmax * mmax;
+    double *V = p; p += (size_t)mmax * mmax;
+    double *beta = p; p += mmax;
+    double *lam = p; p += k;
+    double *bound = p; p += k;
+    double *vr = p; p += (size_t)k * ncc;
+    double *Sk = p; p += (size_t)k * mmax;
+    int *idx = reinterpret_cast<int *>(p); p += k;
+    int *sweeps = reinterpret_cast<int *>(p);
 
-    k_gauss_kernel<<<cdiv(nrx * nrx, 256), 256, 0, st>>>(nrx, dx, a, W.Kx);
-    k_gauss_kernel<<<cdiv(nry * nry, 256), 256, 0, st>>>(nry, dy, a, W.Ky);
+    k_gauss_kernel<<<cdiv(nrx * nrx, 256), 256, 0, st>>>(nrx, dx, a, Kx);
+    k_gauss_kernel<<<cdiv(nry * nry, 256), 256, 0, st>>>(nry, dy, a, Ky);
     count_launches(2);
-    cudaMemsetAsync(W.T, 0, sizeof(double) * (size_t)m * m, st);
-    // seeded start vector
-    launch_normals(seed, 7ULL, 0LL, ncc, W.Q, st);
-    k_normalize<<<1, 1024, 0, st>>>(ncc, W.Q);
+    cudaMemsetAsync(T, 0, sizeof(double) * (size_t)mmax * mmax, st);
+    launch_normals(seed, 7ULL, 0LL, ncc, Q, st);   // seeded start vector
+    k_normalize<<<1, 1024, 0, st>>>(ncc, Q);
     count_launches(1);
     const int gb = cdiv(ncc, 256);
-    for (int j = 0; j < m; ++j) {
-        const double *qj = W.Q + (size_t)j * ncc;
-        // w = B_s q_j
-        cudaMemsetAsync(W.R, 0, sizeof(double) * (size_t)nrx * nry, st);
-        k_scatter_cc<<<gb, 256, 0, st>>>(ncc, cidx, qj, W.R);
+    int done = 0, m = m0;
+    std::vector<double> hb((size_t)k);
+    double worst = 0.0;
+    for (;;) {
+        for (int j = done; j < m; ++j) {
+            const double *qj = Q + (size_t)j * ncc;
+            // w = B_s q_j
+            cudaMemsetAsync(R, 0, sizeof(double) * (size_t)nrx * nry, st);
+            k_scatter_cc<<<gb, 256, 0, st>>>(ncc, cidx, qj, R);
+            count_launches(1);
+            gemm_nn(nry, nrx, nry, Ky, R, T1, st);
+            gemm_nn(nry, nrx, nrx, T1, Kx, R, st);
+            k_gather_cc<<<gb, 256, 0, st>>>(ncc, cidx, R, sigma * sigma, w);
+            // two Gram-Schmidt passes against q_0 .. q_j, then |w|^2 into c2[j+1]
+            k_dots<<<j + 1, 256, 0, st>>>(ncc, j + 1, Q, w, c1);
+            k_subtract<<<gb, 256, 0, st>>>(ncc, j + 1, Q, c1, w);
+            k_dots<<<j + 1, 256, 0, st>>>(ncc, j + 1, Q, w, c2);
+            k_subtract<<<gb, 256, 0, st>>>(ncc, j + 1, Q, c2, w);
+            k_dots<<<1, 256, 0, st>>>(ncc, 0, Q, w, c2 + j + 1);
+            k_lanczos_close<<<gb, 256, 0, st>>>(ncc, j, mmax, c1, c2, w, Q + (size_t)(j + 1) * ncc, T, beta);
+            count_launches(7);
+        }
+        done = m;
+        const size_t smem = sizeof(double) * m + sizeof(int) * m;
+        k_copy_block<<<cdiv(m * m, 256), 256, 0, st>>>(m, mmax, T, A);
+        k_jacobi<<<1, 1024, smem, st>>>(m, A, V, 1e-15, 60, sweeps);
+        k_top_diag<<<1, 32, 0, st>>>(m, k, A, idx, lam);
+        count_launches(3);
+        double bm = 0.0;
+        cudaMemcpyAsync(&bm, beta + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        k_ritz_bounds<<<1, 256, 0, st>>>(m, k, V, idx, lam, bm, bound);
         count_launches(1);
-        gemm_nn(nry, nrx, nry, W.Ky, W.R, W.T1, st);
-        gemm_nn(nry, nrx, nrx, W.T1, W.Kx, W.R, st);
-        k_gather_cc<<<gb, 256, 0, st>>>(ncc, cidx, W.R, sigma * sigma, W.w);
-        count_launches(1);
-        // two Gram-Schmidt passes against q_0 .. q_j, then |w|^2 into c2[j+1]
-        k_dots<<<j + 1, 256, 0, st>>>(ncc, j + 1, W.Q, W.w, W.c1);
-        k_subtract<<<gb, 256, 0, st>>>(ncc, j + 1, W.Q, W.c1, W.w);
-        k_dots<<<j + 1, 256, 0, st>>>(ncc, j + 1, W.Q, W.w, W.c2);
-        k_subtract<<<gb, 256, 0, st>>>(ncc, j + 1, W.Q, W.c2, W.w);
-        k_dots<<<1, 256, 0, st>>>(ncc, 0, W.Q, W.w, W.c2 + j + 1);
-        count_launches(5);
-        k_lanczos_close<<<gb, 256, 0, st>>>(ncc, j, m, W.c1, W.c2, W.w, W.Q + (size_t)(j + 1) * ncc, W.T, W.beta);
-        count_launches(1);
+        cudaMemcpyAsync(hb.data(), bound, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        worst = 0.0;
+        for (double b : hb) worst = std::max(worst, b);
+        if (worst <= tol || m >= mmax) break;
+        m = std::min(2 * m, mmax);
     }
-    const size_t smem = sizeof(double) * m + sizeof(int) * m;
-    k_jacobi<<<1, 1024, smem, st>>>(m, W.T, W.V, 1e-15, 60, W.sweeps);
-    k_top_diag<<<1, 32, 0, st>>>(m, k, W.T, W.idx, W.lam);
-    k_gather_ritz<<<cdiv(m * k, 256), 256, 0, st>>>(m, k, W.V, W.idx, W.Sk);
-    count_launches(3);
-    gemm_nn(k, ncc, m, W.Sk, W.Q, W.vr, st);
-    k_ritz_members<<<k, 1024, 0, st>>>(ncc, N, y_only, W.lam, W.vr, E);
+    k_gather_ritz<<<cdiv(m * k, 256), 256, 0, st>>>(m, k, V, idx, Sk);
     count_launches(1);
-    if (lam_host) cudaMemcpyAsync(lam_host, W.lam, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
-    if (sweeps_host) cudaMemcpyAsync(sweeps_host, W.sweeps, sizeof(int), cudaMemcpyDeviceToHost, st);
+    gemm_nn(k, ncc, m, Sk, Q, vr, st);
+    k_ritz_members<<<k, 1024, 0, st>>>(ncc, N, y_only, lam, vr, E);
+    count_launches(1);
+    if (lam_host) cudaMemcpyAsync(lam_host, lam, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
+    if (steps_host) *steps_host = m;
+    if (bound_host) *bound_host = worst;
     return 0;
 }
 
