@@ -155,8 +155,11 @@ __device__ __forceinline__ RBuf rbuf(const MixState &s, long long off, int step)
 // Predictor on u face (i, j) of member m: R = diffusion - advection (central, divergence form, FP32 on
 // the high words), u* = u^n + dt (c1 R + c0 R^{n-1}) - dt G p^n + dt f on an unknown face (df64 sum),
 // the inlet profile or the convective outlet value on boundary faces, 0 on walls.  Rout (nullable)
-// receives R.
-__device__ __forceinline__ f2 ustar_mx(const Grid &g, const MixConst &K, const MixState &s, long long off, int m, int i,
+// receives R.  Not inlined: the owner of a face and the neighbouring block that recomputes it must
+// run the same instructions (an inlined copy may contract products into FMAs differently, and a
+// last-bit difference between the stored u* and the u* of the right-hand side leaves a divergence
+// the pressure solve cannot remove).
+__device__ __noinline__ f2 ustar_mx(const Grid &g, const MixConst &K, const MixState &s, long long off, int m, int i,
                                        int j, const float *__restrict__ Rin, float *Rout, const double *__restrict__ ubc,
                                        const float *__restrict__ inh, const float *__restrict__ inl, float c1, float c0)
 {
@@ -192,7 +195,7 @@ __device__ __forceinline__ f2 ustar_mx(const Grid &g, const MixConst &K, const M
 }
 
 // Predictor on v face (i, j) of member m (as ustar_mx; v = 0 on every face but the unknown ones).
-__device__ __forceinline__ f2 vstar_mx(const Grid &g, const MixConst &K, const MixState &s, long long off, int m, int i,
+__device__ __noinline__ f2 vstar_mx(const Grid &g, const MixConst &K, const MixState &s, long long off, int m, int i,
                                        int j, const float *__restrict__ Rin, float *Rout, float c1, float c0)
 {
     const int P = g.P;
