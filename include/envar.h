@@ -226,9 +226,10 @@ int envar_gn_hessian(envar_handle h, double *H_host);
  * Armijo condition J(w + a p) <= J(w) + 1e-4 a g^T p, each trial cost J = J_obs + (N-1)/2 w^T w
  * from one forward run of the unperturbed member alone.  Either cost mode.
  * w_inout_host: N doubles (host, in/out).  J0_out_host (nullable): J(w) before the update;
- * alpha_out_host (nullable): the accepted step length; evals_out_host (nullable): trial runs.
- * ENVAR_ESTATE (w unchanged, history kept but no pair pending) if no trial met the condition or
- * member 0 failed.  Leaves member slot 0 holding the last trial run. */
+ * alpha_out_host (nullable): the accepted step length, 0 if no trial met the condition (then w is
+ * unchanged: it is stationary to the accuracy of J, and no pair is pending); evals_out_host
+ * (nullable): trial runs.  ENVAR_ESTATE (w unchanged) if member 0 failed.  Leaves member slot 0
+ * holding the last trial run. */
 int envar_lbfgs_step(envar_handle h, double *w_inout_host, double *J0_out_host, double *alpha_out_host,
                      int *evals_out_host);
 
@@ -319,8 +320,9 @@ int envar_h1_smooth(envar_handle h, const double *g_dev, double *gs_dev, double 
  * trials, each one forward run of member slot 0) that meets the Armijo condition
  * J(f + a p) <= J(f) + 1e-4 a (dJ/df . p); a0 = 1 with curvature pairs, else the length that moves f
  * by first_step in the max norm.  f_inout_dev: n_ctrl doubles (device, in/out).  J_out_host (nullable):
- * J(f) before the update; alpha_out_host, evals_out_host (nullable): step length and trial runs.
- * Needs what envar_adjoint_gradient needs.  ENVAR_ESTATE (f unchanged) if no trial met the condition. */
+ * J(f) before the update; alpha_out_host, evals_out_host (nullable): step length (0, with f
+ * unchanged, if no trial met the condition: f is stationary to the accuracy of J) and trial runs.
+ * Needs what envar_adjoint_gradient needs. */
 int envar_adjoint_lbfgs_step(envar_handle h, double *f_inout_dev, int max_snapshots, double l_sob, double first_step,
                              double *J_out_host, double *alpha_out_host, int *evals_out_host);
 

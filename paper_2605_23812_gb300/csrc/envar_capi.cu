@@ -97,6 +97,7 @@ struct envar_handle_s {
     cudaStream_t side[ENVAR_MAX_GROUPS] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[ENVAR_MAX_GROUPS] = {};
     cudaEvent_t ev_solved0 = nullptr;   // member 0's pressure increment is final (group 0)
+    cudaEvent_t ev_corr[ENVAR_MAX_GROUPS] = {};   // a group's correction has read member 0's increment
     int cimg_bytes = 0;
     // reduced-space optimisers (allocated on first use)
     double *d_Y = nullptr, *d_h0 = nullptr, *d_smean = nullptr, *d_H = nullptr, *d_L = nullptr, *d_x = nullptr;
@@ -643,9 +644,10 @@ static RefMember ref_member(envar_handle h)
     return r;
 }
 
-// One time step of M member slots starting at the view's first member, in two parts: the
-// predictor and the pressure solve (part 0), then the projection correction with the cost
-// accumulation (part 1).
+// One time step of M member slots starting at the view's first member, in three parts: the
+// predictor and the pressure solve (part 0), the projection correction with the cost accumulation
+// (part 1), and (FP64) the re-centring of the pressure increment, the next step's initial guess
+// (part 2; the mixed path re-centres inside the correction and has no part 2).
 static void enqueue_range(envar_handle h, int M, const MemberView &v, cudaStream_t st, int part)
 {
     const Grid &g = h->g;
@@ -655,7 +657,7 @@ static void enqueue_range(envar_handle h, int M, const MemberView &v, cudaStream
             launch_outflow_mx(g, M, v.ms, v.ubc, v.ctl, st);
             launch_predict_rhs_mx(g, h->mc, M, v.ms, v.ubc, h->d_inh, h->d_inl, v.ctl, st);
             launch_pressure_solve<float>(g, h->lev, M, v.pb, h->pc, v.pt, v.ctl, st);
-        } else {
+        } else if (part == 1) {
             launch_correct_mx(g, h->mc, M, v.ms, h->ms, h->x0, h->y0, want_wf, v.series, v.pt, v.ctl, h->cfg.div_tol,
                               h->nfluid, st);
         }
@@ -667,9 +669,10 @@ static void enqueue_range(envar_handle h, int M, const MemberView &v, cudaStream
                                st);
         launch_rhs(g, M, v.us, v.vs, v.pb.b, v.ctl, st);
         launch_pressure_solve<double>(g, h->lev, M, v.pb, h->pc, v.pt, v.ctl, st);
-    } else {
+    } else if (part == 1) {
         launch_correct(g, h->x0, h->y0, M, v.u, v.v, v.p, v.us, v.vs, v.pb.x, v.wf, v.wd, ref_member(h), want_wf,
                        v.series, v.pt, v.ctl, h->cfg.div_tol, h->nfluid, st);
+    } else {
         launch_recenter(g, M, v.pb.x, v.pt, h->nfluid, st);
     }
 }
@@ -677,23 +680,24 @@ static void enqueue_range(envar_handle h, int M, const MemberView &v, cudaStream
 // One time step of the first M member slots.  With all slots and several member groups, the
 // groups' steps are independent chains on side streams (parallel branches of the captured graph),
 // so one group's latency-bound phases overlap another's bandwidth-bound ones.  The corrections of
-// groups 1.. read member 0's pressure increment (the exact DOMAIN contraction), so they wait for
-// group 0's pressure solve.
+// groups 1.. read member 0's pressure increment (the exact DOMAIN contraction): they wait for group
+// 0's pressure solve, and group 0 re-centres that increment only after all of them have read it.
 static void enqueue_step(envar_handle h, int M)
 {
     const int G = (M == h->Mall) ? h->ngroups : 1;
     if (G <= 1) {
         const MemberView v = member_view(h, 0);
-        enqueue_range(h, M, v, h->st, 0);
-        enqueue_range(h, M, v, h->st, 1);
+        for (int part = 0; part < 3; ++part) enqueue_range(h, M, v, h->st, part);
         return;
     }
     const bool need_m0 = h->ms.wd != nullptr || h->d_wd != nullptr;
     cudaEventRecord(h->ev_fork, h->st);
     const int per = (M + G - 1) / G;
+    int ng = 0;
     for (int k = 0; k < G; ++k) {
         const int m0 = k * per, Mg = std::min(per, M - m0);
         if (Mg <= 0) break;
+        ng = k + 1;
         const MemberView v = member_view(h, m0);
         cudaStreamWaitEvent(h->side[k], h->ev_fork, 0);
         enqueue_range(h, Mg, v, h->side[k], 0);
@@ -702,6 +706,13 @@ static void enqueue_step(envar_handle h, int M)
             else cudaStreamWaitEvent(h->side[k], h->ev_solved0, 0);
         }
         enqueue_range(h, Mg, v, h->side[k], 1);
+        if (need_m0 && k > 0) cudaEventRecord(h->ev_corr[k], h->side[k]);
+    }
+    for (int k = 0; k < ng; ++k) {
+        const int m0 = k * per, Mg = std::min(per, M - m0);
+        if (k == 0 && need_m0)
+            for (int q = 1; q < ng; ++q) cudaStreamWaitEvent(h->side[0], h->ev_corr[q], 0);
+        enqueue_range(h, Mg, member_view(h, m0), h->side[k], 2);
         cudaEventRecord(h->ev_join[k], h->side[k]);
         cudaStreamWaitEvent(h->st, h->ev_join[k], 0);
     }
@@ -896,7 +907,8 @@ extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda
                       cudaEventCreateWithFlags(&h->ev_solved0, cudaEventDisableTiming) == cudaSuccess;
             for (int k = 0; ok && k < h->ngroups; ++k)
                 ok = cudaStreamCreateWithFlags(&h->side[k], cudaStreamNonBlocking) == cudaSuccess &&
-                     cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+                     cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&h->ev_corr[k], cudaEventDisableTiming) == cudaSuccess;
             if (!ok) {
                 set_err(nullptr, "envar_init: stream or event creation failed");
                 envar_destroy(h);
@@ -959,6 +971,7 @@ extern "C" int envar_destroy(envar_handle h)
     for (int k = 0; k < ENVAR_MAX_GROUPS; ++k) {
         if (h->side[k]) cudaStreamDestroy(h->side[k]);
         if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
+        if (h->ev_corr[k]) cudaEventDestroy(h->ev_corr[k]);
     }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_solved0) cudaEventDestroy(h->ev_solved0);
@@ -1534,9 +1547,10 @@ extern "C" int envar_lbfgs_step(envar_handle h, double *w_inout, double *J0_out,
     if (evals_out) *evals_out = evals;
     if (J0_out) *J0_out = Jw;
     if (!ok) {
-        set_err(h, "envar_lbfgs_step: no step length met the Armijo condition (g^T p = %g)", gp);
+        // no trial decreased J by the Armijo margin: w is stationary to the accuracy of J
         L.have_prev = false;
-        return ENVAR_ESTATE;
+        if (alpha_out) *alpha_out = 0.0;
+        return ENVAR_OK;
     }
     CK(cudaMemcpyAsync(h->d_w, h->d_wt, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(w_inout, h->d_wt, sizeof(double) * N, cudaMemcpyDeviceToHost, h->st));
@@ -1641,9 +1655,10 @@ extern "C" int envar_adjoint_lbfgs_step(envar_handle h, double *f_inout, int max
     if (evals_out) *evals_out = evals;
     if (J_out) *J_out = J;
     if (!ok) {
-        set_err(h, "envar_adjoint_lbfgs_step: no step length met the Armijo condition");
+        // no trial decreased J by the Armijo margin: f is stationary to the accuracy of J
         L.have_prev = false;
-        return ENVAR_ESTATE;
+        if (alpha_out) *alpha_out = 0.0;
+        return ENVAR_OK;
     }
     CK(cudaMemcpyAsync(f_inout, h->d_fs, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -2071,10 +2086,13 @@ extern "C" int envar_adjoint_stats(envar_handle h, long long *forward_steps, lon
 // Solver parameters that change only the speed of a time step (the refinement loop still stops at
 // div_tol): refinement cap, inner-iteration cap and tolerance, smoothing sweeps, coarse sweeps.
 struct SolverParams { int max_outer, max_inner, nu, coarse_sweeps; double inner_rtol; };
+// With the refinement loop as a conditional graph node a high refinement cap costs nothing unless
+// a step needs it, so every candidate keeps a cap of 10 (margin for the long runs after the probe)
+// and the candidates differ in what sets the cost of a refinement.
 static const SolverParams kTuneCandidates[] = {
-    {4, 3, 2, 2, 1e-3}, {4, 3, 2, 4, 1e-3}, {4, 4, 1, 2, 1e-3}, {4, 4, 2, 4, 1e-3},
-    {6, 2, 2, 2, 1e-3}, {4, 6, 2, 8, 1e-4}, {6, 4, 1, 4, 1e-3}, {6, 3, 2, 2, 1e-3},
-    {5, 2, 2, 2, 1e-3}, {5, 3, 2, 2, 1e-3}, {4, 3, 1, 2, 1e-3}, {5, 2, 3, 2, 1e-3},
+    {10, 2, 3, 2, 1e-3}, {10, 3, 2, 2, 1e-3}, {10, 2, 2, 2, 1e-3}, {10, 3, 3, 2, 1e-3},
+    {10, 4, 2, 4, 1e-3}, {10, 2, 3, 4, 1e-3}, {10, 6, 2, 8, 1e-4}, {10, 3, 1, 2, 1e-3},
+    {10, 2, 1, 2, 1e-3}, {10, 1, 3, 2, 1e-3}, {10, 1, 2, 2, 1e-3}, {10, 2, 3, 1, 1e-3},
 };
 
 static void drop_graphs(envar_handle h)

@@ -155,11 +155,15 @@ __device__ __forceinline__ RBuf rbuf(const MixState &s, long long off, int step)
 // Predictor on u face (i, j) of member m: R = diffusion - advection (central, divergence form, FP32 on
 // the high words), u* = u^n + dt (c1 R + c0 R^{n-1}) - dt G p^n + dt f on an unknown face (df64 sum),
 // the inlet profile or the convective outlet value on boundary faces, 0 on walls.  Rout (nullable)
-// receives R.  Not inlined: the owner of a face and the neighbouring block that recomputes it must
-// run the same instructions (an inlined copy may contract products into FMAs differently, and a
-// last-bit difference between the stored u* and the u* of the right-hand side leaves a divergence
-// the pressure solve cannot remove).
-__device__ __noinline__ f2 ustar_mx(const Grid &g, const MixConst &K, const MixState &s, long long off, int m, int i,
+// receives R.  The owner of a face and the neighbouring block that recomputes it must get the same
+// bits (a last-bit difference between the stored u* and the u* of the right-hand side leaves a
+// divergence the pressure solve cannot remove), so every FP32 operation is an explicitly rounded
+// intrinsic, which the compiler may not contract into an FMA differently at the two call sites.
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+
+__device__ __forceinline__ f2 ustar_mx(const Grid &g, const MixConst &K, const MixState &s, long long off, int m, int i,
                                        int j, const float *__restrict__ Rin, float *Rout, const double *__restrict__ ubc,
                                        const float *__restrict__ inh, const float *__restrict__ inl, float c1, float c0)
 {
@@ -181,21 +185,23 @@ __device__ __noinline__ f2 ustar_mx(const Grid &g, const MixConst &K, const MixS
     const float vsw = vh[(long long)j * P + iw];
     const float un = (j + 1 == g.ny) ? uc : (kuN == FK_SOLID ? -uc : (kuN == FK_SLIP ? uc : un0));
     const float usv = (j == 0) ? -uc : (kuS == FK_SOLID ? -uc : (kuS == FK_SLIP ? uc : us0));
-    const float fe = uc + ue, fw = uw + uc;
-    const float adv = (fe * fe - fw * fw) * K.i4dx + ((uc + un) * (vnw + vn) - (usv + uc) * (vsw + vc)) * K.i4dy;
-    const float dif = K.nudx2 * (ue - 2.f * uc + uw) + K.nudy2 * (un - 2.f * uc + usv);
-    const float R = dif - adv;
+    const float fe = fa(uc, ue), fw = fa(uw, uc);
+    const float adv = fa(fm(fs(fm(fe, fe), fm(fw, fw)), K.i4dx),
+                         fm(fs(fm(fa(uc, un), fa(vnw, vn)), fm(fa(usv, uc), fa(vsw, vc))), K.i4dy));
+    const float uc2 = fm(2.f, uc);
+    const float dif = fa(fm(K.nudx2, fa(fs(ue, uc2), uw)), fm(K.nudy2, fa(fs(un, uc2), usv)));
+    const float R = fs(dif, adv);
     if (Rout) Rout[c] = R;
-    const float du = K.dt * (c1 * R + c0 * Rin[c]) - K.gxf * (pm[c] - pm[(long long)j * P + iw]);
+    const float du = fs(fm(K.dt, fa(fm(c1, R), fm(c0, Rin[c]))), fm(K.gxf, fs(pm[c], pm[(long long)j * P + iw])));
     f2 out = df_add_f(f2{uc, s.ul[off + c]}, du);
     const float *__restrict__ fr = s.frect + (long long)m * 2 * g.nry * g.nrx;
-    const float f = 0.5f * (cell_forcing_f(g, fr, 0, i - 1, j) + cell_forcing_f(g, fr, 0, i, j));
-    if (f != 0.f) out = df_add_f(out, K.dt * f);
+    const float f = fm(0.5f, fa(cell_forcing_f(g, fr, 0, i - 1, j), cell_forcing_f(g, fr, 0, i, j)));
+    if (f != 0.f) out = df_add_f(out, fm(K.dt, f));
     return out;
 }
 
 // Predictor on v face (i, j) of member m (as ustar_mx; v = 0 on every face but the unknown ones).
-__device__ __noinline__ f2 vstar_mx(const Grid &g, const MixConst &K, const MixState &s, long long off, int m, int i,
+__device__ __forceinline__ f2 vstar_mx(const Grid &g, const MixConst &K, const MixState &s, long long off, int m, int i,
                                        int j, const float *__restrict__ Rin, float *Rout, float c1, float c0)
 {
     const int P = g.P;
@@ -213,16 +219,18 @@ __device__ __noinline__ f2 vstar_mx(const Grid &g, const MixConst &K, const MixS
     const float ve0 = vh[(long long)j * P + ive], vw0 = vh[(long long)j * P + ivw];
     const float ve = (i + 1 == g.nx) ? vc : (kvE == FK_SOLID ? -vc : ve0);
     const float vw = (i == 0) ? -vc : (kvW == FK_SOLID ? -vc : vw0);
-    const float fn = vc + vn, fs = vs0 + vc;
-    const float adv = ((use + ue) * (vc + ve) - (usw + uc) * (vw + vc)) * K.i4dx + (fn * fn - fs * fs) * K.i4dy;
-    const float dif = K.nudx2 * (ve - 2.f * vc + vw) + K.nudy2 * (vn - 2.f * vc + vs0);
-    const float R = dif - adv;
+    const float fn = fa(vc, vn), fsf = fa(vs0, vc);
+    const float adv = fa(fm(fs(fm(fa(use, ue), fa(vc, ve)), fm(fa(usw, uc), fa(vw, vc))), K.i4dx),
+                         fm(fs(fm(fn, fn), fm(fsf, fsf)), K.i4dy));
+    const float vc2 = fm(2.f, vc);
+    const float dif = fa(fm(K.nudx2, fa(fs(ve, vc2), vw)), fm(K.nudy2, fa(fs(vn, vc2), vs0)));
+    const float R = fs(dif, adv);
     if (Rout) Rout[c] = R;
-    const float dv = K.dt * (c1 * R + c0 * Rin[c]) - K.gyf * (pm[c] - pm[(long long)js * P + i]);
+    const float dv = fs(fm(K.dt, fa(fm(c1, R), fm(c0, Rin[c]))), fm(K.gyf, fs(pm[c], pm[(long long)js * P + i])));
     f2 out = df_add_f(f2{vc, s.vl[off + c]}, dv);
     const float *__restrict__ fr = s.frect + (long long)m * 2 * g.nry * g.nrx;
-    const float f = 0.5f * (cell_forcing_f(g, fr, 1, i, j - 1) + cell_forcing_f(g, fr, 1, i, j));
-    if (f != 0.f) out = df_add_f(out, K.dt * f);
+    const float f = fm(0.5f, fa(cell_forcing_f(g, fr, 1, i, j - 1), cell_forcing_f(g, fr, 1, i, j)));
+    if (f != 0.f) out = df_add_f(out, fm(K.dt, f));
     return out;
 }
 
