@@ -7,7 +7,8 @@ one forward evaluation of the 512x256 / Re 7500 / 33-member ensemble over --step
 warm up (graph capture), then a second one inside the NVTX range "timed" (for
 ncu --nvtx --nvtx-include "timed/").  --kernels additionally launches the listed
 hot kernels standalone (envar_time_kernel, one launch each) inside the range "kernels", for
-targeted captures of a single launch.
+targeted captures of a single launch.  --unrolled replaces the conditional refinement loop by the
+unrolled one, whose kernel nodes a profiler can list one by one.
 """
 from __future__ import annotations
 
@@ -30,6 +31,10 @@ def main():
     ap.add_argument("--max-inner", type=int, default=0, help="with --nu: the inner-iteration cap")
     ap.add_argument("--coarse-sweeps", type=int, default=0, help="with --nu: coarse-level sweep pairs")
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="with --nu: inner tolerance")
+    ap.add_argument("--unrolled", action="store_true",
+                    help="capture the refinement loop unrolled instead of as a conditional graph node (ncu does "
+                         "not profile the kernel nodes of graphs that hold conditional nodes); refinements past "
+                         "convergence then launch and return at once")
     args = ap.parse_args()
     import torch
 
@@ -49,6 +54,8 @@ def main():
             cfg.coarse_sweeps = args.coarse_sweeps
         if args.inner_rtol:
             cfg.inner_rtol = args.inner_rtol
+    if args.unrolled:
+        cfg.conditional_refinement = 0
     ens = pkg.Ensemble(cfg, stream=torch.cuda.Stream())
     ens.set_initial_state(*synth.cavity_ic(512, 256))
     if not args.nu and not args.no_autotune:   # the solver parameters the bench uses
