@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define ENVAR_ABI_VERSION 3
+#define ENVAR_ABI_VERSION 4
 
 enum {
     ENVAR_OK = 0,
@@ -117,6 +117,11 @@ typedef struct envar_config {
                                 refinement loop is a conditional WHILE graph node, run as often as
                                 the slowest member of the group needs (at most max_outer); 0: the
                                 loop is unrolled to max_outer refinements */
+    int guess_extrapolation; /* MIXED, 1 (default): the pressure increment's initial guess is the
+                                linear extrapolation 2 dp^n - dp^(n-1) of the last two increments
+                                (both re-centred on their fluid mean) from the third step on, the
+                                last increment before; 0: the last increment.  Only the number
+                                of refinements changes: every solve still ends at div_tol */
 } envar_config;
 
 typedef struct envar_handle_s *envar_handle;

@@ -39,7 +39,7 @@ class Config(ctypes.Structure):
         ("nu_pre", c_int), ("nu_post", c_int), ("coarse_sweeps", c_int), ("steps_per_graph", c_int),
         ("member_groups", c_int),
         ("lip_slip", c_int), ("noslip_span", c_double * 2), ("forcing_y_only", c_int),
-        ("conditional_refinement", c_int),
+        ("conditional_refinement", c_int), ("guess_extrapolation", c_int),
     ]
 
 

@@ -169,6 +169,7 @@ extern "C" int envar_default_config(envar_config *c, int nx, int ny)
     c->nu_pre = 2; c->nu_post = 2; c->coarse_sweeps = 8; c->steps_per_graph = 10;
     c->lip_slip = 0; c->noslip_span[0] = -0.4; c->noslip_span[1] = 1.75; c->forcing_y_only = 0;
     c->conditional_refinement = 1;
+    c->guess_extrapolation = 1;
     return ENVAR_OK;
 }
 
@@ -510,6 +511,7 @@ static int alloc_buffers(envar_handle h)
         DA(ms.p, n0); DA(ms.Ru, 2 * n0); DA(ms.Rv, 2 * n0);
         ms.rstride = (long long)n0;
         DA(ms.bh, n0); DA(ms.bl, n0); DA(ms.xh, n0); DA(ms.xl, n0);
+        if (h->cfg.guess_extrapolation) DA(ms.xp, n0);
         if (h->cfg.cost_mode == ENVAR_COST_DOMAIN) DA(ms.wf, 6 * n0);
         if (h->cfg.cost_mode == ENVAR_COST_DOMAIN && h->N > 0) DA(ms.wd, 4 * n0);
         DA(ms.frect, (size_t)M * 2 * h->nrect);
@@ -605,6 +607,7 @@ static MemberView member_view(envar_handle h, int m0)
         w.ush = fs(w.ush, o); w.usl = fs(w.usl, o); w.vsh = fs(w.vsh, o); w.vsl = fs(w.vsl, o);
         w.p = fs(w.p, o); w.Ru = fs(w.Ru, o); w.Rv = fs(w.Rv, o);
         w.bh = fs(w.bh, o); w.bl = fs(w.bl, o); w.xh = fs(w.xh, o); w.xl = fs(w.xl, o);
+        w.xp = fs(w.xp, o);
         w.wf = fs(w.wf, 6 * o);
         w.wd = fs(w.wd, 4 * o);
         w.frect = fs(w.frect, (long long)m0 * 2 * h->nrect);
@@ -655,7 +658,7 @@ static void enqueue_range(envar_handle h, int M, const MemberView &v, cudaStream
     if (h->mixed) {
         if (part == 0) {
             launch_outflow_mx(g, M, v.ms, v.ubc, v.ctl, st);
-            launch_predict_rhs_mx(g, h->mc, M, v.ms, v.ubc, h->d_inh, h->d_inl, v.ctl, st);
+            launch_predict_rhs_mx(g, h->mc, M, v.ms, v.ubc, h->d_inh, h->d_inl, v.ctl, v.pt.red, h->nfluid, st);
             launch_pressure_solve<float>(g, h->lev, M, v.pb, h->pc, v.pt, v.ctl, st);
         } else if (part == 1) {
             launch_correct_mx(g, h->mc, M, v.ms, h->ms, h->x0, h->y0, want_wf, v.series, v.pt, v.ctl, h->cfg.div_tol,
@@ -1789,7 +1792,8 @@ extern "C" int envar_time_kernel(envar_handle h, int which, int reps, double *ms
         switch (which) {
         case 0:
             if (h->mixed)
-                launch_predict_rhs_mx(g, h->mc, M, h->ms, h->d_ubc, h->d_inh, h->d_inl, h->d_ctl, h->st);
+                launch_predict_rhs_mx(g, h->mc, M, h->ms, h->d_ubc, h->d_inh, h->d_inl, h->d_ctl, h->pt.red,
+                                      h->nfluid, h->st);
             else
                 launch_predict<double>(g, M, h->d_u, h->d_v, h->d_p, (double *)h->d_Ru, (double *)h->d_Rv, h->d_us,
                                        h->d_vs, h->d_ubc, h->d_frect, h->d_ctl, h->st);
@@ -1805,7 +1809,9 @@ extern "C" int envar_time_kernel(envar_handle h, int which, int reps, double *ms
                            h->pt, h->d_ctl, h->cfg.div_tol, h->nfluid, h->st);
             return 0;
         case 8:
-            if (h->mixed) launch_predict_rhs_mx(g, h->mc, M, h->ms, h->d_ubc, h->d_inh, h->d_inl, h->d_ctl, h->st);
+            if (h->mixed)
+                launch_predict_rhs_mx(g, h->mc, M, h->ms, h->d_ubc, h->d_inh, h->d_inl, h->d_ctl, h->pt.red,
+                                      h->nfluid, h->st);
             else launch_rhs(g, M, h->d_us, h->d_vs, h->pb.b, h->d_ctl, h->st);
             return 0;
         default:

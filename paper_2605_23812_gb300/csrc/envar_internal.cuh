@@ -93,6 +93,7 @@ struct MixState {
     float *Ru, *Rv;                 // tendencies (FP32, AB2), two buffers each: +0 and +rstride
     long long rstride;              // offset of the second tendency buffer (elements)
     float *bh, *bl, *xh, *xl;       // Poisson right-hand side and solution (df64)
+    float *xp;                      // previous pressure increment, re-centred (FP32; guess extrapolation)
     float *wf;                      // Welford per member: 6 planes (mean_u, mean_v, M2; hi/lo)
     float *wd;                      // Welford of d = u - u_0 per member: 4 planes (mean_du, mean_dv, M2 hi/lo)
     float *frect;                   // member forcing on the control rectangle (FP32)
@@ -304,13 +305,17 @@ void launch_reset_mx(const Grid &g, int M, const MixState &ic, const MixState &s
 void launch_export_mx(const Grid &g, const MixState &s, long long off, double *uo, double *vo, double *po,
                       cudaStream_t st);
 void launch_outflow_mx(const Grid &g, int M, const MixState &s, double *ubc, MemberCtl *ctl, cudaStream_t st);
+// red, nfluid: the members' reductions (the fluid sum of the last increment) for the extrapolated
+// initial guess of the pressure increment (s.xp set), none without it.
 void launch_predict_rhs_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const double *ubc,
-                           const float *inh, const float *inl, const MemberCtl *ctl, cudaStream_t st);
+                           const float *inh, const float *inl, const MemberCtl *ctl, const MemberRed *red,
+                           long long nfluid, cudaStream_t st);
 void launch_outer_residual_mx(const Grid &g, const Level &L0, const MixConst &K, int M, const MixState &s, float *r,
                               float *e, const RedCtx &rc, MemberCtl *ctl, double rtol_abs, int count_it,
                               cudaStream_t st);
-void launch_outer_update_mx(const Grid &g, int M, const MixState &s, const float *e, const MemberCtl *ctl,
-                            cudaStream_t st);
+// The last inner CG update fused with the refinement's x += e (df64 x).
+void launch_axpy_last_mx(const Grid &g, int M, const MixState &s, const float *e, const float *p, const RedCtx &rc,
+                         MemberCtl *ctl, int k, cudaStream_t st);
 // ref: member 0's slot (its u*, v* and increment x are read for the Welford of d = u - u_0).
 void launch_correct_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const MixState &ref, double x0,
                        double y0, int want_welford, double *series, const Partials &pt, MemberCtl *ctl,

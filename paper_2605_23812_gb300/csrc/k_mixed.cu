@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(PR_TX *PR_TY) k_predict_rhs_mx(Grid g, MixCons
                                                                 const double *__restrict__ ubc,
                                                                 const float *__restrict__ inh,
                                                                 const float *__restrict__ inl,
-                                                                const MemberCtl *__restrict__ ctl)
+                                                                const MemberCtl *__restrict__ ctl,
+                                                                const MemberRed *__restrict__ red, float inv_nfluid)
 {
     __shared__ float suh[PR_TY][PR_TX + 1], sul[PR_TY][PR_TX + 1];
     __shared__ float svh[PR_TY + 1][PR_TX], svl[PR_TY + 1][PR_TX];
@@ -287,6 +288,16 @@ __global__ void __launch_bounds__(PR_TX *PR_TY) k_predict_rhs_mx(Grid g, MixCons
     if (i < g.nx && j < g.ny) {
         f2 b{0.f, 0.f};
         if (g.fluid[c]) {
+            // initial guess of this step's pressure increment (no other kernel of the step reads x yet)
+            if (s.xp && step >= 2) {
+                const float mean = (float)(red[m].val[RS_XSUM]) * inv_nfluid;
+                const f2 xr = df_add_f(f2{s.xh[off + c], s.xl[off + c]}, -mean);
+                f2 guess = xr;
+                if (step >= 3) guess = df_add_f(f2{2.f * xr.h, 2.f * xr.l}, -s.xp[off + c]);
+                s.xp[off + c] = xr.h;
+                s.xh[off + c] = guess.h;
+                s.xl[off + c] = guess.l;
+            }
             const f2 dU = df_sub(f2{suh[ty][tx + 1], sul[ty][tx + 1]}, f2{suh[ty][tx], sul[ty][tx]});
             const f2 dV = df_sub(f2{svh[ty + 1][tx], svl[ty + 1][tx]}, f2{svh[ty][tx], svl[ty][tx]});
             b = df_add(df_mul(dU, f2{K.kxh, K.kxl}), df_mul(dV, f2{K.kyh, K.kyl}));
@@ -298,48 +309,102 @@ __global__ void __launch_bounds__(PR_TX *PR_TY) k_predict_rhs_mx(Grid g, MixCons
 }
 
 void launch_predict_rhs_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const double *ubc,
-                           const float *inh, const float *inl, const MemberCtl *ctl, cudaStream_t st)
+                           const float *inh, const float *inl, const MemberCtl *ctl, const MemberRed *red,
+                           long long nfluid, cudaStream_t st)
 {
     dim3 blk(PR_TX, PR_TY), grd(cdiv(g.nx + 1, PR_TX), cdiv(g.ny + 1, PR_TY), M);
-    k_predict_rhs_mx<<<grd, blk, 0, st>>>(g, K, s, ubc, inh, inl, ctl);
+    k_predict_rhs_mx<<<grd, blk, 0, st>>>(g, K, s, ubc, inh, inl, ctl, red, (float)(1.0 / (double)nfluid));
     count_launches(1);
 }
 
 // ---------------------------------------------------------------------------- outer residual (df64)
-__global__ void __launch_bounds__(256) k_outer_residual_mx(Grid g, Level L0, MixConst K, const float *__restrict__ bh,
-                                                           const float *__restrict__ bl, const float *__restrict__ xh,
-                                                           const float *__restrict__ xl, float *__restrict__ r,
-                                                           float *__restrict__ e, RedCtx rc, MemberCtl *ctl,
-                                                           double rtol_abs, int count_it)
+// k_outer_residual_mx: r = b - A x in df64 on every fluid cell (FP32 r = its leading word; 0 on the
+// other cells), e = 0, and per member the maximum |r| and the fluid sum of x.  A warp owns a
+// 64-column strip of OR_ROWS rows, lane l the cell pair (2l, 2l+1): x of the rows below, at and
+// above the current one stays in registers, the east / west neighbours come from the neighbouring
+// lanes by shuffle (from memory at the strip's edges), and the level-0 open-face bits select the
+// operator's terms (an open face joins two fluid cells).
+constexpr int OR_ROWS = 8, OR_WARPS = 8;
+
+struct XPair { float2 h, l; };
+
+__global__ void __launch_bounds__(OR_WARPS * 32) k_outer_residual_mx(Grid g, Level L0, MixConst K,
+                                                                     const float *__restrict__ bh,
+                                                                     const float *__restrict__ bl,
+                                                                     const float *__restrict__ xh,
+                                                                     const float *__restrict__ xl,
+                                                                     float *__restrict__ r, float *__restrict__ e,
+                                                                     RedCtx rc, MemberCtl *ctl, double rtol_abs,
+                                                                     int count_it)
 {
     const int m = blockIdx.z;
     if (ctl[m].outer_done) return;
     const long long off = (long long)m * g.S;
-    const int i0 = blockIdx.x * TILE_W, j0 = blockIdx.y * TILE_H;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int iL = blockIdx.x * 64 + 2 * lane;
+    const bool colok = iL < g.nx;                               // nx is even: both cells of the pair
+    const int j0 = (blockIdx.y * OR_WARPS + w) * OR_ROWS;
+    const float *xhm = xh + off, *xlm = xl + off;
+    auto ld_x = [&](int j) -> XPair {                          // zeros outside the domain
+        XPair v{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (!colok || j < 0 || j >= g.ny) return v;
+        const long long c = (long long)j * g.P + iL;
+        v.h = *reinterpret_cast<const float2 *>(xhm + c);
+        v.l = *reinterpret_cast<const float2 *>(xlm + c);
+        return v;
+    };
+    auto ld_x1 = [&](int j, int i) -> f2 {
+        if (i < 0 || i >= g.nx) return f2{0.f, 0.f};
+        const long long c = (long long)j * g.P + i;
+        return f2{xhm[c], xlm[c]};
+    };
+    const f2 cx{K.cxh, K.cxl}, cy{K.cyh, K.cyl};
+    auto cell_r = [&](unsigned int ob, f2 xc, f2 xw, f2 xe, f2 xs_, f2 xn, f2 b) -> float {
+        f2 sx{0.f, 0.f}, sy{0.f, 0.f};
+        if (ob & 1u) sx = df_add(sx, df_sub(xc, xw));
+        if (ob & 2u) sx = df_add(sx, df_sub(xc, xe));
+        if (ob & 4u) sy = df_add(sy, df_sub(xc, xs_));
+        if (ob & 8u) sy = df_add(sy, df_sub(xc, xn));
+        const f2 ax = df_add(df_mul(sx, cx), df_mul(sy, cy));
+        return df_sub(b, ax).h;
+    };
     float rmax = 0.f;
     f2 xs{0.f, 0.f};
-#pragma unroll
-    for (int q = threadIdx.x; q < TILE_W * TILE_H; q += TILE_THREADS) {
-        int i = i0 + (q % TILE_W), j = j0 + (q / TILE_W);
-        if (i >= g.nx || j >= g.ny) continue;
-        long long c = (long long)j * g.P + i;
-        float rv = 0.f;
-        if (g.fluid[c]) {
-            const long long o = off + c;
-            f2 xc{xh[o], xl[o]};
-            f2 sx{0.f, 0.f}, sy{0.f, 0.f};
-            if (L0.cwf[c] != 0.f) sx = df_add(sx, df_sub(xc, f2{xh[o - 1], xl[o - 1]}));
-            if (L0.cwf[c + 1] != 0.f) sx = df_add(sx, df_sub(xc, f2{xh[o + 1], xl[o + 1]}));
-            if (L0.csf[c] != 0.f) sy = df_add(sy, df_sub(xc, f2{xh[o - g.P], xl[o - g.P]}));
-            if (L0.csf[c + g.P] != 0.f) sy = df_add(sy, df_sub(xc, f2{xh[o + g.P], xl[o + g.P]}));
-            f2 ax = df_add(df_mul(sx, f2{K.cxh, K.cxl}), df_mul(sy, f2{K.cyh, K.cyl}));
-            f2 res = df_sub(f2{bh[o], bl[o]}, ax);
-            rv = res.h;
-            rmax = fmaxf(rmax, fabsf(rv));
-            xs = df_add_f(xs, xc.h);
+    if (j0 < g.ny) {
+        XPair xS = ld_x(j0 - 1), xC = ld_x(j0);
+#pragma unroll 2
+        for (int rr = 0; rr < OR_ROWS; ++rr) {
+            const int j = j0 + rr;
+            if (j >= g.ny) break;
+            const XPair xN = ld_x(j + 1);
+            f2 xw{__shfl_up_sync(0xffffffffu, xC.h.y, 1), __shfl_up_sync(0xffffffffu, xC.l.y, 1)};
+            f2 xe{__shfl_down_sync(0xffffffffu, xC.h.x, 1), __shfl_down_sync(0xffffffffu, xC.l.x, 1)};
+            if (lane == 0) xw = ld_x1(j, iL - 1);
+            if (lane == 31) xe = ld_x1(j, iL + 2);
+            if (colok) {
+                const long long c = (long long)j * g.P + iL;
+                const unsigned int ob = *reinterpret_cast<const unsigned short *>(L0.open + c);
+                const unsigned int fl = *reinterpret_cast<const unsigned short *>(g.fluid + c);
+                const float2 b0 = *reinterpret_cast<const float2 *>(bh + off + c);
+                const float2 b1 = *reinterpret_cast<const float2 *>(bl + off + c);
+                const f2 x0{xC.h.x, xC.l.x}, x1{xC.h.y, xC.l.y};
+                float2 rv = make_float2(0.f, 0.f);
+                if (fl & 0xffu) {
+                    rv.x = cell_r(ob & 15u, x0, xw, x1, f2{xS.h.x, xS.l.x}, f2{xN.h.x, xN.l.x}, f2{b0.x, b1.x});
+                    rmax = fmaxf(rmax, fabsf(rv.x));
+                    xs = df_add_f(xs, x0.h);
+                }
+                if (fl >> 8) {
+                    rv.y = cell_r((ob >> 8) & 15u, x1, x0, xe, f2{xS.h.y, xS.l.y}, f2{xN.h.y, xN.l.y}, f2{b0.y, b1.y});
+                    rmax = fmaxf(rmax, fabsf(rv.y));
+                    xs = df_add_f(xs, x1.h);
+                }
+                *reinterpret_cast<float2 *>(r + off + c) = rv;
+                *reinterpret_cast<float2 *>(e + off + c) = make_float2(0.f, 0.f);
+            }
+            xS = xC;
+            xC = xN;
         }
-        r[off + c] = rv;
-        e[off + c] = 0.f;
     }
     double rm = (double)block_max_f(rmax);
     double xsum = block_sum_df(xs);
@@ -357,40 +422,59 @@ __global__ void __launch_bounds__(256) k_outer_residual_mx(Grid g, Level L0, Mix
     if (last2 && threadIdx.x == 0) rc.red[m].val[RS_XSUM] = tot;
 }
 
-__global__ void __launch_bounds__(256) k_outer_update_mx(Grid g, float *__restrict__ xh, float *__restrict__ xl,
-                                                         const float *__restrict__ e, const MemberCtl *ctl)
+// k_axpy_last_mx: the last inner CG update fused with the refinement's update of x: e + alpha p is
+// formed in registers and added to x in df64 (x += e) on the cells where it is nonzero (the fluid
+// cells: e and p vanish elsewhere); r, and e itself, are not needed after the last inner
+// iteration.  A member whose inner loop already stopped (inner_done) only takes x += e.  Four
+// values per thread (two aligned pairs), pointwise.
+__global__ void __launch_bounds__(128) k_axpy_last_mx(Grid g, float *__restrict__ xh, float *__restrict__ xl,
+                                                      const float *__restrict__ e, const float *__restrict__ p,
+                                                      RedCtx rc, MemberCtl *ctl, int k)
 {
     const int m = blockIdx.z;
     if (ctl[m].outer_done) return;
-    const long long off = (long long)m * g.S;
-    const int i0 = blockIdx.x * TILE_W, j0 = blockIdx.y * TILE_H;
+    const bool moving = !ctl[m].inner_done;
+    float a = 0.f;
+    if (moving) a = (float)(rc.red[m].val[(k & 1) ? RS_RZB : RS_RZA] / rc.red[m].val[RS_PQ]);
+    const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y;
+    if (i < g.nx) {
+        const long long c = (long long)m * g.S + (long long)j * g.P + i;
 #pragma unroll
-    for (int q = threadIdx.x; q < TILE_W * TILE_H; q += TILE_THREADS) {
-        int i = i0 + (q % TILE_W), j = j0 + (q / TILE_W);
-        if (i >= g.nx || j >= g.ny) continue;
-        long long c = (long long)j * g.P + i;
-        if (!g.fluid[c]) continue;
-        f2 x = df_add_f(f2{xh[off + c], xl[off + c]}, e[off + c]);
-        xh[off + c] = x.h;
-        xl[off + c] = x.l;
+        for (int h = 0; h < 4; h += 2) {
+            if (i + h >= g.nx) break;                           // nx is even: pairs are whole
+            float2 ev = *reinterpret_cast<const float2 *>(e + c + h);
+            if (moving) {
+                const float2 pv = *reinterpret_cast<const float2 *>(p + c + h);
+                ev.x += a * pv.x;
+                ev.y += a * pv.y;
+            }
+            if (ev.x != 0.f || ev.y != 0.f) {
+                float2 x0 = *reinterpret_cast<const float2 *>(xh + c + h), x1 = *reinterpret_cast<const float2 *>(xl + c + h);
+                if (ev.x != 0.f) { const f2 s = df_add_f(f2{x0.x, x1.x}, ev.x); x0.x = s.h; x1.x = s.l; }
+                if (ev.y != 0.f) { const f2 s = df_add_f(f2{x0.y, x1.y}, ev.y); x0.y = s.h; x1.y = s.l; }
+                *reinterpret_cast<float2 *>(xh + c + h) = x0;
+                *reinterpret_cast<float2 *>(xl + c + h) = x1;
+            }
+        }
     }
+    if (moving && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctl[m].inner_its += 1;
 }
 
 void launch_outer_residual_mx(const Grid &g, const Level &L0, const MixConst &K, int M, const MixState &s, float *r,
                               float *e, const RedCtx &rc, MemberCtl *ctl, double rtol_abs, int count_it,
                               cudaStream_t st)
 {
-    dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
-    k_outer_residual_mx<<<grd, TILE_THREADS, 0, st>>>(g, L0, K, s.bh, s.bl, s.xh, s.xl, r, e, rc, ctl, rtol_abs,
-                                                     count_it);
+    dim3 grd(cdiv(g.nx, 64), cdiv(g.ny, OR_WARPS * OR_ROWS), M);
+    k_outer_residual_mx<<<grd, OR_WARPS * 32, 0, st>>>(g, L0, K, s.bh, s.bl, s.xh, s.xl, r, e, rc, ctl, rtol_abs,
+                                                       count_it);
     count_launches(1);
 }
 
-void launch_outer_update_mx(const Grid &g, int M, const MixState &s, const float *e, const MemberCtl *ctl,
-                            cudaStream_t st)
+void launch_axpy_last_mx(const Grid &g, int M, const MixState &s, const float *e, const float *p, const RedCtx &rc,
+                         MemberCtl *ctl, int k, cudaStream_t st)
 {
-    dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
-    k_outer_update_mx<<<grd, TILE_THREADS, 0, st>>>(g, s.xh, s.xl, e, ctl);
+    dim3 grd(cdiv(cdiv(g.nx, 4), 128), g.ny, M);
+    k_axpy_last_mx<<<grd, 128, 0, st>>>(g, s.xh, s.xl, e, p, rc, ctl, k);
     count_launches(1);
 }
 

@@ -341,6 +341,7 @@ struct SmoothArgs {
     int order;            // 0: red then black; 1: black then red
     int flags;
     int k;                // inner iteration (for the dot slot)
+    double rtol2;         // SF_DOT: the inner loop stops once r^T z <= rtol2 (r^T z)_0
 };
 
 // Thread layout: a block of 384 threads covers a 64 x 42 region (tile + halo); each thread owns a
@@ -489,6 +490,8 @@ __global__ void __launch_bounds__(SC_THREADS, sizeof(T) == 4 ? 2 : 1) k_smooth(S
             if (sa.flags & SF_INIT_DOT) {
                 rc.red[m].val[RS_RZ0] = tot;
                 if (!(tot > 0.0)) ctl[m].inner_done = 1;
+            } else if (!(tot > sa.rtol2 * rc.red[m].val[RS_RZ0])) {
+                ctl[m].inner_done = 1;   // inner convergence, decided where the total is formed
             }
         }
     }
@@ -731,6 +734,8 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
             if (sa.flags & SF_INIT_DOT) {
                 rc.red[m].val[RS_RZ0] = tot;
                 if (!(tot > 0.0)) ctl[m].inner_done = 1;
+            } else if (!(tot > sa.rtol2 * rc.red[m].val[RS_RZ0])) {
+                ctl[m].inner_done = 1;   // inner convergence, decided where the total is formed
             }
         }
     }
@@ -959,17 +964,6 @@ static size_t coarse_args(const Level *lev, const PoissonCfg &pc, int inner_guar
 }
 
 // ------------------------------------------------------------------------------------------------
-// Inner convergence flag after the V-cycle's dot: set by a one-warp kernel per member.
-__global__ void k_inner_check(RedCtx rc, MemberCtl *ctl, int k, double rtol2, int M)
-{
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= M) return;
-    if (ctl[m].outer_done || ctl[m].inner_done) return;
-    double rz = rc.red[m].val[((k + 1) & 1) ? RS_RZB : RS_RZA];
-    if (!(rz > rtol2 * rc.red[m].val[RS_RZ0])) ctl[m].inner_done = 1;
-}
-
-// ------------------------------------------------------------------------------------------------
 template <class T, bool BIN>
 static void launch_smooth_b(int M, int nsweep, cudaStream_t st, const SmoothArgs &sa, const T *f, const T *ein, T *e,
                             const T *ec, T *fc, const RedCtx &rc, MemberCtl *ctl, int inner_guard)
@@ -1064,7 +1058,7 @@ static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B,
         const Level &Lc = lev[l + 1];
         int flags = SF_PROLONG;
         if (l == 0) flags |= init ? SF_INIT_DOT : SF_DOT;
-        SmoothArgs sa{L, Lc.P, Lc.S, pc.nu_post, 1, flags, k};
+        SmoothArgs sa{L, Lc.P, Lc.S, pc.nu_post, 1, flags, k, pc.inner_rtol2};
         const T *f = (l == 0) ? f0 : (const T *)B.lev_f[l];
         T *e = (l == 0) ? z : (T *)B.lev_e[l];
         launch_smooth<T>(M, pc.nu_post, st, sa, f, (const T *)B.lev_t[l], e, (const T *)B.lev_e[l + 1], (T *)nullptr,
@@ -1150,15 +1144,19 @@ static void refinement(const Grid &g, const Level *lev, int M, const PoissonBufs
     vcycle<TM>(g, lev, M, B, pc, rc, ctl, 0, 0, 1, st);
     for (int k = 0; k < pc.max_inner; ++k) {
         launch_spmv<TM>(g, L0, M, z, pv[k & 1], pv[(k + 1) & 1], q, rc, ctl, k, st);
-        launch_axpy<TM>(g, M, e, r, pv[(k + 1) & 1], q, rc, ctl, k, st);
-        count_launches(2);
-        if (k + 1 == pc.max_inner) break;   // the last update needs no new preconditioned residual
-        vcycle<TM>(g, lev, M, B, pc, rc, ctl, 1, k, 0, st);
-        k_inner_check<<<cdiv(M, 32), 32, 0, st>>>(rc, ctl, k, pc.inner_rtol2, M);
         count_launches(1);
+        if (k + 1 == pc.max_inner && pc.df_outer) {
+            // df64 x: the last update goes straight into x (x += e + alpha p), r is not needed
+            launch_axpy_last_mx(g, M, B.ms, (const float *)e, (const float *)pv[(k + 1) & 1], rc, ctl, k, st);
+            return;
+        }
+        launch_axpy<TM>(g, M, e, r, pv[(k + 1) & 1], q, rc, ctl, k, st);
+        count_launches(1);
+        if (k + 1 == pc.max_inner) break;   // the last update needs no new preconditioned residual
+        vcycle<TM>(g, lev, M, B, pc, rc, ctl, 1, k, 0, st);   // also decides inner convergence
     }
     if (pc.df_outer) {
-        launch_outer_update_mx(g, M, B.ms, (const float *)e, ctl, st);
+        return;   // max_inner == 0: nothing to add
     } else {
         dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
         k_outer_update<TM><<<grd, TILE_THREADS, 0, st>>>(g, B.x, e, ctl);
@@ -1249,7 +1247,7 @@ int launch_poisson_single(int which, const Grid &g, const Level *lev, int M, con
         return 0;
     }
     case 2: {
-        SmoothArgs sa{L0, L1.P, L1.S, pc.nu_post, 1, SF_PROLONG | SF_DOT, 1};
+        SmoothArgs sa{L0, L1.P, L1.S, pc.nu_post, 1, SF_PROLONG | SF_DOT, 1, pc.inner_rtol2};
         launch_smooth<TM>(M, pc.nu_post, st, sa, r, (const TM *)B.lev_t[0], z, (const TM *)B.lev_e[1], (TM *)nullptr,
                           rc, ctl, 0);
         return 0;
