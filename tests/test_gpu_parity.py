@@ -390,6 +390,32 @@ def test_conditional_refinement_loop_is_exact_and_skips_work(precision):
     assert l1 < 0.8 * l0, (l0, l1)
 
 
+def test_extrapolated_initial_guess_changes_only_the_refinement_count():
+    """MIXED: the pressure increment's initial guess 2 dp^n - dp^(n-1) against the last increment
+    alone, at the bench grid over 300 steps with the tuned solver.  Every solve ends at div_tol
+    either way, so costs and gradients agree to the solver's accuracy (the trajectories differ by
+    the divergence tolerance only), and the extrapolated guess needs fewer refinements."""
+    nx, ny, N, n = 512, 256, 8, 300
+    out = []
+    for ex in (0, 1):
+        cfg = pkg.default_config(nx, ny, Re=7500.0, n_steps=n, n_window=n // 2, n_members=N, precision=pkg.MIXED,
+                                 guess_extrapolation=ex, max_outer=10, max_inner=2, coarse_sweeps=1, inner_rtol=1e-3)
+        cfg.nu_pre = cfg.nu_post = 3
+        ens = pkg.Ensemble(cfg)
+        ens.set_initial_state(*synth.cavity_ic(nx, ny))
+        ens.forward_ensemble(synth.weights(N))
+        J, _ = ens.cost()
+        d = ens.diagnostics()
+        out.append((J, ens.gradient(), d["outer_its"], d["max_div"]))
+        assert (ens.member_status() == 0).all()
+        ens.close()
+    (J0, g0, o0, d0), (J1, g1, o1, d1) = out
+    assert d0 <= 1e-10 and d1 <= 1e-10
+    np.testing.assert_allclose(J1, J0, rtol=1e-6)
+    assert np.linalg.norm(g1 - g0) <= 1e-5 * np.linalg.norm(g0)
+    assert o1 < 0.9 * o0, (o0, o1)
+
+
 def test_chaotic_configuration_statistics_mixed_against_fp64():
     """The chaotic-regime configuration (1024x512, Re 15000) shortened to 600 + 600 steps with N = 8:
     the mixed-precision batched path against the FP64 batched path (itself tied to the oracle at
