@@ -870,7 +870,8 @@ extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda
         c.precision < 0 || c.precision > 2 || c.cost_mode < 0 || c.cost_mode > 1 || !(c.div_tol > 0) ||
         c.max_outer < 1 || c.max_inner < 1 || c.nu_pre < 1 || c.nu_pre > 3 || c.nu_post < 1 || c.nu_post > 3 ||
         c.coarse_sweeps < 1 || c.steps_per_graph < 1 || !(c.x1 > c.x0) || !(c.y1 > c.y0) || !(c.inner_rtol > 0) ||
-        c.member_groups < 0 || c.member_groups > ENVAR_MAX_GROUPS) {
+        c.member_groups < 0 || c.member_groups > ENVAR_MAX_GROUPS || c.guess_extrapolation < 0 ||
+        c.guess_extrapolation > 1) {
         set_err(nullptr, "envar_init: invalid configuration");
         return ENVAR_EINVAL;
     }

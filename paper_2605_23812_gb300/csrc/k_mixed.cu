@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(PR_TX *PR_TY) k_predict_rhs_mx(Grid g, MixCons
             if (s.xp && step >= 2) {
                 const float mean = (float)(red[m].val[RS_XSUM]) * inv_nfluid;
                 const f2 xr = df_add_f(f2{s.xh[off + c], s.xl[off + c]}, -mean);
-                f2 guess = xr;
+                f2 guess = xr;                                // from the third step: 2 dp^n - dp^(n-1)
                 if (step >= 3) guess = df_add_f(f2{2.f * xr.h, 2.f * xr.l}, -s.xp[off + c]);
                 s.xp[off + c] = xr.h;
                 s.xh[off + c] = guess.h;
