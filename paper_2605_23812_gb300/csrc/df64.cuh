@@ -63,6 +63,7 @@ __device__ __forceinline__ f2 df_mul_f(f2 a, float b)
 }
 __device__ __forceinline__ f2 df_scale_half(f2 a) { return {0.5f * a.h, 0.5f * a.l}; }
 __device__ __forceinline__ double df_to_d(f2 a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ double to_dbl(f2 a) { return df_to_d(a); }
 __device__ __forceinline__ f2 d_to_df(double d)
 {
     float h = (float)d;
@@ -88,8 +89,9 @@ __device__ __forceinline__ f2 warp_sum_df(f2 v)
     return v;
 }
 
-// Block-wide df64 sum returned as a double in every thread (one FP64 add per warp).
-__device__ __forceinline__ double block_sum_df(f2 v)
+// Block-wide df64 sum returned as a df64 pair in every thread (converted to double where it is
+// published, by one thread).
+__device__ __forceinline__ f2 block_sum_df(f2 v)
 {
     __shared__ f2 red_df[33];
     int t = threadIdx.x + threadIdx.y * blockDim.x;
@@ -104,7 +106,7 @@ __device__ __forceinline__ double block_sum_df(f2 v)
         if (t == 0) red_df[32] = w;
     }
     __syncthreads();
-    double r = df_to_d(red_df[32]);
+    const f2 r = red_df[32];
     __syncthreads();
     return r;
 }

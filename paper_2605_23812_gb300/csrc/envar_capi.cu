@@ -326,7 +326,7 @@ static int build_geometry(envar_handle h)
         CK(cudaMemcpy(csf, f2.data(), sizeof(float) * L.S, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(cwd, L.cw.data(), sizeof(double) * L.S, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(csd, L.cs.data(), sizeof(double) * L.S, cudaMemcpyHostToDevice));
-        h->lev[l] = Level{L.nx, L.ny, L.P, L.S, dfl, cwf, csf, cwd, csd, nullptr, 0.0, 0.0, nullptr, nullptr, nullptr};
+        h->lev[l] = Level{L.nx, L.ny, L.P, L.S, dfl, cwf, csf, cwd, csd, nullptr, 0.0, 0.0, 0.f, 0.f, nullptr, nullptr, nullptr};
         if (l == 0 || L.nx % 2) continue;   // the coded smoother works on cell pairs
         // conductance codes: the distinct conductances of each direction in first-seen order
         std::vector<double> tx, ty;
@@ -400,6 +400,8 @@ static int build_geometry(envar_handle h)
         h->lev[0].open = dop;
         h->lev[0].cx = g.cx;
         h->lev[0].cy = g.cy;
+        h->lev[0].cxf = (float)g.cx;
+        h->lev[0].cyf = (float)g.cy;
     }
     // coarse block must fit in shared memory
     if (coarse_bytes(h->ncoarse) > (size_t)COARSE_SMEM_MAX) {

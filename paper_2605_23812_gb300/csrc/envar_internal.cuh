@@ -36,6 +36,7 @@ struct Level {
     const double *csd;
     const uint8_t *open;    // level 0 only: open-face bits (1 W, 2 E, 4 S, 8 N) of fluid cells
     double cx, cy;          // level 0 only: conductance of an open x / y face
+    float cxf, cyf;         // level 0 only: the same in FP32
     // levels >= 1 with at most 16 distinct conductances per direction: per cell the table indices
     // of its W, E, S, N faces (4 bits each, W lowest) and the tables [x faces 0..15 | y faces 0..15]
     const uint16_t *code;
@@ -77,6 +78,10 @@ enum RedSlot { RS_RMAX = 0, RS_XSUM = 1, RS_RZ0 = 2, RS_RZA = 3, RS_RZB = 4, RS_
 struct MemberRed {
     unsigned int cnt[RS_COUNT];   // arrival tickets
     double val[RS_COUNT];         // max |r| (outer residual), sum x, r^T z (start, ping, pong), p^T A p
+    // FP32 inner CG: alpha = (r^T z)_k / p^T A p and beta = (r^T z)_k / (r^T z)_(k-1), each formed once
+    // by the block that completes its last total (a double division in every thread would occupy
+    // the FP64 pipe, about 1/64 of the FP32 rate, for longer than the kernel's memory traffic)
+    float fa, fb;
 };
 struct Partials {
     int nblk;               // partial slots per member (>= blocks per member of any producing kernel)
@@ -160,17 +165,23 @@ struct RedCtx {
 };
 static inline RedCtx make_ctx(const Partials &pt) { return RedCtx{pt.nblk, pt.part, pt.red, pt.stride}; }
 
+__device__ __forceinline__ double to_dbl(double v) { return v; }
+__device__ __forceinline__ double to_dbl(float v) { return (double)v; }
+
 // Publish a block partial of a per-member scalar; the blocks of one member are the kernel's
 // blockIdx.x/y grid.  Returns true in the (single) last block to arrive, whose thread 0 then holds
-// the fixed-order total in *total (sum, or max when is_max).
-__device__ __forceinline__ bool publish_partial(const RedCtx &rc, int slot, int m, double v, bool is_max, double *total)
+// the fixed-order total in *total (sum, or max when is_max).  v is read in thread 0 only, where it
+// is converted to double (a float, a double, or a df64 pair), so the other threads issue no FP64
+// instruction for it.
+template <class V>
+__device__ __forceinline__ bool publish_partial(const RedCtx &rc, int slot, int m, V v, bool is_max, double *total)
 {
     __shared__ bool s_last;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nb = gridDim.x * gridDim.y;
     double *p = rc.part + ((long long)slot * rc.stride + m) * rc.nblk;
     if (tid == 0) {
-        p[blockIdx.x + blockIdx.y * gridDim.x] = v;
+        p[blockIdx.x + blockIdx.y * gridDim.x] = to_dbl(v);
         __threadfence();
         unsigned int t = atomicAdd(&rc.red[m].cnt[slot], 1u);
         s_last = (t == (unsigned int)nb - 1);

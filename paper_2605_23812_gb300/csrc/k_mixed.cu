@@ -240,7 +240,7 @@ __device__ __forceinline__ f2 vstar_mx(const Grid &g, const MixConst &K, const M
 // the four faces of b = -(dy (u*_E - u*_W) + dx (v*_N - v*_S)) / dt (df64, zero in solid cells)
 // on chip; the right-hand side never re-reads u*, v*.
 constexpr int PR_TX = 32, PR_TY = 8;
-__global__ void __launch_bounds__(PR_TX *PR_TY) k_predict_rhs_mx(Grid g, MixConst K, MixState s,
+__global__ void __launch_bounds__(PR_TX *PR_TY, 6) k_predict_rhs_mx(Grid g, MixConst K, MixState s,
                                                                 const double *__restrict__ ubc,
                                                                 const float *__restrict__ inh,
                                                                 const float *__restrict__ inl,
@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(PR_TX *PR_TY) k_predict_rhs_mx(Grid g, MixCons
 {
     __shared__ float suh[PR_TY][PR_TX + 1], sul[PR_TY][PR_TX + 1];
     __shared__ float svh[PR_TY + 1][PR_TX], svl[PR_TY + 1][PR_TX];
+    __shared__ float s_xmean;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i0 = blockIdx.x * PR_TX, j0 = blockIdx.y * PR_TY;
     const int i = i0 + tx, j = j0 + ty;
@@ -259,6 +260,11 @@ __global__ void __launch_bounds__(PR_TX *PR_TY) k_predict_rhs_mx(Grid g, MixCons
     const float c1 = first ? 1.f : 1.5f, c0 = first ? 0.f : -0.5f;
     const RBuf R = rbuf(s, off, step);
     const long long c = (long long)j * g.P + i;
+    // the fluid sum of the last increment: loaded by one thread at entry, stored to shared memory
+    // after the face updates (its latency overlaps them), read after the barrier
+    const bool lead = tx == 0 && ty == 0 && s.xp && step >= 2;
+    double xsum = 0.0;
+    if (lead) xsum = __ldcg(&red[m].val[RS_XSUM]);
     if (i <= g.nx && j < g.ny) {
         const f2 u = ustar_mx(g, K, s, off, m, i, j, R.uin, R.uout, ubc, inh, inl, c1, c0);
         s.ush[off + c] = u.h; s.usl[off + c] = u.l;
@@ -284,14 +290,14 @@ __global__ void __launch_bounds__(PR_TX *PR_TY) k_predict_rhs_mx(Grid g, MixCons
             svh[PR_TY][tx] = v.h; svl[PR_TY][tx] = v.l;
         }
     }
+    if (lead) s_xmean = (float)xsum * inv_nfluid;
     __syncthreads();
     if (i < g.nx && j < g.ny) {
         f2 b{0.f, 0.f};
         if (g.fluid[c]) {
             // initial guess of this step's pressure increment (no other kernel of the step reads x yet)
             if (s.xp && step >= 2) {
-                const float mean = (float)(red[m].val[RS_XSUM]) * inv_nfluid;
-                const f2 xr = df_add_f(f2{s.xh[off + c], s.xl[off + c]}, -mean);
+                const f2 xr = df_add_f(f2{s.xh[off + c], s.xl[off + c]}, -s_xmean);
                 f2 guess = xr;                                // from the third step: 2 dp^n - dp^(n-1)
                 if (step >= 3) guess = df_add_f(f2{2.f * xr.h, 2.f * xr.l}, -s.xp[off + c]);
                 s.xp[off + c] = xr.h;
@@ -406,8 +412,8 @@ __global__ void __launch_bounds__(OR_WARPS * 32) k_outer_residual_mx(Grid g, Lev
             xC = xN;
         }
     }
-    double rm = (double)block_max_f(rmax);
-    double xsum = block_sum_df(xs);
+    const float rm = block_max_f(rmax);
+    const f2 xsum = block_sum_df(xs);
     double tot;
     bool last1 = publish_partial(rc, RS_RMAX, m, rm, true, &tot);
     if (last1 && threadIdx.x == 0) {
@@ -434,8 +440,7 @@ __global__ void __launch_bounds__(128) k_axpy_last_mx(Grid g, float *__restrict_
     const int m = blockIdx.z;
     if (ctl[m].outer_done) return;
     const bool moving = !ctl[m].inner_done;
-    float a = 0.f;
-    if (moving) a = (float)(rc.red[m].val[(k & 1) ? RS_RZB : RS_RZA] / rc.red[m].val[RS_PQ]);
+    const float a = moving ? rc.red[m].fa : 0.f;   // alpha of this iteration, formed by the SpMV
     const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y;
     if (i < g.nx) {
         const long long c = (long long)m * g.S + (long long)j * g.P + i;
@@ -571,7 +576,7 @@ __device__ __forceinline__ void welford2_diff(float a, float b, int n, float *w,
     w[2 * S + c] = m2.h; w[3 * S + c] = m2.l;
 }
 
-__global__ void __launch_bounds__(256) k_correct_mx(Grid g, MixConst K, MixState s, MixState ref, double x0, double y0,
+__global__ void __launch_bounds__(256, 5) k_correct_mx(Grid g, MixConst K, MixState s, MixState ref, double x0, double y0,
                                                     int want_welford, double *__restrict__ series, Partials pt,
                                                     MemberCtl *ctl, double div_tol, long long nfluid)
 {

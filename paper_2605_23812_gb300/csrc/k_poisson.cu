@@ -30,7 +30,7 @@ template <> struct DotAcc<float> {
     __device__ __forceinline__ void add(float a, float b) { v = df_add(v, two_prod(a, b)); }
     // a0 b0 + a1 b1 rounded once in FP32 (the pair of a lane's cells), then added exactly
     __device__ __forceinline__ void add_pair(float a0, float b0, float a1, float b1) { v = df_add_f(v, fmaf(a0, b0, a1 * b1)); }
-    __device__ __forceinline__ double total() { return block_sum_df(v); }
+    __device__ __forceinline__ f2 total() { return block_sum_df(v); }
 };
 template <> struct DotAcc<double> {
     double v = 0.0;
@@ -38,6 +38,40 @@ template <> struct DotAcc<double> {
     __device__ __forceinline__ void add_pair(double a0, double b0, double a1, double b1) { v = fma(a0, b0, fma(a1, b1, v)); }
     __device__ __forceinline__ double total() { return block_reduce(v, false); }
 };
+
+// Level-0 conductances in the vectors' precision.
+template <class T> __device__ __forceinline__ T lev0_cx(const Level &L);
+template <> __device__ __forceinline__ float lev0_cx<float>(const Level &L) { return L.cxf; }
+template <> __device__ __forceinline__ double lev0_cx<double>(const Level &L) { return L.cx; }
+template <class T> __device__ __forceinline__ T lev0_cy(const Level &L);
+template <> __device__ __forceinline__ float lev0_cy<float>(const Level &L) { return L.cyf; }
+template <> __device__ __forceinline__ double lev0_cy<double>(const Level &L) { return L.cy; }
+
+// Inner CG scalars.  FP32 vectors read the FP32 copies formed once per member by the block that
+// completes the total (set_alpha, set_beta: one thread); FP64 vectors divide in FP64.
+__device__ __forceinline__ int rz_slot(int k) { return (k & 1) ? RS_RZB : RS_RZA; }
+template <class T> __device__ __forceinline__ T cg_alpha(const RedCtx &rc, int m, int k);
+template <> __device__ __forceinline__ float cg_alpha<float>(const RedCtx &rc, int m, int) { return rc.red[m].fa; }
+template <> __device__ __forceinline__ double cg_alpha<double>(const RedCtx &rc, int m, int k)
+{
+    return rc.red[m].val[rz_slot(k)] / rc.red[m].val[RS_PQ];
+}
+template <class T> __device__ __forceinline__ T cg_beta(const RedCtx &rc, int m, int k);
+template <> __device__ __forceinline__ float cg_beta<float>(const RedCtx &rc, int m, int) { return rc.red[m].fb; }
+template <> __device__ __forceinline__ double cg_beta<double>(const RedCtx &rc, int m, int k)
+{
+    return rc.red[m].val[rz_slot(k)] / rc.red[m].val[rz_slot(k + 1)];
+}
+// p^T A p of iteration k complete: alpha_k = (r^T z)_k / p^T A p
+__device__ __forceinline__ void set_alpha(const RedCtx &rc, int m, int k, double pq)
+{
+    rc.red[m].fa = (float)(rc.red[m].val[rz_slot(k)] / pq);
+}
+// (r^T z)_(k+1) complete (slot rz_slot(k + 1)): beta_(k+1) = (r^T z)_(k+1) / (r^T z)_k
+__device__ __forceinline__ void set_beta(const RedCtx &rc, int m, int k, double rz)
+{
+    rc.red[m].fb = (float)(rz / rc.red[m].val[rz_slot(k)]);
+}
 
 // ------------------------------------------------------------------------------------------------
 // outer FP64 residual:  r = b - A x  (written in TM as the inner right-hand side), e = 0,
@@ -118,13 +152,7 @@ __global__ void __launch_bounds__(256) k_spmv(Grid g, Level L0, const TM *__rest
     const int m = blockIdx.z;
     if (ctl[m].outer_done || ctl[m].inner_done) return;
     const long long off = (long long)m * g.S;
-    double beta = 0.0;
-    if (k > 0) {
-        double rzk = rc.red[m].val[(k & 1) ? RS_RZB : RS_RZA];
-        double rzp = rc.red[m].val[(k & 1) ? RS_RZA : RS_RZB];
-        beta = rzk / rzp;
-    }
-    const TM bt = (TM)beta;
+    const TM bt = (k > 0) ? cg_beta<TM>(rc, m, k) : (TM)0;
     const int i0 = blockIdx.x * TILE_W, j0 = blockIdx.y * TILE_H;
     const TM *zm = z + off, *pm = pold + off;
     DotAcc<TM> pq;
@@ -149,10 +177,11 @@ __global__ void __launch_bounds__(256) k_spmv(Grid g, Level L0, const TM *__rest
         pnew[off + c] = pc;
         q[off + c] = qv;
     }
-    double pqt = pq.total();
+    const auto pqt = pq.total();
     double tot;
     if (publish_partial(rc, RS_PQ, m, pqt, false, &tot) && threadIdx.x == 0) {
         rc.red[m].val[RS_PQ] = tot;
+        set_alpha(rc, m, k, tot);
         if (!(tot > 0.0)) ctl[m].inner_done = 1;   // breakdown: stop this member's inner loop
     }
 }
@@ -165,8 +194,7 @@ __global__ void __launch_bounds__(256) k_axpy(Grid g, TM *__restrict__ e, TM *__
     const int m = blockIdx.z;
     if (ctl[m].outer_done || ctl[m].inner_done) return;
     const long long off = (long long)m * g.S;
-    const double alpha = rc.red[m].val[(k & 1) ? RS_RZB : RS_RZA] / rc.red[m].val[RS_PQ];
-    const TM a = (TM)alpha;
+    const TM a = cg_alpha<TM>(rc, m, k);
     const int i0 = blockIdx.x * TILE_W, j0 = blockIdx.y * TILE_H;
 #pragma unroll
     for (int qq = threadIdx.x; qq < TILE_W * TILE_H; qq += TILE_THREADS) {
@@ -203,14 +231,8 @@ __global__ void __launch_bounds__(SPMV_WARPS * 32) k_spmv0(Grid g, Level L0, con
     const int m = blockIdx.z;
     if (ctl[m].outer_done || ctl[m].inner_done) return;
     const long long off = (long long)m * g.S;
-    double beta = 0.0;
-    if (k > 0) {
-        double rzk = rc.red[m].val[(k & 1) ? RS_RZB : RS_RZA];
-        double rzp = rc.red[m].val[(k & 1) ? RS_RZA : RS_RZB];
-        beta = rzk / rzp;
-    }
-    const T bt = (T)beta;
-    const T cx = (T)L0.cx, cy = (T)L0.cy;
+    const T bt = (k > 0) ? cg_beta<T>(rc, m, k) : (T)0;
+    const T cx = lev0_cx<T>(L0), cy = lev0_cy<T>(L0);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int iL = blockIdx.x * 64 + 2 * lane;
     const bool colok = iL + 1 < g.nx;                       // nx is even
@@ -258,10 +280,11 @@ __global__ void __launch_bounds__(SPMV_WARPS * 32) k_spmv0(Grid g, Level L0, con
             pC = pN;
         }
     }
-    double pqt = pq.total();
+    const auto pqt = pq.total();
     double tot;
     if (publish_partial(rc, RS_PQ, m, pqt, false, &tot) && threadIdx.x == 0) {
         rc.red[m].val[RS_PQ] = tot;
+        set_alpha(rc, m, k, tot);
         if (!(tot > 0.0)) ctl[m].inner_done = 1;   // breakdown: stop this member's inner loop
     }
 }
@@ -275,8 +298,7 @@ __global__ void __launch_bounds__(128) k_axpy4(Grid g, T *__restrict__ e, T *__r
     using T2 = typename Pair2Of<T>::type;
     const int m = blockIdx.z;
     if (ctl[m].outer_done || ctl[m].inner_done) return;
-    const double alpha = rc.red[m].val[(k & 1) ? RS_RZB : RS_RZA] / rc.red[m].val[RS_PQ];
-    const T a = (T)alpha;
+    const T a = cg_alpha<T>(rc, m, k);
     const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y;
     if (i < g.nx) {
         const long long c = (long long)m * g.S + (long long)j * g.P + i;
@@ -382,7 +404,7 @@ __global__ void __launch_bounds__(SC_THREADS, sizeof(T) == 4 ? 2 : 1) k_smooth(S
     const T *__restrict__ cs = cs_of<T>(L);
     const uint8_t *__restrict__ opn = L.open;
     const uint8_t *__restrict__ fl = L.fluid;
-    const T cx = (T)L.cx, cy = (T)L.cy;
+    const T cx = lev0_cx<T>(L), cy = lev0_cy<T>(L);
     const bool zero = (sa.flags & SF_ZERO_INIT) != 0;
     const bool prolong = (sa.flags & SF_PROLONG) != 0;
 
@@ -482,7 +504,7 @@ __global__ void __launch_bounds__(SC_THREADS, sizeof(T) == 4 ? 2 : 1) k_smooth(S
         }
     }
     if (sa.flags & (SF_DOT | SF_INIT_DOT)) {
-        double dtot = dot.total();
+        const auto dtot = dot.total();
         double tot;
         int slot = (sa.flags & SF_INIT_DOT) ? RS_RZA : (((sa.k + 1) & 1) ? RS_RZB : RS_RZA);
         if (publish_partial(rc, slot, m, dtot, false, &tot) && threadIdx.x == 0) {
@@ -490,8 +512,10 @@ __global__ void __launch_bounds__(SC_THREADS, sizeof(T) == 4 ? 2 : 1) k_smooth(S
             if (sa.flags & SF_INIT_DOT) {
                 rc.red[m].val[RS_RZ0] = tot;
                 if (!(tot > 0.0)) ctl[m].inner_done = 1;
-            } else if (!(tot > sa.rtol2 * rc.red[m].val[RS_RZ0])) {
-                ctl[m].inner_done = 1;   // inner convergence, decided where the total is formed
+            } else {
+                set_beta(rc, m, sa.k, tot);
+                if (!(tot > sa.rtol2 * rc.red[m].val[RS_RZ0]))
+                    ctl[m].inner_done = 1;   // inner convergence, decided where the total is formed
             }
         }
     }
@@ -562,7 +586,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
     const T *__restrict__ eim = ein + off;
     T *__restrict__ em = e + off;
     const T *__restrict__ ecm = ec + (long long)m * sa.Sc;
-    const T cx = (T)L.cx, cy = (T)L.cy;
+    const T cx = lev0_cx<T>(L), cy = lev0_cy<T>(L);
     // ORDER 0: pre-smoothing (zero guess, red first, residual restricted); ORDER 1:
     // post-smoothing (coarse correction prolonged, black first)
     constexpr bool zero = ORDER == 0, prolong = ORDER == 1;
@@ -726,7 +750,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
         }
     }
     if (want_dot) {
-        double dtot = dot.total();
+        const auto dtot = dot.total();
         double tot;
         int slot = (sa.flags & SF_INIT_DOT) ? RS_RZA : (((sa.k + 1) & 1) ? RS_RZB : RS_RZA);
         if (publish_partial(rc, slot, m, dtot, false, &tot) && threadIdx.x == 0) {
@@ -734,8 +758,10 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
             if (sa.flags & SF_INIT_DOT) {
                 rc.red[m].val[RS_RZ0] = tot;
                 if (!(tot > 0.0)) ctl[m].inner_done = 1;
-            } else if (!(tot > sa.rtol2 * rc.red[m].val[RS_RZ0])) {
-                ctl[m].inner_done = 1;   // inner convergence, decided where the total is formed
+            } else {
+                set_beta(rc, m, sa.k, tot);
+                if (!(tot > sa.rtol2 * rc.red[m].val[RS_RZ0]))
+                    ctl[m].inner_done = 1;   // inner convergence, decided where the total is formed
             }
         }
     }

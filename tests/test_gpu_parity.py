@@ -392,10 +392,13 @@ def test_conditional_refinement_loop_is_exact_and_skips_work(precision):
 
 def test_extrapolated_initial_guess_changes_only_the_refinement_count():
     """MIXED: the pressure increment's initial guess 2 dp^n - dp^(n-1) against the last increment
-    alone, at the bench grid over 300 steps with the tuned solver.  Every solve ends at div_tol
-    either way, so costs and gradients agree to the solver's accuracy (the trajectories differ by
-    the divergence tolerance only), and the extrapolated guess needs fewer refinements."""
-    nx, ny, N, n = 512, 256, 8, 300
+    alone, at the bench grid, 33 member slots, over 1000 steps with the tuned solver.  Every solve
+    ends at div_tol either way, so costs and gradients agree to the solver's accuracy (the
+    trajectories differ by the divergence tolerance only).  In this forced, unsteady flow the
+    extrapolated guess needs fewer refinements; in a near-steady one both guesses sit at the floor
+    set by the FP32 rounding of the tendencies (fresh divergence every step), which no guess
+    predicts."""
+    nx, ny, N, n = 512, 256, 32, 1000
     out = []
     for ex in (0, 1):
         cfg = pkg.default_config(nx, ny, Re=7500.0, n_steps=n, n_window=n // 2, n_members=N, precision=pkg.MIXED,
