@@ -105,7 +105,7 @@ typedef struct envar_config {
     int steps_per_graph;     /* time steps per captured CUDA graph (even) */
     int member_groups;       /* batched runs: member groups whose time steps run as concurrent
                                 branches of the captured graph; 0 = automatic (4 from 24 member
-                                slots, 2 from 8), 1 .. 4 */
+                                slots, 2 from 8), 1 .. 8 */
     int lip_slip;            /* 1: the lower wall of the channel (y = 0) is free slip outside
                                 noslip_span and no slip inside it (the slip segments of Sec. 4.4);
                                 0: no slip everywhere */

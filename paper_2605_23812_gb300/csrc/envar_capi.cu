@@ -23,7 +23,7 @@ void launch_axis_factor(double h, double a, int ncell, int m, int pad, int nxi, 
 }
 using namespace envar;
 
-constexpr int ENVAR_MAX_GROUPS = 4;
+constexpr int ENVAR_MAX_GROUPS = 8;
 
 // Limited-memory BFGS history in device memory (Sec. 3.3.1, Eq. update_BFGS): the newest `count`
 // of at most m pairs (s, y) in ring slots, with the previous iterate and gradient.

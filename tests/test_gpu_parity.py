@@ -321,7 +321,7 @@ def test_member_groups_give_identical_results(precision):
     member's arithmetic: states, costs and the gradient agree bit for bit with one group."""
     nx, ny, N = 64, 32, 8
     out = []
-    for groups in (1, 2, 3):
+    for groups in (1, 2, 3, 8):
         cfg = pkg.default_config(nx, ny, Re=1000.0, n_steps=24, n_window=8, n_members=N, precision=precision,
                                  member_groups=groups, steps_per_graph=10)
         ens = pkg.Ensemble(cfg)
