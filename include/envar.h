@@ -122,6 +122,9 @@ typedef struct envar_config {
                                 (both re-centred on their fluid mean) from the third step on, the
                                 last increment before; 0: the last increment.  Only the number
                                 of refinements changes: every solve still ends at div_tol */
+    int nu_coarse;           /* smoothing sweep pairs on the multigrid levels below the finest one
+                                (pre- and post-smoothing alike, so the V-cycle stays symmetric);
+                                0 (default): nu_pre / nu_post on every level; 1 .. 3 */
 } envar_config;
 
 typedef struct envar_handle_s *envar_handle;
@@ -346,12 +349,13 @@ int envar_adjoint_stats(envar_handle h, long long *forward_steps, long long *rev
 int envar_revolve_plan(long long n_steps, int n_slots, long long *recompute, long long *stores, long long *restores);
 
 /* Pick the fastest pressure-solve parameters for this handle on this GPU: for each candidate of a
- * fixed list of twelve (refinement cap, inner-iteration cap and tolerance, smoothing sweep pairs, coarse
- * sweeps) run all member slots probe_steps time steps from the initial state with the current
+ * fixed list of seventeen (refinement cap, inner-iteration cap and tolerance, smoothing sweep pairs
+ * on the finest and on the coarser levels, coarse sweeps) run all member slots probe_steps time steps from the initial state with the current
  * forcing, and keep the fastest candidate under which no member reports a status bit (every solve
  * met div_tol).  The divergence tolerance itself is not a candidate parameter: results change only
  * within it.  *best_ms_per_step (may be NULL): the winner's time per step; chosen (may be NULL,
- * 4 ints): max_outer, max_inner, nu_pre (= nu_post), coarse_sweeps.  Overwrites the members' state
+ * 4 ints): max_outer, max_inner, nu_pre (= nu_post), coarse_sweeps; the rest of the choice
+ * (inner_rtol, nu_coarse) is in envar_get_config.  Overwrites the members' state
  * and recaptures the step graphs.  ENVAR_ESTATE (parameters unchanged) if no candidate qualifies. */
 int envar_autotune(envar_handle h, int probe_steps, double *best_ms_per_step, int *chosen);
 

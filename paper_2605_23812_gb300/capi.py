@@ -39,7 +39,7 @@ class Config(ctypes.Structure):
         ("nu_pre", c_int), ("nu_post", c_int), ("coarse_sweeps", c_int), ("steps_per_graph", c_int),
         ("member_groups", c_int),
         ("lip_slip", c_int), ("noslip_span", c_double * 2), ("forcing_y_only", c_int),
-        ("conditional_refinement", c_int), ("guess_extrapolation", c_int),
+        ("conditional_refinement", c_int), ("guess_extrapolation", c_int), ("nu_coarse", c_int),
     ]
 
 
@@ -330,8 +330,9 @@ class Ensemble:
         ch = (c_int * 4)()
         self.torch.cuda.current_stream().synchronize()
         self._check(lib().envar_autotune(self._h, int(probe_steps), ctypes.byref(ms), ch), "envar_autotune")
+        c = self.config()
         return {"max_outer": ch[0], "max_inner": ch[1], "nu": ch[2], "coarse_sweeps": ch[3],
-                "inner_rtol": self.config().inner_rtol, "probe_ms_per_step": ms.value}
+                "inner_rtol": c.inner_rtol, "nu_coarse": c.nu_coarse, "probe_ms_per_step": ms.value}
 
     def config(self) -> Config:
         c = Config()

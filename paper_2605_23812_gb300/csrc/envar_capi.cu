@@ -170,6 +170,7 @@ extern "C" int envar_default_config(envar_config *c, int nx, int ny)
     c->lip_slip = 0; c->noslip_span[0] = -0.4; c->noslip_span[1] = 1.75; c->forcing_y_only = 0;
     c->conditional_refinement = 1;
     c->guess_extrapolation = 1;
+    c->nu_coarse = 0;
     return ENVAR_OK;
 }
 
@@ -873,7 +874,7 @@ extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda
         c.max_outer < 1 || c.max_inner < 1 || c.nu_pre < 1 || c.nu_pre > 3 || c.nu_post < 1 || c.nu_post > 3 ||
         c.coarse_sweeps < 1 || c.steps_per_graph < 1 || !(c.x1 > c.x0) || !(c.y1 > c.y0) || !(c.inner_rtol > 0) ||
         c.member_groups < 0 || c.member_groups > ENVAR_MAX_GROUPS || c.guess_extrapolation < 0 ||
-        c.guess_extrapolation > 1) {
+        c.guess_extrapolation > 1 || c.nu_coarse < 0 || c.nu_coarse > 3) {
         set_err(nullptr, "envar_init: invalid configuration");
         return ENVAR_EINVAL;
     }
@@ -928,6 +929,7 @@ extern "C" int envar_init(envar_handle *out, const envar_config *cfg, void *cuda
         PoissonCfg &pc = h->pc;
         pc.nlev = h->nlev; pc.ncoarse = h->ncoarse;
         pc.nu_pre = c.nu_pre; pc.nu_post = c.nu_post; pc.coarse_sweeps = c.coarse_sweeps;
+        pc.nu_c = c.nu_coarse;
         pc.max_outer = c.max_outer; pc.max_inner = c.max_inner;
         pc.inner_rtol2 = c.inner_rtol * c.inner_rtol;
         pc.rtol_abs = c.div_tol * h->g.hxy / h->g.dt;
@@ -2094,14 +2096,18 @@ extern "C" int envar_adjoint_stats(envar_handle h, long long *forward_steps, lon
 // ------------------------------------------------------------------------------------ autotuning
 // Solver parameters that change only the speed of a time step (the refinement loop still stops at
 // div_tol): refinement cap, inner-iteration cap and tolerance, smoothing sweeps, coarse sweeps.
-struct SolverParams { int max_outer, max_inner, nu, coarse_sweeps; double inner_rtol; };
+struct SolverParams { int max_outer, max_inner, nu, coarse_sweeps; double inner_rtol; int nu_coarse; };
 // With the refinement loop as a conditional graph node a high refinement cap costs nothing unless
 // a step needs it, so every candidate keeps a cap of 10 (margin for the long runs after the probe)
 // and the candidates differ in what sets the cost of a refinement.
+// The last five smooth the coarser levels less than the finest one (their share of the V-cycle's
+// SM time is large and mostly latency).
 static const SolverParams kTuneCandidates[] = {
-    {10, 2, 3, 2, 1e-3}, {10, 3, 2, 2, 1e-3}, {10, 2, 2, 2, 1e-3}, {10, 3, 3, 2, 1e-3},
-    {10, 4, 2, 4, 1e-3}, {10, 2, 3, 4, 1e-3}, {10, 6, 2, 8, 1e-4}, {10, 3, 1, 2, 1e-3},
-    {10, 2, 1, 2, 1e-3}, {10, 1, 3, 2, 1e-3}, {10, 1, 2, 2, 1e-3}, {10, 2, 3, 1, 1e-3},
+    {10, 2, 3, 2, 1e-3, 0}, {10, 3, 2, 2, 1e-3, 0}, {10, 2, 2, 2, 1e-3, 0}, {10, 3, 3, 2, 1e-3, 0},
+    {10, 4, 2, 4, 1e-3, 0}, {10, 2, 3, 4, 1e-3, 0}, {10, 6, 2, 8, 1e-4, 0}, {10, 3, 1, 2, 1e-3, 0},
+    {10, 2, 1, 2, 1e-3, 0}, {10, 1, 3, 2, 1e-3, 0}, {10, 1, 2, 2, 1e-3, 0}, {10, 2, 3, 1, 1e-3, 0},
+    {10, 2, 3, 1, 1e-3, 1}, {10, 2, 3, 1, 1e-3, 2}, {10, 2, 3, 2, 1e-3, 1}, {10, 3, 3, 1, 1e-3, 1},
+    {10, 2, 2, 1, 1e-3, 1},
 };
 
 static void drop_graphs(envar_handle h)
@@ -2120,8 +2126,9 @@ static void apply_params(envar_handle h, const SolverParams &p)
 {
     h->cfg.max_outer = p.max_outer; h->cfg.max_inner = p.max_inner;
     h->cfg.nu_pre = h->cfg.nu_post = p.nu; h->cfg.coarse_sweeps = p.coarse_sweeps; h->cfg.inner_rtol = p.inner_rtol;
+    h->cfg.nu_coarse = p.nu_coarse;
     h->pc.max_outer = p.max_outer; h->pc.max_inner = p.max_inner;
-    h->pc.nu_pre = h->pc.nu_post = p.nu; h->pc.coarse_sweeps = p.coarse_sweeps;
+    h->pc.nu_pre = h->pc.nu_post = p.nu; h->pc.coarse_sweeps = p.coarse_sweeps; h->pc.nu_c = p.nu_coarse;
     h->pc.inner_rtol2 = p.inner_rtol * p.inner_rtol;
     drop_graphs(h);
 }
@@ -2130,7 +2137,8 @@ extern "C" int envar_autotune(envar_handle h, int probe_steps, double *best_ms_p
 {
     if (!h || probe_steps < 2) return ENVAR_EINVAL;
     if (!h->have_ic) { set_err(h, "envar_autotune: no initial state"); return ENVAR_ESTATE; }
-    const SolverParams orig{h->cfg.max_outer, h->cfg.max_inner, h->cfg.nu_pre, h->cfg.coarse_sweeps, h->cfg.inner_rtol};
+    const SolverParams orig{h->cfg.max_outer, h->cfg.max_inner, h->cfg.nu_pre, h->cfg.coarse_sweeps, h->cfg.inner_rtol,
+                            h->cfg.nu_coarse};
     const int M = h->Mall;
     std::vector<MemberCtl> c((size_t)M);
     cudaEvent_t e0 = nullptr, e1 = nullptr;

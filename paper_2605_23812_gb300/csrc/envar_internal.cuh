@@ -165,6 +165,53 @@ struct RedCtx {
 };
 static inline RedCtx make_ctx(const Partials &pt) { return RedCtx{pt.nblk, pt.part, pt.red, pt.stride}; }
 
+// Loads issued where they stand: volatile inline PTX is neither sunk into the branch that uses it
+// nor dropped, so a block's data is in flight while its control word (has this member converged?)
+// and its CG scalar are still on their way.  nc: data the kernel does not write.
+__device__ __forceinline__ float2 ld_early_nc(const float2 *p)
+{
+    float2 v;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double2 ld_early_nc(const double2 *p)
+{
+    double2 v;
+    asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_early_nc(const float *p)
+{
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_early_nc(const double *p)
+{
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_early_nc_u16(const uint8_t *p)
+{
+    unsigned short v;
+    asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+// coherent variants for data the same thread writes back later in the kernel
+__device__ __forceinline__ float2 ld_early(const float2 *p)
+{
+    float2 v;
+    asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double2 ld_early(const double2 *p)
+{
+    double2 v;
+    asm volatile("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ double to_dbl(double v) { return v; }
 __device__ __forceinline__ double to_dbl(float v) { return (double)v; }
 
@@ -273,6 +320,7 @@ struct PoissonCfg {
     int nlev;                       // number of levels
     int ncoarse;                    // first level handled by the per-member coarse kernel
     int nu_pre, nu_post, coarse_sweeps;
+    int nu_c;                       // sweep pairs on the levels below the finest (0: nu_pre / nu_post)
     int max_outer, max_inner;
     double inner_rtol2;             // inner_rtol^2
     double rtol_abs;                // outer stop: max |r| <= rtol_abs (r = b - A x, FV form)

@@ -438,28 +438,38 @@ __global__ void __launch_bounds__(128) k_axpy_last_mx(Grid g, float *__restrict_
                                                       RedCtx rc, MemberCtl *ctl, int k)
 {
     const int m = blockIdx.z;
+    const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y;
+    const long long c = (long long)m * g.S + (long long)j * g.P + i;
+    // the data first (none of it depends on the control word or on alpha); pairs past nx are not
+    // touched (nx is even: pairs are whole)
+    float2 ev[2], pv[2], x0[2], x1[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        ev[h] = pv[h] = x0[h] = x1[h] = make_float2(0.f, 0.f);
+        if (i + 2 * h < g.nx) {
+            ev[h] = ld_early_nc(reinterpret_cast<const float2 *>(e + c + 2 * h));
+            pv[h] = ld_early_nc(reinterpret_cast<const float2 *>(p + c + 2 * h));
+            x0[h] = ld_early(reinterpret_cast<const float2 *>(xh + c + 2 * h));
+            x1[h] = ld_early(reinterpret_cast<const float2 *>(xl + c + 2 * h));
+        }
+    }
     if (ctl[m].outer_done) return;
     const bool moving = !ctl[m].inner_done;
     const float a = moving ? rc.red[m].fa : 0.f;   // alpha of this iteration, formed by the SpMV
-    const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y;
-    if (i < g.nx) {
-        const long long c = (long long)m * g.S + (long long)j * g.P + i;
 #pragma unroll
-        for (int h = 0; h < 4; h += 2) {
-            if (i + h >= g.nx) break;                           // nx is even: pairs are whole
-            float2 ev = *reinterpret_cast<const float2 *>(e + c + h);
-            if (moving) {
-                const float2 pv = *reinterpret_cast<const float2 *>(p + c + h);
-                ev.x += a * pv.x;
-                ev.y += a * pv.y;
-            }
-            if (ev.x != 0.f || ev.y != 0.f) {
-                float2 x0 = *reinterpret_cast<const float2 *>(xh + c + h), x1 = *reinterpret_cast<const float2 *>(xl + c + h);
-                if (ev.x != 0.f) { const f2 s = df_add_f(f2{x0.x, x1.x}, ev.x); x0.x = s.h; x1.x = s.l; }
-                if (ev.y != 0.f) { const f2 s = df_add_f(f2{x0.y, x1.y}, ev.y); x0.y = s.h; x1.y = s.l; }
-                *reinterpret_cast<float2 *>(xh + c + h) = x0;
-                *reinterpret_cast<float2 *>(xl + c + h) = x1;
-            }
+    for (int h = 0; h < 2; ++h) {
+        if (i + 2 * h >= g.nx) break;
+        float2 d = ev[h];
+        if (moving) {
+            d.x += a * pv[h].x;
+            d.y += a * pv[h].y;
+        }
+        if (d.x != 0.f || d.y != 0.f) {
+            float2 hi = x0[h], lo = x1[h];
+            if (d.x != 0.f) { const f2 sx = df_add_f(f2{hi.x, lo.x}, d.x); hi.x = sx.h; lo.x = sx.l; }
+            if (d.y != 0.f) { const f2 sy = df_add_f(f2{hi.y, lo.y}, d.y); hi.y = sy.h; lo.y = sy.l; }
+            *reinterpret_cast<float2 *>(xh + c + 2 * h) = hi;
+            *reinterpret_cast<float2 *>(xl + c + 2 * h) = lo;
         }
     }
     if (moving && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctl[m].inner_its += 1;

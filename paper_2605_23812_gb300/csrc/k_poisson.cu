@@ -228,56 +228,77 @@ __global__ void __launch_bounds__(SPMV_WARPS * 32) k_spmv0(Grid g, Level L0, con
                                                           T *__restrict__ q, RedCtx rc, MemberCtl *ctl, int k)
 {
     using T2 = typename Pair2Of<T>::type;
+    constexpr int R = SPMV_ROWS, NR = SPMV_ROWS + 2;
     const int m = blockIdx.z;
-    if (ctl[m].outer_done || ctl[m].inner_done) return;
     const long long off = (long long)m * g.S;
-    const T bt = (k > 0) ? cg_beta<T>(rc, m, k) : (T)0;
-    const T cx = lev0_cx<T>(L0), cy = lev0_cy<T>(L0);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int iL = blockIdx.x * 64 + 2 * lane;
     const bool colok = iL + 1 < g.nx;                       // nx is even
     const int j0 = (blockIdx.y * SPMV_WARPS + w) * SPMV_ROWS;
     const T *zm = z + off, *pm = pold + off;
-    auto ld_p = [&](int j) -> T2 {
-        if (!colok || j < 0 || j >= g.ny) return T2{(T)0, (T)0};
-        const long long c = (long long)j * g.P + iL;
-        const T2 zz = *reinterpret_cast<const T2 *>(zm + c);
-        if (k == 0) return zz;
-        const T2 pp = *reinterpret_cast<const T2 *>(pm + c);
-        return T2{zz.x + bt * pp.x, zz.y + bt * pp.y};
-    };
-    auto ld_p1 = [&](int j, int i) -> T {
-        if (i < 0 || i >= g.nx || j < 0 || j >= g.ny) return (T)0;
-        const long long c = (long long)j * g.P + i;
-        return (k == 0) ? zm[c] : zm[c] + bt * pm[c];
-    };
+    // every load of the warp's rows first (rows j0 - 1 .. j0 + R; z, and p for k > 0; the strip's
+    // edge cells; the open-face bits): none depends on the control word or on beta
+    T2 zr[NR], pr[NR];
+    T zw[R], ze[R], pw[R], pe[R];
+    unsigned int ob[R];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int j = j0 - 1 + r;
+        zr[r] = T2{(T)0, (T)0};
+        pr[r] = T2{(T)0, (T)0};
+        if (colok && j >= 0 && j < g.ny) {
+            const long long c = (long long)j * g.P + iL;
+            zr[r] = ld_early_nc(reinterpret_cast<const T2 *>(zm + c));
+            if (k > 0) pr[r] = ld_early_nc(reinterpret_cast<const T2 *>(pm + c));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = j0 + r;
+        zw[r] = ze[r] = pw[r] = pe[r] = (T)0;
+        ob[r] = 0u;
+        if (j < g.ny) {
+            const long long c = (long long)j * g.P + iL;
+            if (colok) ob[r] = ld_early_nc_u16(L0.open + c);
+            if (lane == 0 && iL >= 1) {
+                zw[r] = ld_early_nc(zm + c - 1);
+                if (k > 0) pw[r] = ld_early_nc(pm + c - 1);
+            }
+            if (lane == 31 && iL + 2 < g.nx) {
+                ze[r] = ld_early_nc(zm + c + 2);
+                if (k > 0) pe[r] = ld_early_nc(pm + c + 2);
+            }
+        }
+    }
+    if (ctl[m].outer_done || ctl[m].inner_done) return;
+    const T bt = (k > 0) ? cg_beta<T>(rc, m, k) : (T)0;
+    const T cx = lev0_cx<T>(L0), cy = lev0_cy<T>(L0);
     auto diag = [&](unsigned int b) {
         return ((b & 1u) ? cx : (T)0) + ((b & 2u) ? cx : (T)0) + ((b & 4u) ? cy : (T)0) + ((b & 8u) ? cy : (T)0);
     };
+    // p = z + beta p_old (zero outside the domain: z and p_old are zero there)
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+        if (k > 0) zr[r] = T2{zr[r].x + bt * pr[r].x, zr[r].y + bt * pr[r].y};
     DotAcc<T> pq;
     if (j0 < g.ny) {
-        T2 pS = ld_p(j0 - 1), pC = ld_p(j0);
-#pragma unroll 4
-        for (int r = 0; r < SPMV_ROWS; ++r) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
             const int j = j0 + r;
             if (j >= g.ny) break;
-            const T2 pN = ld_p(j + 1);
+            const T2 pS = zr[r], pC = zr[r + 1], pN = zr[r + 2];
             T pW = __shfl_up_sync(0xffffffffu, pC.y, 1), pE = __shfl_down_sync(0xffffffffu, pC.x, 1);
-            if (lane == 0) pW = ld_p1(j, iL - 1);
-            if (lane == 31) pE = ld_p1(j, iL + 2);
+            if (lane == 0) pW = (k > 0) ? zw[r] + bt * pw[r] : zw[r];
+            if (lane == 31) pE = (k > 0) ? ze[r] + bt * pe[r] : ze[r];
             if (colok) {
                 const long long c = (long long)j * g.P + iL;
-                const unsigned int b2 = *reinterpret_cast<const unsigned short *>(L0.open + c);
-                const unsigned int bl = b2 & 15u, br = (b2 >> 8) & 15u;
+                const unsigned int bl = ob[r] & 15u, br = (ob[r] >> 8) & 15u;
                 const T ql = bl ? diag(bl) * pC.x - cx * (pW + pC.y) - cy * (pS.x + pN.x) : (T)0;
                 const T qr = br ? diag(br) * pC.y - cx * (pC.x + pE) - cy * (pS.y + pN.y) : (T)0;
                 *reinterpret_cast<T2 *>(pnew + off + c) = pC;
                 *reinterpret_cast<T2 *>(q + off + c) = T2{ql, qr};
-                pq.add(pC.x, ql);
-                pq.add(pC.y, qr);
+                pq.add_pair(pC.x, ql, pC.y, qr);
             }
-            pS = pC;
-            pC = pN;
         }
     }
     const auto pqt = pq.total();
@@ -297,19 +318,30 @@ __global__ void __launch_bounds__(128) k_axpy4(Grid g, T *__restrict__ e, T *__r
 {
     using T2 = typename Pair2Of<T>::type;
     const int m = blockIdx.z;
+    const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y;
+    const long long c = (long long)m * g.S + (long long)j * g.P + i;
+    const bool in = i < g.nx;                                // nx % 4 == 0: all four values in
+    // the data first (none of it depends on the control word or on alpha)
+    T2 ev[2], rv[2], pv[2], qv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        ev[h] = rv[h] = pv[h] = qv[h] = T2{(T)0, (T)0};
+        if (in) {
+            ev[h] = ld_early(reinterpret_cast<const T2 *>(e + c + 2 * h));
+            rv[h] = ld_early(reinterpret_cast<const T2 *>(r + c + 2 * h));
+            pv[h] = ld_early_nc(reinterpret_cast<const T2 *>(p + c + 2 * h));
+            qv[h] = ld_early_nc(reinterpret_cast<const T2 *>(q + c + 2 * h));
+        }
+    }
     if (ctl[m].outer_done || ctl[m].inner_done) return;
     const T a = cg_alpha<T>(rc, m, k);
-    const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y;
-    if (i < g.nx) {
-        const long long c = (long long)m * g.S + (long long)j * g.P + i;
+    if (in) {
 #pragma unroll
-        for (int h = 0; h < 4; h += 2) {
-            T2 ev = *reinterpret_cast<const T2 *>(e + c + h), rv = *reinterpret_cast<const T2 *>(r + c + h);
-            const T2 pv = *reinterpret_cast<const T2 *>(p + c + h), qv = *reinterpret_cast<const T2 *>(q + c + h);
-            ev.x += a * pv.x; ev.y += a * pv.y;
-            rv.x -= a * qv.x; rv.y -= a * qv.y;
-            *reinterpret_cast<T2 *>(e + c + h) = ev;
-            *reinterpret_cast<T2 *>(r + c + h) = rv;
+        for (int h = 0; h < 2; ++h) {
+            ev[h].x += a * pv[h].x; ev[h].y += a * pv[h].y;
+            rv[h].x -= a * qv[h].x; rv[h].y -= a * qv[h].y;
+            *reinterpret_cast<T2 *>(e + c + 2 * h) = ev[h];
+            *reinterpret_cast<T2 *>(r + c + 2 * h) = rv[h];
         }
     }
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctl[m].inner_its += 1;
@@ -970,6 +1002,9 @@ __global__ void __launch_bounds__(1024) k_coarse(CoarseArgs ca, const T *__restr
     }
 }
 
+// smoothing sweep pairs on level l: the finest level's own, or nu_c below it when set
+static inline int level_sweeps(const PoissonCfg &pc, int l, int nu_finest) { return (l > 0 && pc.nu_c) ? pc.nu_c : nu_finest; }
+
 // kernel arguments and dynamic shared memory of the coarse block
 template <class T>
 static size_t coarse_args(const Level *lev, const PoissonCfg &pc, int inner_guard, CoarseArgs *ca)
@@ -982,8 +1017,8 @@ static size_t coarse_args(const Level *lev, const PoissonCfg &pc, int inner_guar
     ca->lw = pc.nlev;
     for (int l = pc.ncoarse; l < pc.nlev; ++l)
         if (lev[l].nx * lev[l].ny <= COARSE_WARP_CELLS) { ca->lw = l; break; }
-    ca->nu_pre = pc.nu_pre;
-    ca->nu_post = pc.nu_post;
+    ca->nu_pre = level_sweeps(pc, pc.ncoarse, pc.nu_pre);
+    ca->nu_post = level_sweeps(pc, pc.ncoarse, pc.nu_post);
     ca->coarse_sweeps = pc.coarse_sweeps;
     ca->inner_guard = inner_guard;
     return (size_t)ca->lay.total_bytes;
@@ -1063,10 +1098,11 @@ static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B,
     for (int l = 0; l < lc; ++l) {
         const Level &L = lev[l];
         const Level &Lc = lev[l + 1];
-        SmoothArgs sa{L, Lc.P, Lc.S, pc.nu_pre, 0, SF_ZERO_INIT | SF_RESTRICT, k};
+        const int nu = level_sweeps(pc, l, pc.nu_pre);
+        SmoothArgs sa{L, Lc.P, Lc.S, nu, 0, SF_ZERO_INIT | SF_RESTRICT, k};
         const T *f = (l == 0) ? f0 : (const T *)B.lev_f[l];
         T *et = (T *)B.lev_t[l];     // pre-smoothed guess, read by the post-smoothing below
-        launch_smooth<T>(M, pc.nu_pre, st, sa, f, (const T *)nullptr, et, (const T *)nullptr, (T *)B.lev_f[l + 1], rc,
+        launch_smooth<T>(M, nu, st, sa, f, (const T *)nullptr, et, (const T *)nullptr, (T *)B.lev_f[l + 1], rc,
                          ctl, inner_guard);
     }
     // coarse block
@@ -1084,10 +1120,11 @@ static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B,
         const Level &Lc = lev[l + 1];
         int flags = SF_PROLONG;
         if (l == 0) flags |= init ? SF_INIT_DOT : SF_DOT;
-        SmoothArgs sa{L, Lc.P, Lc.S, pc.nu_post, 1, flags, k, pc.inner_rtol2};
+        const int nu = level_sweeps(pc, l, pc.nu_post);
+        SmoothArgs sa{L, Lc.P, Lc.S, nu, 1, flags, k, pc.inner_rtol2};
         const T *f = (l == 0) ? f0 : (const T *)B.lev_f[l];
         T *e = (l == 0) ? z : (T *)B.lev_e[l];
-        launch_smooth<T>(M, pc.nu_post, st, sa, f, (const T *)B.lev_t[l], e, (const T *)B.lev_e[l + 1], (T *)nullptr,
+        launch_smooth<T>(M, nu, st, sa, f, (const T *)B.lev_t[l], e, (const T *)B.lev_e[l + 1], (T *)nullptr,
                          rc, ctl, inner_guard);
     }
 }
