@@ -683,42 +683,50 @@ static void enqueue_range(envar_handle h, int M, const MemberView &v, cudaStream
     }
 }
 
-// One time step of the first M member slots.  With all slots and several member groups, the
-// groups' steps are independent chains on side streams (parallel branches of the captured graph),
-// so one group's latency-bound phases overlap another's bandwidth-bound ones.  The corrections of
-// groups 1.. read member 0's pressure increment (the exact DOMAIN contraction): they wait for group
-// 0's pressure solve, and group 0 re-centres that increment only after all of them have read it.
-static void enqueue_step(envar_handle h, int M)
+// nsteps time steps of the first M member slots.  With all slots and several member groups, each
+// group's steps form one chain on its side stream (a parallel branch of the captured graph, forked
+// once and joined once), so one group's latency-bound phases overlap another's bandwidth-bound
+// ones and the groups need not meet at every step.  The only coupling is member 0: the corrections
+// of groups 1.. read its pressure increment and predictor (the exact DOMAIN contraction), so they
+// wait for group 0's solve of the same step, and group 0 changes member 0's increment again (the
+// FP64 re-centring, the mixed path's next initial guess) only after every group has read it.
+static void enqueue_steps(envar_handle h, int M, int nsteps)
 {
     const int G = (M == h->Mall) ? h->ngroups : 1;
     if (G <= 1) {
         const MemberView v = member_view(h, 0);
-        for (int part = 0; part < 3; ++part) enqueue_range(h, M, v, h->st, part);
+        for (int s = 0; s < nsteps; ++s)
+            for (int part = 0; part < 3; ++part) enqueue_range(h, M, v, h->st, part);
         return;
     }
     const bool need_m0 = h->ms.wd != nullptr || h->d_wd != nullptr;
-    cudaEventRecord(h->ev_fork, h->st);
     const int per = (M + G - 1) / G;
     int ng = 0;
-    for (int k = 0; k < G; ++k) {
-        const int m0 = k * per, Mg = std::min(per, M - m0);
-        if (Mg <= 0) break;
-        ng = k + 1;
-        const MemberView v = member_view(h, m0);
-        cudaStreamWaitEvent(h->side[k], h->ev_fork, 0);
-        enqueue_range(h, Mg, v, h->side[k], 0);
-        if (need_m0) {
-            if (k == 0) cudaEventRecord(h->ev_solved0, h->side[0]);
-            else cudaStreamWaitEvent(h->side[k], h->ev_solved0, 0);
+    while (ng < G && ng * per < M) ++ng;
+    cudaEventRecord(h->ev_fork, h->st);
+    for (int k = 0; k < ng; ++k) cudaStreamWaitEvent(h->side[k], h->ev_fork, 0);
+    for (int s = 0; s < nsteps; ++s) {
+        for (int k = 0; k < ng; ++k) {
+            const int m0 = k * per, Mg = std::min(per, M - m0);
+            const MemberView v = member_view(h, m0);
+            if (need_m0 && k == 0 && s > 0)   // the previous step's corrections have read member 0
+                for (int q = 1; q < ng; ++q) cudaStreamWaitEvent(h->side[0], h->ev_corr[q], 0);
+            enqueue_range(h, Mg, v, h->side[k], 0);
+            if (need_m0) {
+                if (k == 0) cudaEventRecord(h->ev_solved0, h->side[0]);
+                else cudaStreamWaitEvent(h->side[k], h->ev_solved0, 0);
+            }
+            enqueue_range(h, Mg, v, h->side[k], 1);
+            if (need_m0 && k > 0) cudaEventRecord(h->ev_corr[k], h->side[k]);
         }
-        enqueue_range(h, Mg, v, h->side[k], 1);
-        if (need_m0 && k > 0) cudaEventRecord(h->ev_corr[k], h->side[k]);
+        for (int k = 0; k < ng; ++k) {
+            const int m0 = k * per, Mg = std::min(per, M - m0);
+            if (k == 0 && need_m0)
+                for (int q = 1; q < ng; ++q) cudaStreamWaitEvent(h->side[0], h->ev_corr[q], 0);
+            enqueue_range(h, Mg, member_view(h, m0), h->side[k], 2);
+        }
     }
     for (int k = 0; k < ng; ++k) {
-        const int m0 = k * per, Mg = std::min(per, M - m0);
-        if (k == 0 && need_m0)
-            for (int q = 1; q < ng; ++q) cudaStreamWaitEvent(h->side[0], h->ev_corr[q], 0);
-        enqueue_range(h, Mg, member_view(h, m0), h->side[k], 2);
         cudaEventRecord(h->ev_join[k], h->side[k]);
         cudaStreamWaitEvent(h->st, h->ev_join[k], 0);
     }
@@ -729,7 +737,7 @@ static int capture(envar_handle h, int M, int nsteps, cudaGraphExec_t *out, long
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
     set_capturing(true);
-    for (int s = 0; s < nsteps; ++s) enqueue_step(h, M);
+    enqueue_steps(h, M, nsteps);
     set_capturing(false);
     cudaError_t e = cudaStreamEndCapture(h->st, &graph);
     if (e != cudaSuccess || capture_failed()) {
@@ -1108,7 +1116,7 @@ static int batch_capture(envar_batch b)
     for (size_t k = 0; k < b->h.size(); ++k) {
         envar_handle h = b->h[k];
         cudaStreamWaitEvent(h->st, b->ev, 0);
-        for (int s = 0; s < b->per_chunk[k]; ++s) enqueue_step(h, h->Mall);
+        enqueue_steps(h, h->Mall, b->per_chunk[k]);
         cudaEventRecord(b->ev_h[k], h->st);
         cudaStreamWaitEvent(b->st, b->ev_h[k], 0);
     }

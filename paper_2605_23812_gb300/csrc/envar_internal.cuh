@@ -192,7 +192,13 @@ __device__ __forceinline__ double ld_early_nc(const double *p)
     asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
-__device__ __forceinline__ unsigned int ld_early_nc_u16(const uint8_t *p)
+__device__ __forceinline__ unsigned int ld_early_nc_u32(const void *p)
+{
+    unsigned int v;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_early_nc_u16(const void *p)
 {
     unsigned short v;
     asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(v) : "l"(p));

@@ -326,13 +326,12 @@ void launch_predict_rhs_mx(const Grid &g, const MixConst &K, int M, const MixSta
 // ---------------------------------------------------------------------------- outer residual (df64)
 // k_outer_residual_mx: r = b - A x in df64 on every fluid cell (FP32 r = its leading word; 0 on the
 // other cells), e = 0, and per member the maximum |r| and the fluid sum of x.  A warp owns a
-// 64-column strip of OR_ROWS rows, lane l the cell pair (2l, 2l+1): x of the rows below, at and
-// above the current one stays in registers, the east / west neighbours come from the neighbouring
-// lanes by shuffle (from memory at the strip's edges), and the level-0 open-face bits select the
+// 64-column strip of OR_ROWS rows, lane l the cell pair (2l, 2l+1): x of the strip's rows and of
+// the rows above and below, b, the open-face and fluid bits and the strip's edge cells are all
+// loaded first (in flight together, before the control word is tested), east / west neighbours
+// come from the neighbouring lanes by shuffle, and the level-0 open-face bits select the
 // operator's terms (an open face joins two fluid cells).
-constexpr int OR_ROWS = 8, OR_WARPS = 8;
-
-struct XPair { float2 h, l; };
+constexpr int OR_ROWS = 4, OR_WARPS = 8;
 
 __global__ void __launch_bounds__(OR_WARPS * 32) k_outer_residual_mx(Grid g, Level L0, MixConst K,
                                                                      const float *__restrict__ bh,
@@ -343,73 +342,86 @@ __global__ void __launch_bounds__(OR_WARPS * 32) k_outer_residual_mx(Grid g, Lev
                                                                      RedCtx rc, MemberCtl *ctl, double rtol_abs,
                                                                      int count_it)
 {
+    constexpr int R = OR_ROWS, NR = OR_ROWS + 2;
     const int m = blockIdx.z;
-    if (ctl[m].outer_done) return;
     const long long off = (long long)m * g.S;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int iL = blockIdx.x * 64 + 2 * lane;
     const bool colok = iL < g.nx;                               // nx is even: both cells of the pair
     const int j0 = (blockIdx.y * OR_WARPS + w) * OR_ROWS;
     const float *xhm = xh + off, *xlm = xl + off;
-    auto ld_x = [&](int j) -> XPair {                          // zeros outside the domain
-        XPair v{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        if (!colok || j < 0 || j >= g.ny) return v;
-        const long long c = (long long)j * g.P + iL;
-        v.h = *reinterpret_cast<const float2 *>(xhm + c);
-        v.l = *reinterpret_cast<const float2 *>(xlm + c);
-        return v;
-    };
-    auto ld_x1 = [&](int j, int i) -> f2 {
-        if (i < 0 || i >= g.nx) return f2{0.f, 0.f};
-        const long long c = (long long)j * g.P + i;
-        return f2{xhm[c], xlm[c]};
-    };
+    float2 xrh[NR], xrl[NR], brh[R], brl[R];
+    f2 xw[R], xe[R];
+    unsigned int ob[R], fl[R];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {                              // rows j0 - 1 .. j0 + R; zeros outside
+        const int j = j0 - 1 + q;
+        xrh[q] = xrl[q] = make_float2(0.f, 0.f);
+        if (colok && j >= 0 && j < g.ny) {
+            const long long c = (long long)j * g.P + iL;
+            xrh[q] = ld_early_nc(reinterpret_cast<const float2 *>(xhm + c));
+            xrl[q] = ld_early_nc(reinterpret_cast<const float2 *>(xlm + c));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int j = j0 + q;
+        brh[q] = brl[q] = make_float2(0.f, 0.f);
+        xw[q] = xe[q] = f2{0.f, 0.f};
+        ob[q] = fl[q] = 0u;
+        if (j < g.ny) {
+            const long long c = (long long)j * g.P + iL;
+            if (colok) {
+                brh[q] = ld_early_nc(reinterpret_cast<const float2 *>(bh + off + c));
+                brl[q] = ld_early_nc(reinterpret_cast<const float2 *>(bl + off + c));
+                ob[q] = ld_early_nc_u16(L0.open + c);
+                fl[q] = ld_early_nc_u16(g.fluid + c);
+            }
+            if (lane == 0 && iL >= 1) xw[q] = f2{ld_early_nc(xhm + c - 1), ld_early_nc(xlm + c - 1)};
+            if (lane == 31 && iL + 2 < g.nx) xe[q] = f2{ld_early_nc(xhm + c + 2), ld_early_nc(xlm + c + 2)};
+        }
+    }
+    if (ctl[m].outer_done) return;
     const f2 cx{K.cxh, K.cxl}, cy{K.cyh, K.cyl};
-    auto cell_r = [&](unsigned int ob, f2 xc, f2 xw, f2 xe, f2 xs_, f2 xn, f2 b) -> float {
+    auto cell_r = [&](unsigned int o, f2 xc, f2 xW, f2 xE, f2 xS, f2 xN, f2 b) -> float {
         f2 sx{0.f, 0.f}, sy{0.f, 0.f};
-        if (ob & 1u) sx = df_add(sx, df_sub(xc, xw));
-        if (ob & 2u) sx = df_add(sx, df_sub(xc, xe));
-        if (ob & 4u) sy = df_add(sy, df_sub(xc, xs_));
-        if (ob & 8u) sy = df_add(sy, df_sub(xc, xn));
+        if (o & 1u) sx = df_add(sx, df_sub(xc, xW));
+        if (o & 2u) sx = df_add(sx, df_sub(xc, xE));
+        if (o & 4u) sy = df_add(sy, df_sub(xc, xS));
+        if (o & 8u) sy = df_add(sy, df_sub(xc, xN));
         const f2 ax = df_add(df_mul(sx, cx), df_mul(sy, cy));
         return df_sub(b, ax).h;
     };
     float rmax = 0.f;
     f2 xs{0.f, 0.f};
     if (j0 < g.ny) {
-        XPair xS = ld_x(j0 - 1), xC = ld_x(j0);
-#pragma unroll 2
-        for (int rr = 0; rr < OR_ROWS; ++rr) {
-            const int j = j0 + rr;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int j = j0 + q;
             if (j >= g.ny) break;
-            const XPair xN = ld_x(j + 1);
-            f2 xw{__shfl_up_sync(0xffffffffu, xC.h.y, 1), __shfl_up_sync(0xffffffffu, xC.l.y, 1)};
-            f2 xe{__shfl_down_sync(0xffffffffu, xC.h.x, 1), __shfl_down_sync(0xffffffffu, xC.l.x, 1)};
-            if (lane == 0) xw = ld_x1(j, iL - 1);
-            if (lane == 31) xe = ld_x1(j, iL + 2);
+            const f2 x0{xrh[q + 1].x, xrl[q + 1].x}, x1{xrh[q + 1].y, xrl[q + 1].y};
+            f2 xW{__shfl_up_sync(0xffffffffu, x1.h, 1), __shfl_up_sync(0xffffffffu, x1.l, 1)};
+            f2 xE{__shfl_down_sync(0xffffffffu, x0.h, 1), __shfl_down_sync(0xffffffffu, x0.l, 1)};
+            if (lane == 0) xW = xw[q];
+            if (lane == 31) xE = xe[q];
             if (colok) {
                 const long long c = (long long)j * g.P + iL;
-                const unsigned int ob = *reinterpret_cast<const unsigned short *>(L0.open + c);
-                const unsigned int fl = *reinterpret_cast<const unsigned short *>(g.fluid + c);
-                const float2 b0 = *reinterpret_cast<const float2 *>(bh + off + c);
-                const float2 b1 = *reinterpret_cast<const float2 *>(bl + off + c);
-                const f2 x0{xC.h.x, xC.l.x}, x1{xC.h.y, xC.l.y};
                 float2 rv = make_float2(0.f, 0.f);
-                if (fl & 0xffu) {
-                    rv.x = cell_r(ob & 15u, x0, xw, x1, f2{xS.h.x, xS.l.x}, f2{xN.h.x, xN.l.x}, f2{b0.x, b1.x});
+                if (fl[q] & 0xffu) {
+                    rv.x = cell_r(ob[q] & 15u, x0, xW, x1, f2{xrh[q].x, xrl[q].x}, f2{xrh[q + 2].x, xrl[q + 2].x},
+                                  f2{brh[q].x, brl[q].x});
                     rmax = fmaxf(rmax, fabsf(rv.x));
                     xs = df_add_f(xs, x0.h);
                 }
-                if (fl >> 8) {
-                    rv.y = cell_r((ob >> 8) & 15u, x1, x0, xe, f2{xS.h.y, xS.l.y}, f2{xN.h.y, xN.l.y}, f2{b0.y, b1.y});
+                if (fl[q] >> 8) {
+                    rv.y = cell_r((ob[q] >> 8) & 15u, x1, x0, xE, f2{xrh[q].y, xrl[q].y}, f2{xrh[q + 2].y, xrl[q + 2].y},
+                                  f2{brh[q].y, brl[q].y});
                     rmax = fmaxf(rmax, fabsf(rv.y));
                     xs = df_add_f(xs, x1.h);
                 }
                 *reinterpret_cast<float2 *>(r + off + c) = rv;
                 *reinterpret_cast<float2 *>(e + off + c) = make_float2(0.f, 0.f);
             }
-            xS = xC;
-            xC = xN;
         }
     }
     const float rm = block_max_f(rmax);
