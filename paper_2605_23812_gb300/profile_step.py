@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--max-inner", type=int, default=0, help="with --nu: the inner-iteration cap")
     ap.add_argument("--coarse-sweeps", type=int, default=0, help="with --nu: coarse-level sweep pairs")
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="with --nu: inner tolerance")
+    ap.add_argument("--nu-coarse", type=int, default=0, help="with --nu: sweep pairs below the finest level")
     ap.add_argument("--unrolled", action="store_true",
                     help="capture the refinement loop unrolled instead of as a conditional graph node (ncu does "
                          "not profile the kernel nodes of graphs that hold conditional nodes); refinements past "
@@ -54,6 +55,7 @@ def main():
             cfg.coarse_sweeps = args.coarse_sweeps
         if args.inner_rtol:
             cfg.inner_rtol = args.inner_rtol
+        cfg.nu_coarse = args.nu_coarse
     if args.unrolled:
         cfg.conditional_refinement = 0
     ens = pkg.Ensemble(cfg, stream=torch.cuda.Stream())
