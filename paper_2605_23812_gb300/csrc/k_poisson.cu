@@ -605,8 +605,10 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
     static_assert(R % 2 == 0, "rows per warp come in pairs (restriction)");
     __shared__ T2 xb[2][WARPS][2][32];   // [buffer][warp][0: bottom row, 1: top row][lane]
     const int m = blockIdx.z;
-    // the control word is read here and tested once the block's loads are in flight
-    const bool skip = ctl[m].outer_done || (inner_guard && ctl[m].inner_done);
+    // a converged member's blocks return before any load (a group keeps iterating while its slowest
+    // member does, and the loads of the others would be spent for nothing)
+    if (ctl[m].outer_done) return;
+    if (inner_guard && ctl[m].inner_done) return;
     const Level &L = sa.L;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i0 = blockIdx.x * TW, j0 = blockIdx.y * TH;
@@ -657,17 +659,17 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
         unsigned int qq = 0u, actl = 0u, actr = 0u;
         if (ok) {
             if (CODED) {
-                qq = ld_early_nc_u32(L.code + c);                           // left cell low half
-                const unsigned int fl = ld_early_nc_u16(L.fluid + c);
+                qq = *reinterpret_cast<const unsigned int *>(L.code + c);   // left cell low half
+                const unsigned int fl = *reinterpret_cast<const unsigned short *>(L.fluid + c);
                 actl = fl & 0x00ffu; actr = fl & 0xff00u;
             } else {
-                qq = ld_early_nc_u16(L.open + c);                           // left cell low byte
+                qq = *reinterpret_cast<const unsigned short *>(L.open + c);  // left cell low byte
                 actl = qq & 0x00ffu; actr = qq & 0xff00u;
             }
-            fv = ld_early_nc(reinterpret_cast<const T2 *>(fm + c));
-            if (!zero) ev = ld_early_nc(reinterpret_cast<const T2 *>(eim + c));
+            fv = *reinterpret_cast<const T2 *>(fm + c);
+            if (!zero) ev = *reinterpret_cast<const T2 *>(eim + c);
             if (prolong) {
-                const T cv = ld_early_nc(ecm + (long long)(j >> 1) * sa.Pc + (iL >> 1));
+                const T cv = ecm[(long long)(j >> 1) * sa.Pc + (iL >> 1)];
                 if (actl) ev.x += cv;
                 if (actr) ev.y += cv;
             }
@@ -691,7 +693,6 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
         f0[r] = fv.x; f1[r] = fv.y;
         e0[r] = ev.x; e1[r] = ev.y;
     }
-    if (skip) return;                                           // uniform in the block
     xb[1][w][0][lane] = T2{e0[0], e1[0]};
     xb[1][w][1][lane] = T2{e0[R - 1], e1[R - 1]};
     __syncthreads();
