@@ -557,7 +557,8 @@ static int alloc_buffers(envar_handle h)
             h->pb.lev_t[l] = lt;
         }
     }
-    h->pt.nblk = cdiv(h->g.nx, 32) * cdiv(h->g.ny, 16);   // capacity for every partial-producing tiling
+    // capacity for every partial-producing tiling (per-block partials)
+    h->pt.nblk = std::max(cdiv(h->g.nx, 32) * cdiv(h->g.ny, 16), rz_parts_max(h->lev[0], h->mixed));
     h->pt.stride = M;
     DA(h->pt.part, (size_t)RS_COUNT * M * h->pt.nblk);
     DA(h->pt.red, M);

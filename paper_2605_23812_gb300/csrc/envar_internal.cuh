@@ -78,9 +78,9 @@ enum RedSlot { RS_RMAX = 0, RS_XSUM = 1, RS_RZ0 = 2, RS_RZA = 3, RS_RZB = 4, RS_
 struct MemberRed {
     unsigned int cnt[RS_COUNT];   // arrival tickets
     double val[RS_COUNT];         // max |r| (outer residual), sum x, r^T z (start, ping, pong), p^T A p
-    // FP32 inner CG: alpha = (r^T z)_k / p^T A p and beta = (r^T z)_k / (r^T z)_(k-1), each formed once
-    // by the block that completes its last total (a double division in every thread would occupy
-    // the FP64 pipe, about 1/64 of the FP32 rate, for longer than the kernel's memory traffic)
+    // FP32 inner CG: alpha = (r^T z)_k / p^T A p and beta = (r^T z)_k / (r^T z)_(k-1), each formed
+    // once per member (a double division in every thread would occupy the FP64 pipe, about 1/64 of
+    // the FP32 rate, for longer than the kernel's memory traffic)
     float fa, fb;
 };
 struct Partials {
@@ -346,6 +346,8 @@ struct CoarseLayout {
 };
 CoarseLayout coarse_layout(const Level *lev, int lc, int nlev, size_t tsz);
 template <class TM> void prepare_poisson_kernels();
+// The largest number of r^T z partials (blocks per member) a level-0 post-smoothing launch leaves (any sweep count).
+int rz_parts_max(const Level &L0, bool mixed);
 template <class TM>
 void launch_vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc,
                    const Partials &pt, MemberCtl *ctl, cudaStream_t st);

@@ -17,6 +17,8 @@
 // partial, and the last block to arrive (atomic ticket) sums the partials in a fixed order and
 // publishes the scalar and the convergence flags in the member's control block.  Every loop is a
 // fixed number of launches (graph friendly); converged members' blocks exit at once.
+#include <algorithm>
+
 #include "df64.cuh"
 #include "envar_internal.cuh"
 
@@ -47,8 +49,9 @@ template <class T> __device__ __forceinline__ T lev0_cy(const Level &L);
 template <> __device__ __forceinline__ float lev0_cy<float>(const Level &L) { return L.cyf; }
 template <> __device__ __forceinline__ double lev0_cy<double>(const Level &L) { return L.cy; }
 
-// Inner CG scalars.  FP32 vectors read the FP32 copies formed once per member by the block that
-// completes the total (set_alpha, set_beta: one thread); FP64 vectors divide in FP64.
+// Inner CG scalars.  FP32 vectors read the FP32 copies formed once per member, alpha by the SpMV
+// block that completes p^T A p (set_alpha), beta by the r^T z finisher (k_rz_finish); FP64
+// vectors divide in FP64.
 __device__ __forceinline__ int rz_slot(int k) { return (k & 1) ? RS_RZB : RS_RZA; }
 template <class T> __device__ __forceinline__ T cg_alpha(const RedCtx &rc, int m, int k);
 template <> __device__ __forceinline__ float cg_alpha<float>(const RedCtx &rc, int m, int) { return rc.red[m].fa; }
@@ -56,21 +59,27 @@ template <> __device__ __forceinline__ double cg_alpha<double>(const RedCtx &rc,
 {
     return rc.red[m].val[rz_slot(k)] / rc.red[m].val[RS_PQ];
 }
+// p^T A p of iteration k complete: alpha_k = (r^T z)_k / p^T A p
+__device__ __forceinline__ void set_alpha(const RedCtx &rc, int m, int k, double pq)
+{
+    rc.red[m].fa = (float)(rc.red[m].val[rz_slot(k)] / pq);
+}
 template <class T> __device__ __forceinline__ T cg_beta(const RedCtx &rc, int m, int k);
 template <> __device__ __forceinline__ float cg_beta<float>(const RedCtx &rc, int m, int) { return rc.red[m].fb; }
 template <> __device__ __forceinline__ double cg_beta<double>(const RedCtx &rc, int m, int k)
 {
     return rc.red[m].val[rz_slot(k)] / rc.red[m].val[rz_slot(k + 1)];
 }
-// p^T A p of iteration k complete: alpha_k = (r^T z)_k / p^T A p
-__device__ __forceinline__ void set_alpha(const RedCtx &rc, int m, int k, double pq)
+// The dot product r^T z of the level-0 post-smoothing is left as one partial per block (no ticket:
+// a block that waited for an atomic round trip at its end would hold its SM slot through it);
+// k_rz_finish forms the total.  A df64 block total is stored as its float pair in the 8-byte slot,
+// a double as itself (thread 0; v is the block total).
+__device__ __forceinline__ void store_partial(double *p, f2 v) { *reinterpret_cast<float2 *>(p) = make_float2(v.h, v.l); }
+__device__ __forceinline__ void store_partial(double *p, double v) { *p = v; }
+template <class V> __device__ __forceinline__ void write_block_partial(const RedCtx &rc, int slot, int m, V v)
 {
-    rc.red[m].fa = (float)(rc.red[m].val[rz_slot(k)] / pq);
-}
-// (r^T z)_(k+1) complete (slot rz_slot(k + 1)): beta_(k+1) = (r^T z)_(k+1) / (r^T z)_k
-__device__ __forceinline__ void set_beta(const RedCtx &rc, int m, int k, double rz)
-{
-    rc.red[m].fb = (float)(rz / rc.red[m].val[rz_slot(k)]);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        store_partial(rc.part + ((long long)slot * rc.stride + m) * rc.nblk + blockIdx.x + gridDim.x * blockIdx.y, v);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -395,7 +404,6 @@ struct SmoothArgs {
     int order;            // 0: red then black; 1: black then red
     int flags;
     int k;                // inner iteration (for the dot slot)
-    double rtol2;         // SF_DOT: the inner loop stops once r^T z <= rtol2 (r^T z)_0
 };
 
 // Thread layout: a block of 384 threads covers a 64 x 42 region (tile + halo); each thread owns a
@@ -535,22 +543,8 @@ __global__ void __launch_bounds__(SC_THREADS, sizeof(T) == 4 ? 2 : 1) k_smooth(S
             fc[(long long)m * sa.Sc + (long long)J * sa.Pc + I] = sum;
         }
     }
-    if (sa.flags & (SF_DOT | SF_INIT_DOT)) {
-        const auto dtot = dot.total();
-        double tot;
-        int slot = (sa.flags & SF_INIT_DOT) ? RS_RZA : (((sa.k + 1) & 1) ? RS_RZB : RS_RZA);
-        if (publish_partial(rc, slot, m, dtot, false, &tot) && threadIdx.x == 0) {
-            rc.red[m].val[slot] = tot;
-            if (sa.flags & SF_INIT_DOT) {
-                rc.red[m].val[RS_RZ0] = tot;
-                if (!(tot > 0.0)) ctl[m].inner_done = 1;
-            } else {
-                set_beta(rc, m, sa.k, tot);
-                if (!(tot > sa.rtol2 * rc.red[m].val[RS_RZ0]))
-                    ctl[m].inner_done = 1;   // inner convergence, decided where the total is formed
-            }
-        }
-    }
+    if (sa.flags & (SF_DOT | SF_INIT_DOT))   // (r^T z)_0 or (r^T z)_(k+1): per-block partials
+        write_block_partial(rc, (sa.flags & SF_INIT_DOT) ? rz_slot(0) : rz_slot(sa.k + 1), m, dot.total());
 }
 #undef KW
 #undef KE
@@ -783,22 +777,8 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_smoothw(SmoothArgs sa, const 
             }
         }
     }
-    if (want_dot) {
-        const auto dtot = dot.total();
-        double tot;
-        int slot = (sa.flags & SF_INIT_DOT) ? RS_RZA : (((sa.k + 1) & 1) ? RS_RZB : RS_RZA);
-        if (publish_partial(rc, slot, m, dtot, false, &tot) && threadIdx.x == 0) {
-            rc.red[m].val[slot] = tot;
-            if (sa.flags & SF_INIT_DOT) {
-                rc.red[m].val[RS_RZ0] = tot;
-                if (!(tot > 0.0)) ctl[m].inner_done = 1;
-            } else {
-                set_beta(rc, m, sa.k, tot);
-                if (!(tot > sa.rtol2 * rc.red[m].val[RS_RZ0]))
-                    ctl[m].inner_done = 1;   // inner convergence, decided where the total is formed
-            }
-        }
-    }
+    if (want_dot)   // (r^T z)_0 or (r^T z)_(k+1): per-block partials
+        write_block_partial(rc, (sa.flags & SF_INIT_DOT) ? rz_slot(0) : rz_slot(sa.k + 1), m, dot.total());
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1088,6 +1068,63 @@ static void launch_smooth(int M, int nsweep, cudaStream_t st, const SmoothArgs &
     else launch_smooth_b<T, false>(M, nsweep, st, sa, f, ein, e, ec, fc, rc, ctl, inner_guard);
 }
 
+// r^T z total of each member from the level-0 post-smoothing's n block partials, one warp per
+// member, in a fixed order (lane l takes partials l, l + 32, ...; lane 0's butterfly total; df64 on
+// the FP32 pipe for FP32 vectors), and what hangs on it: the start value (r^T z)_0 and a breakdown
+// test (init), or beta_(k+1) and the inner convergence test (r^T z)_(k+1) <= rtol2 (r^T z)_0.
+// Members whose smoothing did not run (converged) are skipped.
+template <class T>
+__global__ void k_rz_finish(RedCtx rc, MemberCtl *ctl, int M, int n, int init, int k, double rtol2, int inner_guard)
+{
+    const int m = blockIdx.x, lane = threadIdx.x;
+    if (m >= M) return;
+    if (ctl[m].outer_done || (inner_guard && ctl[m].inner_done)) return;
+    const int slot = init ? rz_slot(0) : rz_slot(k + 1);
+    const double *pp = rc.part + ((long long)slot * rc.stride + m) * rc.nblk;
+    double tot;
+    if constexpr (sizeof(T) == 4) {
+        const float2 *pf = reinterpret_cast<const float2 *>(pp);
+        f2 a{0.f, 0.f};
+        for (int q = lane; q < n; q += 32) {
+            const float2 v = __ldcg(pf + q);
+            a = df_add(a, f2{v.x, v.y});
+        }
+        a = warp_sum_df(a);
+        tot = (lane == 0) ? df_to_d(a) : 0.0;
+    } else {
+        double a = 0.0;
+        for (int q = lane; q < n; q += 32) a += __ldcg(pp + q);
+        tot = warp_sum(a);
+    }
+    if (lane != 0) return;
+    rc.red[m].val[slot] = tot;
+    if (init) {
+        rc.red[m].val[RS_RZ0] = tot;
+        if (!(tot > 0.0)) ctl[m].inner_done = 1;
+    } else {
+        rc.red[m].fb = (float)(tot / rc.red[m].val[rz_slot(k)]);
+        if (!(tot > rtol2 * rc.red[m].val[RS_RZ0])) ctl[m].inner_done = 1;   // inner convergence
+    }
+}
+
+// Blocks per member of the level-0 post-smoothing launch with nu sweep pairs: the r^T z partials
+// it leaves (launch_smooth: the warp-row kernel with 12 warps on a level with open-face bits, else
+// the column-segment kernel).
+template <class T> int rz_parts(const Level &L0, int nu)
+{
+    if (L0.open) {
+        const int H = s0_halo(nu), TW = S0_COLS - 2 * H, TH = 12 * S0<T>::R - 2 * H;
+        return cdiv(L0.nx, TW) * cdiv(L0.ny, TH);
+    }
+    return cdiv(L0.nx, sc_tw(nu)) * cdiv(L0.ny, sc_th(nu));
+}
+int rz_parts_max(const Level &L0, bool mixed)
+{
+    int n = 0;
+    for (int nu = 1; nu <= 3; ++nu) n = std::max(n, mixed ? rz_parts<float>(L0, nu) : rz_parts<double>(L0, nu));
+    return n;
+}
+
 template <class T>
 static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B, const PoissonCfg &pc, RedCtx rc,
                    MemberCtl *ctl, int inner_guard, int k, int init, cudaStream_t st)
@@ -1123,12 +1160,15 @@ static void vcycle(const Grid &g, const Level *lev, int M, const PoissonBufs &B,
         int flags = SF_PROLONG;
         if (l == 0) flags |= init ? SF_INIT_DOT : SF_DOT;
         const int nu = level_sweeps(pc, l, pc.nu_post);
-        SmoothArgs sa{L, Lc.P, Lc.S, nu, 1, flags, k, pc.inner_rtol2};
+        SmoothArgs sa{L, Lc.P, Lc.S, nu, 1, flags, k};
         const T *f = (l == 0) ? f0 : (const T *)B.lev_f[l];
         T *e = (l == 0) ? z : (T *)B.lev_e[l];
         launch_smooth<T>(M, nu, st, sa, f, (const T *)B.lev_t[l], e, (const T *)B.lev_e[l + 1], (T *)nullptr,
                          rc, ctl, inner_guard);
     }
+    // the r^T z total of the post-smoothing (one warp per member)
+    k_rz_finish<T><<<M, 32, 0, st>>>(rc, ctl, M, rz_parts<T>(lev[0], pc.nu_post), init, k, pc.inner_rtol2, inner_guard);
+    count_launches(1);
 }
 
 // One application of the multigrid preconditioner z = M r (level-0 arrays of every member slot).
@@ -1312,7 +1352,7 @@ int launch_poisson_single(int which, const Grid &g, const Level *lev, int M, con
         return 0;
     }
     case 2: {
-        SmoothArgs sa{L0, L1.P, L1.S, pc.nu_post, 1, SF_PROLONG | SF_DOT, 1, pc.inner_rtol2};
+        SmoothArgs sa{L0, L1.P, L1.S, pc.nu_post, 1, SF_PROLONG | SF_DOT, 1};
         launch_smooth<TM>(M, pc.nu_post, st, sa, r, (const TM *)B.lev_t[0], z, (const TM *)B.lev_e[1], (TM *)nullptr,
                           rc, ctl, 0);
         return 0;
