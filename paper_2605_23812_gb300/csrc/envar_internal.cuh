@@ -377,9 +377,13 @@ void launch_outflow_mx(const Grid &g, int M, const MixState &s, double *ubc, Mem
 void launch_predict_rhs_mx(const Grid &g, const MixConst &K, int M, const MixState &s, const double *ubc,
                            const float *inh, const float *inl, const MemberCtl *ctl, const MemberRed *red,
                            long long nfluid, cudaStream_t st);
+// The df64 residual leaves block partials; finish = 1 forms the totals and the convergence test
+// right after it (k_res_finish), finish = 0 leaves them to the refinement loop's condition kernel
+// (res_finish_member in res_finish.cuh).
 void launch_outer_residual_mx(const Grid &g, const Level &L0, const MixConst &K, int M, const MixState &s, float *r,
-                              float *e, const RedCtx &rc, MemberCtl *ctl, double rtol_abs, int count_it,
+                              float *e, const RedCtx &rc, MemberCtl *ctl, double rtol_abs, int count_it, int finish,
                               cudaStream_t st);
+int outer_residual_parts_mx(const Grid &g);
 // The last inner CG update fused with the refinement's x += e (df64 x).
 void launch_axpy_last_mx(const Grid &g, int M, const MixState &s, const float *e, const float *p, const RedCtx &rc,
                          MemberCtl *ctl, int k, cudaStream_t st);

@@ -12,6 +12,7 @@
 // of the corrected field equals -dt (b - A x)/(dx dy) to df64 rounding.
 #include "df64.cuh"
 #include "envar_internal.cuh"
+#include "res_finish.cuh"
 #include "../../include/envar.h"
 
 namespace envar {
@@ -325,7 +326,9 @@ void launch_predict_rhs_mx(const Grid &g, const MixConst &K, int M, const MixSta
 
 // ---------------------------------------------------------------------------- outer residual (df64)
 // k_outer_residual_mx: r = b - A x in df64 on every fluid cell (FP32 r = its leading word; 0 on the
-// other cells), e = 0, and per member the maximum |r| and the fluid sum of x.  A warp owns a
+// other cells), e = 0, and per block the maximum |r| and the fluid sum of x as partials (no ticket:
+// the totals, the convergence test and the refinement count are formed after the kernel by one
+// warp per member, res_finish_member).  A warp owns a
 // 64-column strip of OR_ROWS rows, lane l the cell pair (2l, 2l+1): x of the strip's rows and of
 // the rows above and below, b, the open-face and fluid bits and the strip's edge cells are all
 // loaded first (in flight together, before the control word is tested), east / west neighbours
@@ -339,8 +342,7 @@ __global__ void __launch_bounds__(OR_WARPS * 32) k_outer_residual_mx(Grid g, Lev
                                                                      const float *__restrict__ xh,
                                                                      const float *__restrict__ xl,
                                                                      float *__restrict__ r, float *__restrict__ e,
-                                                                     RedCtx rc, MemberCtl *ctl, double rtol_abs,
-                                                                     int count_it)
+                                                                     RedCtx rc, const MemberCtl *ctl)
 {
     constexpr int R = OR_ROWS, NR = OR_ROWS + 2;
     const int m = blockIdx.z;
@@ -426,18 +428,18 @@ __global__ void __launch_bounds__(OR_WARPS * 32) k_outer_residual_mx(Grid g, Lev
     }
     const float rm = block_max_f(rmax);
     const f2 xsum = block_sum_df(xs);
-    double tot;
-    bool last1 = publish_partial(rc, RS_RMAX, m, rm, true, &tot);
-    if (last1 && threadIdx.x == 0) {
-        rc.red[m].val[RS_RMAX] = tot;
-        int done = (tot <= rtol_abs) ? 1 : 0;
-        ctl[m].outer_done = done;
-        ctl[m].inner_done = done;
-        if (!done && count_it) ctl[m].outer_its += 1;
+    if (threadIdx.x == 0) {
+        const long long blk = blockIdx.x + gridDim.x * blockIdx.y;
+        float *pr = reinterpret_cast<float *>(rc.part + ((long long)RS_RMAX * rc.stride + m) * rc.nblk + blk);
+        *pr = rm;
+        *reinterpret_cast<float2 *>(rc.part + ((long long)RS_XSUM * rc.stride + m) * rc.nblk + blk) =
+            make_float2(xsum.h, xsum.l);
     }
-    __syncthreads();
-    bool last2 = publish_partial(rc, RS_XSUM, m, xsum, false, &tot);
-    if (last2 && threadIdx.x == 0) rc.red[m].val[RS_XSUM] = tot;
+}
+
+__global__ void k_res_finish(RedCtx rc, MemberCtl *ctl, int M, int n, double rtol_abs, int count_it)
+{
+    if (blockIdx.x < M) res_finish_member(rc, ctl, blockIdx.x, n, rtol_abs, count_it);
 }
 
 // k_axpy_last_mx: the last inner CG update fused with the refinement's update of x: e + alpha p is
@@ -487,14 +489,19 @@ __global__ void __launch_bounds__(128) k_axpy_last_mx(Grid g, float *__restrict_
     if (moving && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctl[m].inner_its += 1;
 }
 
+int outer_residual_parts_mx(const Grid &g) { return cdiv(g.nx, 64) * cdiv(g.ny, OR_WARPS * OR_ROWS); }
+
 void launch_outer_residual_mx(const Grid &g, const Level &L0, const MixConst &K, int M, const MixState &s, float *r,
-                              float *e, const RedCtx &rc, MemberCtl *ctl, double rtol_abs, int count_it,
+                              float *e, const RedCtx &rc, MemberCtl *ctl, double rtol_abs, int count_it, int finish,
                               cudaStream_t st)
 {
     dim3 grd(cdiv(g.nx, 64), cdiv(g.ny, OR_WARPS * OR_ROWS), M);
-    k_outer_residual_mx<<<grd, OR_WARPS * 32, 0, st>>>(g, L0, K, s.bh, s.bl, s.xh, s.xl, r, e, rc, ctl, rtol_abs,
-                                                       count_it);
+    k_outer_residual_mx<<<grd, OR_WARPS * 32, 0, st>>>(g, L0, K, s.bh, s.bl, s.xh, s.xl, r, e, rc, ctl);
     count_launches(1);
+    if (finish) {
+        k_res_finish<<<M, 32, 0, st>>>(rc, ctl, M, outer_residual_parts_mx(g), rtol_abs, count_it);
+        count_launches(1);
+    }
 }
 
 void launch_axpy_last_mx(const Grid &g, int M, const MixState &s, const float *e, const float *p, const RedCtx &rc,

@@ -21,6 +21,7 @@
 
 #include "df64.cuh"
 #include "envar_internal.cuh"
+#include "res_finish.cuh"
 
 namespace envar {
 
@@ -1206,11 +1207,14 @@ unsigned long long conditional_body_launches()
 // refinements were made in this step (reset = 1 before the loop starts the count at zero).  The
 // count bounds the loop whatever the members' state.  body_kernels > 0: this launch closes a body
 // of that many kernels (itself included), which is added to the device launch counter.
-__global__ void k_refine_condition(const MemberCtl *__restrict__ ctl, int M, int *count, int max_outer, int reset,
-                                   int body_kernels, cudaGraphConditionalHandle handle)
+__global__ void k_refine_condition(MemberCtl *ctl, int M, int *count, int max_outer, int reset, int body_kernels,
+                                   cudaGraphConditionalHandle handle, RedCtx rc, int finish_n, double rtol_abs)
 {
     __shared__ int s_any;
     if (threadIdx.x == 0) s_any = 0;
+    // the df64 residual's totals first (finish_n > 0: its block partials per member), one warp per member
+    if (finish_n > 0)
+        for (int m = threadIdx.x >> 5; m < M; m += blockDim.x >> 5) res_finish_member(rc, ctl, m, finish_n, rtol_abs, 1);
     __syncthreads();
     int any = 0;
     for (int m = threadIdx.x; m < M; m += blockDim.x) any |= !ctl[m].outer_done;
@@ -1224,12 +1228,15 @@ __global__ void k_refine_condition(const MemberCtl *__restrict__ ctl, int M, int
     }
 }
 
+// finish: 1 forms the df64 residual's totals right after it, 0 leaves them to the condition kernel
+// that follows (the FP64 residual forms its own)
 template <class TM>
 static void outer_residual(const Grid &g, const Level &L0, int M, const PoissonBufs &B, const PoissonCfg &pc, RedCtx rc,
-                           MemberCtl *ctl, int count_it, cudaStream_t st)
+                           MemberCtl *ctl, int count_it, int finish, cudaStream_t st)
 {
     if (pc.df_outer) {
-        launch_outer_residual_mx(g, L0, pc.mc, M, B.ms, (float *)B.r, (float *)B.e, rc, ctl, pc.rtol_abs, count_it, st);
+        launch_outer_residual_mx(g, L0, pc.mc, M, B.ms, (float *)B.r, (float *)B.e, rc, ctl, pc.rtol_abs, count_it,
+                                 finish, st);
     } else {
         dim3 grd(cdiv(g.nx, TILE_W), cdiv(g.ny, TILE_H), M);
         k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, (TM *)B.r, (TM *)B.e, rc, ctl, pc.rtol_abs,
@@ -1288,12 +1295,14 @@ void launch_pressure_solve(const Grid &g, const Level *lev, int M, const Poisson
     bool conditional = pc.conditional_loop && B.refine_count &&
                        cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, &edata, &ndeps) == cudaSuccess &&
                        cs == cudaStreamCaptureStatusActive;
+    const int finish_n = pc.df_outer ? outer_residual_parts_mx(g) : 0;   // totals formed by the condition kernel
     if (conditional) {
-        outer_residual<TM>(g, L0, M, B, pc, rc, ctl, 1, st);
         cudaGraphConditionalHandle handle;
         conditional = cudaGraphConditionalHandleCreate(&handle, graph, 0, 0) == cudaSuccess;
         if (conditional) {
-            k_refine_condition<<<1, 128, 0, st>>>(ctl, M, B.refine_count, pc.max_outer, 1, 0, handle);
+            outer_residual<TM>(g, L0, M, B, pc, rc, ctl, 1, 0, st);
+            k_refine_condition<<<1, 128, 0, st>>>(ctl, M, B.refine_count, pc.max_outer, 1, 0, handle, rc, finish_n,
+                                                  pc.rtol_abs);
             count_launches(1);
             cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, &edata, &ndeps);
             cudaGraphNodeParams np{};
@@ -1314,9 +1323,10 @@ void launch_pressure_solve(const Grid &g, const Level *lev, int M, const Poisson
                 if (ok) {
                     const long long c0 = captured_launches();
                     refinement<TM>(g, lev, M, B, pc, rc, ctl, bs);
-                    outer_residual<TM>(g, L0, M, B, pc, rc, ctl, 1, bs);
+                    outer_residual<TM>(g, L0, M, B, pc, rc, ctl, 1, 0, bs);
                     const int nb = (int)(captured_launches() - c0) + 1;
-                    k_refine_condition<<<1, 128, 0, bs>>>(ctl, M, B.refine_count, pc.max_outer, 0, nb, handle);
+                    k_refine_condition<<<1, 128, 0, bs>>>(ctl, M, B.refine_count, pc.max_outer, 0, nb, handle, rc,
+                                                          finish_n, pc.rtol_abs);
                     count_launches(1);
                     ok = cudaStreamEndCapture(bs, &body) == cudaSuccess;
                 }
@@ -1329,7 +1339,7 @@ void launch_pressure_solve(const Grid &g, const Level *lev, int M, const Poisson
         }
     }
     for (int o = 0; o <= pc.max_outer; ++o) {
-        outer_residual<TM>(g, L0, M, B, pc, rc, ctl, o < pc.max_outer ? 1 : 0, st);
+        outer_residual<TM>(g, L0, M, B, pc, rc, ctl, o < pc.max_outer ? 1 : 0, 1, st);
         if (o == pc.max_outer) break;
         refinement<TM>(g, lev, M, B, pc, rc, ctl, st);
     }
@@ -1361,7 +1371,7 @@ int launch_poisson_single(int which, const Grid &g, const Level *lev, int M, con
     case 4: launch_axpy<TM>(g, M, e, r, pv[0], q, rc, ctl, 1, st); break;
     case 5:
         if (pc.df_outer) {
-            launch_outer_residual_mx(g, L0, pc.mc, M, B.ms, (float *)r, (float *)e, rc, ctl, -1.0, 0, st);
+            launch_outer_residual_mx(g, L0, pc.mc, M, B.ms, (float *)r, (float *)e, rc, ctl, -1.0, 0, 0, st);
             return 0;
         }
         k_outer_residual<TM><<<grd, TILE_THREADS, 0, st>>>(g, L0, B.b, B.x, r, e, rc, ctl, -1.0, 0);
