@@ -78,10 +78,10 @@ def main():
     n = args.warmup + args.window
     geo, ic = {}, {}
     if args.paper_workload:
-        box = (-1.2, 2.5, -1.0, 0.5)
-        geo = dict(x0=box[0], x1=box[1], y0=box[2], y1=box[3], inlet_delta=1e-6, lip_slip=1,
-                   noslip_span=(-0.4, 1.75))
-        ic = dict(box=box, delta=1e-6)
+        box = synth.PAPER_BOX
+        geo = dict(x0=box[0], x1=box[1], y0=box[2], y1=box[3], inlet_delta=synth.PAPER_INLET_DELTA, lip_slip=1,
+                   noslip_span=synth.PAPER_NOSLIP_SPAN)
+        ic = dict(box=box, delta=synth.PAPER_INLET_DELTA)
     res = {}
     paths = [("mixed", pkg.MIXED, dict(div_tol=1e-10))]
     if not args.skip_fp64:

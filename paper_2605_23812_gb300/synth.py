@@ -8,6 +8,9 @@ CUDA path (through the C-ABI) and the CPU oracle take these arrays as inputs.
   Gaussian noise of the given amplitude.  Each solver applies its own boundary
   rules (walls, inlet, outlet) when it loads them.
 * ``weights``: seeded ensemble weights w (the reduced control vector).
+* ``PAPER_BOX``, ``PAPER_NOSLIP_SPAN``, ``PAPER_INLET_DELTA``: the paper's own flow configuration
+  (its Table 1 geometry: the box [-L1, D + L2] x [-D, H], the no-slip part [-L1_slip, D + L2_slip]
+  of the lower wall, and a uniform inflow written as an erf profile of negligible width).
 """
 from __future__ import annotations
 
@@ -16,6 +19,9 @@ import math
 import numpy as np
 
 CAVITY_BOX = (-1.2, 2.5, -1.0, 1.0)
+PAPER_BOX = (-1.2, 2.5, -1.0, 0.5)
+PAPER_NOSLIP_SPAN = (-0.4, 1.75)
+PAPER_INLET_DELTA = 1e-6          # erf(y / delta) = 1 on every fluid row: uniform inflow
 
 
 def cavity_ic(nx: int, ny: int, box=CAVITY_BOX, seed: int = 1234, noise: float = 1e-3,

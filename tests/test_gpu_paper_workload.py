@@ -13,8 +13,9 @@ from paper_2605_23812_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-BOX = (-1.2, 2.5, -1.0, 0.5)
-DELTA = 1e-6          # erf(y / DELTA) = 1 on every fluid row: uniform inflow
+BOX = synth.PAPER_BOX
+DELTA = synth.PAPER_INLET_DELTA
+SPAN = synth.PAPER_NOSLIP_SPAN
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -25,14 +26,14 @@ def _built():
 
 def paper_cfg(nx, ny, **kw):
     base = dict(x0=BOX[0], x1=BOX[1], y0=BOX[2], y1=BOX[3], Re=6250.0, inlet_delta=DELTA, lip_slip=1,
-                noslip_span=(-0.4, 1.75), forcing_y_only=1, cost_mode=pkg.COST_SENSORS, precision=pkg.FP64_BATCHED,
+                noslip_span=SPAN, forcing_y_only=1, cost_mode=pkg.COST_SENSORS, precision=pkg.FP64_BATCHED,
                 div_tol=1e-12, max_outer=4, max_inner=40, inner_rtol=1e-12)
     base.update(kw)
     return pkg.default_config(nx, ny, **base)
 
 
 def paper_params(nx, ny):
-    return oracle.cavity_params(nx, ny, 6250.0, box=BOX, inlet_delta=DELTA, lip_slip=1, noslip_span=(-0.4, 1.75))
+    return oracle.cavity_params(nx, ny, 6250.0, box=BOX, inlet_delta=DELTA, lip_slip=1, noslip_span=SPAN)
 
 
 def test_paper_workload_trajectories_and_ensemble():

@@ -6,6 +6,7 @@ Each pin is chosen so that a plausible mistake (a dropped term, a wrong sign, a
 transposed index, a wrong boundary reflection) fails at least one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -941,3 +942,39 @@ def test_faces_to_control_is_transpose_of_control_to_faces():
     lhs = (fu * gu).sum() + (fv * gv).sum()
     rhs = f @ oracle.faces_to_control(P, gu, gv)
     assert lhs == pytest.approx(rhs, rel=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# the paper's own flow configuration against its printed geometry (golden fixture)
+# ----------------------------------------------------------------------------
+def _table1():
+    vals = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_table1_geometry.txt")
+    for line in open(path):
+        f = line.split("#")[0].split()
+        if len(f) == 2:
+            vals[f[0]] = float(f[1])
+    return vals
+
+
+def test_paper_workload_geometry_matches_table_1():
+    """The paper workload (its Table 1, tests/golden/paper_table1_geometry.txt): the box
+    [-L1, D + L2] x [-D, H], the no-slip part [-L1_slip, D + L2_slip] of the lower wall, and on that
+    box the oracle's mask: every cell of the channel (y > 0) fluid, below it exactly the cavity
+    0 < x < D, so the fluid area is (L1 + D + L2) H + D^2 on a grid whose faces meet the edges."""
+    t = _table1()
+    assert synth.PAPER_BOX == pytest.approx((-t["L1"], t["D"] + t["L2"], -t["D"], t["H"]), abs=1e-15)
+    assert synth.PAPER_NOSLIP_SPAN == pytest.approx((-t["L1_slip"], t["D"] + t["L2_slip"]), abs=1e-15)
+    nx, ny = 74, 30                        # dx = dy = 0.05
+    P = oracle.cavity_params(nx, ny, 6250.0, box=synth.PAPER_BOX, inlet_delta=synth.PAPER_INLET_DELTA, lip_slip=1,
+                             noslip_span=synth.PAPER_NOSLIP_SPAN)
+    assert P.slip_lo == pytest.approx(-t["L1_slip"]) and P.slip_hi == pytest.approx(t["D"] + t["L2_slip"])
+    F = oracle.fluid_mask(P).astype(bool)
+    xc = P.x0 + (np.arange(nx) + 0.5) * P.dx
+    yc = P.y0 + (np.arange(ny) + 0.5) * P.dy
+    channel = yc > 0
+    assert F[channel].all()
+    cavity_cols = (xc > 0) & (xc < t["D"])
+    assert np.array_equal(F[~channel], np.broadcast_to(cavity_cols, F[~channel].shape))
+    area = F.sum() * P.dx * P.dy
+    assert area == pytest.approx((t["L1"] + t["D"] + t["L2"]) * t["H"] + t["D"] ** 2, rel=1e-12)
