@@ -2,7 +2,7 @@
 
     python -m paper_2605_23812_gb300.gradient_study [--nx 512 --ny 256 --Re 7500 --spinup 20000
                                                      --horizon 10000 --members 16,32,64,128,256
-                                                     --snapshots 64 --fd-directions 16]
+                                                     --snapshots 64 --fd-directions 16 --fd-step 0.01]
 
 The open cavity is first spun up from the seeded initial state (mixed precision, no forcing); the
 spun-up state is the initial state of every run below.  The cost is the DOMAIN fluctuation energy
@@ -11,8 +11,8 @@ over the whole horizon (Sec. 4.1), the forcing is zero (w = 0, the first EnVar i
   * reference: dJ/df by the discrete adjoint of the FP64 stepper (Sec. 3.2) with binomial
     checkpointing;
   * the adjoint itself against central differences of the FP64 forward model in --fd-directions
-    smooth random control directions d_k (normalised prior draws; one FP64 batched ensemble whose
-    members carry +h d_k and -h d_k);
+    smooth random control directions d_k (normalised prior draws; one one-member FP64 run per point
+    +h d_k and -h d_k);
   * EnVar: for each ensemble size N, the mixed-precision batched gradient of Eq. (gradient_EnVar) at
     w = 0, g = Y^T h_0 with Y from Eq. (fdapprox) (the explicit contraction), and for comparison the
     scalar-anomaly form (J_i - J_0)/eps, both estimates of E^T dJ/df.
@@ -41,7 +41,7 @@ def main():
     ap.add_argument("--horizon", type=int, default=10000)
     ap.add_argument("--members", default="16,32,64,128,256")
     ap.add_argument("--fd-directions", type=int, default=16)
-    ap.add_argument("--fd-step", type=float, default=1e-3)
+    ap.add_argument("--fd-step", type=float, default=1e-2)
     ap.add_argument("--snapshots", type=int, default=64)
     ap.add_argument("--eps", type=float, default=1e-2)
     args = ap.parse_args()
@@ -83,31 +83,38 @@ def main():
           flush=True)
 
     if args.fd_directions > 0:
-        # central differences of the same FP64 forward model along random unit directions: the
-        # members of one batched ensemble carry +h d_k (k < K) and -h d_k (k >= K), w = 0, eps = h
-        # The directions are smooth prior draws (the library's sampler, another seed), normalised:
-        # white-noise directions force grid-scale modes that the central advection scheme at cell
-        # Reynolds numbers near 50 does not damp, and several such members left the FP64 run
-        # non-finite over the 10k-step horizon.
+        # central differences of the FP64 forward model along smooth random unit directions d_k
+        # (normalised prior draws: the library's sampler, another seed), one member run per point
+        # (+h d_k and -h d_k) on a one-member FP64 handle.  White-noise directions force grid-scale
+        # modes that the central advection scheme at cell Reynolds numbers near 50 does not damp.
         K, hstep = args.fd_directions, args.fd_step
-        fd = pkg.Ensemble(pkg.default_config(nx, ny, Re=args.Re, n_steps=T, n_window=T, n_members=2 * K,
-                                             precision=pkg.FP64_BATCHED, div_tol=1e-9, max_outer=20, max_inner=30,
-                                             inner_rtol=1e-6, eps=hstep, seed=2024), stream=stream)
-        fd.set_initial_state(u0, v0)
-        D = fd.get_ensemble().cpu().numpy()[:, :K]
+        draw = pkg.Ensemble(pkg.default_config(nx, ny, Re=args.Re, n_steps=2, n_window=1, n_members=K,
+                                               precision=pkg.MIXED, seed=2024), stream=stream)
+        D = draw.get_ensemble().cpu().numpy()[:, :K]
+        draw.close()
         D /= np.linalg.norm(D, axis=0)
-        fd.set_ensemble(np.concatenate([D, -D], axis=1))
+        fd = pkg.Ensemble(pkg.default_config(nx, ny, Re=args.Re, n_steps=T, n_window=T, n_members=0,
+                                             precision=pkg.FP64_PLAIN, div_tol=1e-9), stream=stream)
+        fd.set_initial_state(u0, v0)
+        with torch.cuda.stream(stream):
+            fd_solver = fd.autotune(200)
         t0 = time.perf_counter()
-        fd.forward_ensemble(np.zeros(2 * K))
+        Jp, Jm, st = [], [], []
+        for k in range(K):
+            Jp.append(fd.forward_control(hstep * D[:, k]))
+            st.append(int(fd.member_status()[0]))
+            Jm.append(fd.forward_control(-hstep * D[:, k]))
+            st.append(int(fd.member_status()[0]))
         torch.cuda.synchronize()
         t_fd = time.perf_counter() - t0
-        J, _ = fd.cost()
-        cfd = (J[1:K + 1] - J[K + 1:]) / (2 * hstep)
+        cfd = (np.array(Jp) - np.array(Jm)) / (2 * hstep)
         adj_dir = D.T @ g_adj
         print(json.dumps({"adjoint_fd_check": {
-            "directions": K, "h": hstep, "max_rel_err": float(np.abs(adj_dir - cfd).max() / np.abs(cfd).max()),
+            "directions": K, "h": hstep, "path": "FP64, one member per run", "solver": fd_solver,
+            "max_rel_err": float(np.abs(adj_dir - cfd).max() / np.abs(cfd).max()),
             "cos": float(adj_dir @ cfd / (np.linalg.norm(adj_dir) * np.linalg.norm(cfd))),
-            "status": [int(x) for x in fd.member_status()], "J0": float(J[0]), "seconds": t_fd}}), flush=True)
+            "adjoint_directional": [float(x) for x in adj_dir], "central_differences": [float(x) for x in cfd],
+            "status": st, "seconds": t_fd}}), flush=True)
         fd.close()
 
     for N in [int(x) for x in args.members.split(",")]:
