@@ -44,6 +44,9 @@ def main():
     ap.add_argument("--fd-step", type=float, default=1e-2)
     ap.add_argument("--snapshots", type=int, default=64)
     ap.add_argument("--eps", type=float, default=1e-2)
+    ap.add_argument("--fd-batched", default="",
+                    help="also run the FD points as the members of one FP64 batched ensemble with these solver "
+                         "settings, 'max_outer,max_inner,inner_rtol' (e.g. 20,30,1e-6 or 10,2,1e-3)")
     args = ap.parse_args()
     import numpy as np
     import torch
@@ -114,6 +117,25 @@ def main():
             "adjoint_directional": [float(x) for x in adj_dir], "central_differences": [float(x) for x in cfd],
             "seconds": t_fd}}), flush=True)
         fd.close()
+        for spec in [x for x in args.fd_batched.split(";") if x]:
+            mo, mi, rt = spec.split(",")
+            cfg = pkg.default_config(nx, ny, Re=args.Re, n_steps=T, n_window=T, n_members=2 * K,
+                                     precision=pkg.FP64_BATCHED, div_tol=1e-9, eps=hstep, max_outer=int(mo),
+                                     max_inner=int(mi), inner_rtol=float(rt))
+            fb = pkg.Ensemble(cfg, stream=stream)
+            fb.set_initial_state(u0, v0)
+            fb.set_ensemble(np.concatenate([D, -D], axis=1))
+            t0 = time.perf_counter()
+            fb.forward_ensemble(np.zeros(2 * K))
+            torch.cuda.synchronize()
+            tb = time.perf_counter() - t0
+            Jb, _ = fb.cost()
+            cb = (Jb[1:K + 1] - Jb[K + 1:]) / (2 * hstep)
+            print(json.dumps({"fd_batched": {
+                "settings": spec, "seconds": tb, "status": [int(x) for x in fb.member_status()],
+                "max_div": fb.diagnostics()["max_div"],
+                "max_rel_dev_from_one_member_runs": float(np.abs(cb - cfd).max() / np.abs(cfd).max())}}), flush=True)
+            fb.close()
 
     for N in [int(x) for x in args.members.split(",")]:
         cfg = pkg.default_config(nx, ny, Re=args.Re, n_steps=T, n_window=T, n_members=N, precision=pkg.MIXED,
