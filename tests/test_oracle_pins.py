@@ -978,3 +978,38 @@ def test_paper_workload_geometry_matches_table_1():
     assert np.array_equal(F[~channel], np.broadcast_to(cavity_cols, F[~channel].shape))
     area = F.sum() * P.dx * P.dy
     assert area == pytest.approx((t["L1"] + t["D"] + t["L2"]) * t["H"] + t["D"] ** 2, rel=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# planted mistakes in the core arithmetic: each must make an independent pin fail
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("old,new,pin", [
+    # sign of the advective cross term d(uv)/dy of the u equation
+    ("A = (fe * fe - fw * fw) / dx + (un_c * vn_c - us_c * vs_c) / dy;",
+     "A = (fe * fe - fw * fw) / dx - (un_c * vn_c - us_c * vs_c) / dy;",
+     "test_manufactured_solution_second_order"),
+    # the domain cost normalised by n_w + 1 window samples instead of n_w
+    ("jd *= s->dx * s->dy / (2.0 * n_window);",
+     "jd *= s->dx * s->dy / (2.0 * (n_window + 1));",
+     "test_costs_closed_form_on_stokes_decay"),
+    # the sensor cost without its factor 1/2
+    ("        js *= 0.5;",
+     "        js *= 1.0;",
+     "test_costs_closed_form_on_stokes_decay"),
+    # the prior term of Eq. (gradient_EnVar) with N instead of N - 1
+    ("g[i] = (J[i + 1] - J[0]) / eps + (double)(N - 1) * w[i];",
+     "g[i] = (J[i + 1] - J[0]) / eps + (double)N * w[i];",
+     "test_gradient_quadratic_closed_form"),
+    # the exact DOMAIN contraction against the perturbed observation instead of h_0
+    ("            acc += yk * jb->h0[k];",
+     "            acc += yk * hi[k];",
+     "test_domain_gradient_exact_for_linear_dynamics"),
+])
+def test_core_pins_fail_on_planted_mistakes(tmp_path, old, new, pin):
+    """Plant one plausible mistake in a copy of the oracle: the named pin, which does not restate
+    the formula it checks, must fail on it."""
+    if pin == "test_manufactured_solution_second_order":
+        pytest.importorskip("sympy")
+    with oracle.planted_mistake(old, new, str(tmp_path)):
+        with pytest.raises(AssertionError):
+            globals()[pin]()
