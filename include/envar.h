@@ -49,7 +49,7 @@ enum {
     ENVAR_EDEVICE = -5     /* device is not an sm_103 GPU */
 };
 
-/* Precision / batching of the forward ensemble (spec patterns 1 and 2). */
+/* Precision / batching of the forward ensemble (batching and precision). */
 enum {
     ENVAR_FP64_PLAIN = 0,   /* one member at a time, all arithmetic FP64 */
     ENVAR_FP64_BATCHED = 1, /* all N+1 members per launch, all arithmetic FP64 */
@@ -362,8 +362,8 @@ int envar_autotune(envar_handle h, int probe_steps, double *best_ms_per_step, in
 /* The handle's configuration as currently used (after envar_autotune, its solver parameters). */
 int envar_get_config(envar_handle h, envar_config *cfg);
 
-/* Batches of uneven member groups (spec pattern 1: members of uneven grid sizes and horizons
- * advancing together).  A batch advances several batched handles -- each its own grid size, Reynolds
+/* Batches of uneven member groups (members of uneven grid sizes and horizons advancing
+ * together).  A batch advances several batched handles -- each its own grid size, Reynolds
  * number, horizon, ensemble and solver parameters (tune each with envar_autotune first) -- in one
  * captured CUDA graph per chunk, which holds the next c_k time steps of every handle k as parallel
  * branches (each handle's member groups branch further).  c_k = n_steps_k / n_chunks with n_chunks

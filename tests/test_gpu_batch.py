@@ -1,4 +1,4 @@
-"""Uneven member groups in one batch (spec pattern 1): handles of different grid sizes,
+"""Uneven member groups in one batch: handles of different grid sizes,
 Reynolds numbers, horizons and ensemble sizes advance together, one captured CUDA graph per chunk.
 Every handle runs the same kernels on the same data as in its own forward run, so costs, gradients
 and states must agree bit for bit with the separate runs, and the first of them with the oracle."""

@@ -2,7 +2,8 @@
 Table 1): channel height H = 0.5 above a cavity of depth 1, uniform inflow, free slip on the lower
 wall outside the no-slip span [-0.4, 1.75], forcing in the y-momentum equation only, the sensor cost,
 Re = 6250.  The GPU (FP64) against the oracle: trajectories, the ensemble, and the discrete adjoint
-with the slip rule transposed.  (The traction-free outlet is kept convective; see the design notes.)
+with the slip rule transposed.  (The outlet stays convective: a traction-free outlet would make the
+pressure Dirichlet there, a non-singular Poisson problem the solver does not handle.)
 """
 import numpy as np
 import pytest
