@@ -1004,6 +1004,22 @@ def test_paper_workload_geometry_matches_table_1():
     ("            acc += yk * jb->h0[k];",
      "            acc += yk * hi[k];",
      "test_domain_gradient_exact_for_linear_dynamics"),
+    # the Gauss-Newton Hessian with N I instead of (N - 1) I (Eq. Hessian_EnVar)
+    ("            H[(size_t)i * N + j] = a + (i == j ? (double)(N - 1) : 0.0);",
+     "            H[(size_t)i * N + j] = a + (i == j ? (double)N : 0.0);",
+     "test_gauss_newton_is_exact_in_one_step_for_linear_dynamics"),
+    # the L-BFGS second loop with the correction's sign flipped
+    ("        for (int i = 0; i < N; ++i) q[i] += s[i] * (a[k] - b);",
+     "        for (int i = 0; i < N; ++i) q[i] += s[i] * (b - a[k]);",
+     "test_lbfgs_two_loop_equals_dense_bfgs_update"),
+    # the sampler's convolution factor with the kernel's own width (not half of it)
+    ("            G[(size_t)r * nxi + k] = c * exp(-2.0 * d * d / (a * a));",
+     "            G[(size_t)r * nxi + k] = c * exp(-d * d / (a * a));",
+     "test_sampler_factor_reproduces_gaussian_kernel"),
+    # the adjoint of the advective cross term with its operands transposed
+    ("                double bun = a * vn_c / dy, bvn = a * un_c / dy;",
+     "                double bun = a * un_c / dy, bvn = a * vn_c / dy;",
+     "test_adjoint_gradient_matches_central_differences"),
 ])
 def test_core_pins_fail_on_planted_mistakes(tmp_path, old, new, pin):
     """Plant one plausible mistake in a copy of the oracle: the named pin, which does not restate
@@ -1011,5 +1027,42 @@ def test_core_pins_fail_on_planted_mistakes(tmp_path, old, new, pin):
     if pin == "test_manufactured_solution_second_order":
         pytest.importorskip("sympy")
     with oracle.planted_mistake(old, new, str(tmp_path)):
+        with pytest.raises(AssertionError):
+            globals()[pin]()
+
+
+class _planted_py:
+    """Plant a mistake in one function of the oracle's Python layer: its source with one text
+    replacement, compiled in a copy of the module's namespace, stands in for it inside the block."""
+
+    def __init__(self, name, old, new):
+        self.name, self.old, self.new = name, old, new
+
+    def __enter__(self):
+        import inspect
+        import textwrap
+        src = textwrap.dedent(inspect.getsource(getattr(oracle, self.name)))
+        assert src.count(self.old) == 1, src.count(self.old)
+        ns = dict(vars(oracle))
+        exec(compile(src.replace(self.old, self.new), f"<planted {self.name}>", "exec"), ns)
+        self.saved = getattr(oracle, self.name)
+        setattr(oracle, self.name, ns[self.name])
+        return self
+
+    def __exit__(self, *exc):
+        setattr(oracle, self.name, self.saved)
+        return False
+
+
+@pytest.mark.parametrize("name,old,new,pin", [
+    # Eq. (lsob) without the (1 + l^2) normalisation of the right-hand side
+    ("h1_smooth", "spla.spsolve(A, (1.0 + l_sob**2) * g[:n])", "spla.spsolve(A, g[:n])",
+     "test_h1_smoothing_closed_forms"),
+    # Eq. (eigenvm1) scaled by sqrt(N) instead of sqrt(N - 1)
+    ("eigen_ensemble", "np.sqrt(max(lam[r], 0.0) * (N - 1)) * v", "np.sqrt(max(lam[r], 0.0) * N) * v",
+     "test_eigen_ensemble_invariants_on_the_cavity_region"),
+])
+def test_python_layer_pins_fail_on_planted_mistakes(name, old, new, pin):
+    with _planted_py(name, old, new):
         with pytest.raises(AssertionError):
             globals()[pin]()
