@@ -1020,6 +1020,14 @@ def test_paper_workload_geometry_matches_table_1():
     ("                double bun = a * vn_c / dy, bvn = a * un_c / dy;",
      "                double bun = a * un_c / dy, bvn = a * vn_c / dy;",
      "test_adjoint_gradient_matches_central_differences"),
+    # the pressure CG's residual update with the wrong sign
+    ("        for (size_t k = 0; k < nc; ++k) { x[k] += alpha * p[k]; r[k] -= alpha * q[k]; }",
+     "        for (size_t k = 0; k < nc; ++k) { x[k] += alpha * p[k]; r[k] += alpha * q[k]; }",
+     "test_poisson_solve_matches_dense_lstsq"),
+    # the control forcing on u faces from one neighbouring cell instead of the two
+    ("            fu[k] = 0.5 * (FX[(size_t)j * nx + il] + FX[(size_t)j * nx + ir]);",
+     "            fu[k] = FX[(size_t)j * nx + ir];",
+     "test_faces_to_control_is_transpose_of_control_to_faces"),
 ])
 def test_core_pins_fail_on_planted_mistakes(tmp_path, old, new, pin):
     """Plant one plausible mistake in a copy of the oracle: the named pin, which does not restate
