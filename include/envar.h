@@ -281,7 +281,8 @@ int envar_kernel_launches(envar_handle h, long long *count);
  * allocates the 256 MB eviction buffer (kept by the handle).  which: 0 momentum predictor (in MIXED handles fused
  * with the Poisson right-hand side), 1 level-0 pre-smoothing + restriction,
  * 2 level-0 prolongation + post-smoothing + dot product, 3 inner SpMV, 4 inner AXPY,
- * 5 outer FP64 residual, 6 projection correction with the Welford update, 7 coarse-level
+ * 5 outer residual (FP64, or df64 in MIXED handles: block partials only, no totals), 6 projection
+ * correction with the Welford update, 7 coarse-level
  * block kernel, 8 Poisson right-hand side (MIXED: the fused predictor).  Overwrites the members' state: call
  * envar_reset_members or a forward run before using the state again. */
 int envar_time_kernel(envar_handle h, int which, int reps, double *ms_per_launch);
